@@ -1,0 +1,217 @@
+"""CPU oracle for VELO reconstruction -- test infrastructure only.
+
+Plain, slow restatement of the paper's VELO method (section 2.3.1) used to
+check the GPU library: clusters and track hit lists must agree bit for bit,
+fitted states within the stated tolerance.  It shares no code with the GPU
+library and is imported only by ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py``.
+
+``velo_oracle.c`` holds the reconstruction; ``metrics.py`` the truth matching
+(section 3.1 definitions); ``mlp.py`` the ghost-classifier reference.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "velo_oracle.c")
+_LIB = os.path.join(_HERE, "_velo_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NSTATE = 13
+STATE_NAMES = ("x", "y", "z", "tx", "ty", "c00", "c20", "c22", "c11", "c31", "c33", "chi2", "score")
+FLAG_KEEP = 1
+FLAG_3HIT = 2
+
+
+class _Geo(ctypes.Structure):
+    _fields_ = [("n_modules", ctypes.c_uint32), ("sensors_per_module", ctypes.c_uint32),
+                ("n_cols", ctypes.c_uint32), ("n_rows", ctypes.c_uint32),
+                ("pitch", ctypes.c_float), ("module_z", ctypes.c_void_p),
+                ("sensor_ox", ctypes.c_void_p), ("sensor_oy", ctypes.c_void_p),
+                ("col_dx", ctypes.c_void_p), ("col_dy", ctypes.c_void_p),
+                ("row_dx", ctypes.c_void_p), ("row_dy", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("max_slope", ctypes.c_float), ("tan_phi_tol", ctypes.c_float),
+                ("max_scatter_seed", ctypes.c_float), ("max_scatter_fwd", ctypes.c_float),
+                ("max_scatter_3hit", ctypes.c_float), ("max_skipped", ctypes.c_uint32),
+                ("sigma_meas", ctypes.c_float), ("pt_nominal", ctypes.c_float),
+                ("ms_coeff", ctypes.c_float)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("n_threads", ctypes.c_uint32), ("all_candidates", ctypes.c_uint32),
+                ("shuffle_seed", ctypes.c_uint64)]
+
+
+_P = ctypes.POINTER
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint32), ("n_clusters", ctypes.c_uint64),
+                ("n_tracks", ctypes.c_uint64), ("n_track_hits", ctypes.c_uint64),
+                ("cluster_off", _P(ctypes.c_uint32)), ("cl_x", _P(ctypes.c_float)),
+                ("cl_y", _P(ctypes.c_float)), ("cl_key", _P(ctypes.c_uint32)),
+                ("cl_npix", _P(ctypes.c_uint32)), ("track_off", _P(ctypes.c_uint32)),
+                ("hit_off", _P(ctypes.c_uint32)), ("hit_ids", _P(ctypes.c_uint32)),
+                ("states", _P(ctypes.c_float)), ("ndof", _P(ctypes.c_uint32)),
+                ("flags", _P(ctypes.c_uint32)), ("seed_s", _P(ctypes.c_float)),
+                ("event_status", _P(ctypes.c_uint32)), ("n_pixels", ctypes.c_uint64),
+                ("pix_cluster", _P(ctypes.c_int32))]
+
+
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-pthread"]
+
+
+def build(force: bool = False) -> str:
+    """Compiles ``velo_oracle.c`` (plain C, no FMA contraction)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.oracle_reconstruct.argtypes = [_P(_Geo), _P(_Params), _P(_Opts), ctypes.c_uint32,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           _P(_Result)]
+        lib.oracle_reconstruct.restype = ctypes.c_int
+        lib.oracle_free.argtypes = [_P(_Result)]
+        lib.oracle_fit.argtypes = [_P(_Geo), _P(_Params), ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+        _lib = lib
+    return _lib
+
+
+@dataclasses.dataclass
+class Params:
+    """Tracking and fit parameters (mm, GeV).  Defaults: the frozen readings."""
+    max_slope: float = 0.4
+    tan_phi_tol: float = math.tan(0.05)
+    max_scatter_seed: float = 0.1
+    max_scatter_fwd: float = 0.1
+    max_scatter_3hit: float = 0.02
+    max_skipped: int = 1
+    sigma_meas: float = 0.055 / math.sqrt(12.0)
+    pt_nominal: float = 0.4
+    ms_coeff: float = 1.0
+
+    def _c(self) -> _Params:
+        p = _Params()
+        for name, _ in _Params._fields_:
+            setattr(p, name, getattr(self, name))
+        return p
+
+
+def _geo_c(g):
+    keep = [np.ascontiguousarray(a) for a in (g.module_z.astype(np.float32), g.sensor_ox.astype(np.float32),
+                                              g.sensor_oy.astype(np.float32), g.col_dx.astype(np.int8),
+                                              g.col_dy.astype(np.int8), g.row_dx.astype(np.int8),
+                                              g.row_dy.astype(np.int8))]
+    c = _Geo(g.n_modules, g.sensors_per_module, g.n_cols, g.n_rows, g.pitch,
+             *[a.ctypes.data for a in keep])
+    return c, keep
+
+
+@dataclasses.dataclass
+class OracleResult:
+    n_events: int
+    cluster_off: np.ndarray
+    cl_x: np.ndarray
+    cl_y: np.ndarray
+    cl_key: np.ndarray
+    cl_npix: np.ndarray
+    track_off: np.ndarray
+    hit_off: np.ndarray
+    hit_ids: np.ndarray
+    states: np.ndarray      # float32 [n_tracks, 13]
+    ndof: np.ndarray
+    flags: np.ndarray
+    seed_s: np.ndarray
+    event_status: np.ndarray
+    pix_cluster: np.ndarray  # int32 [n_pixels] event-local cluster id per raw pixel
+
+    @property
+    def n_tracks(self) -> int:
+        return int(self.track_off[-1])
+
+    def track_hits(self, t: int) -> np.ndarray:
+        return self.hit_ids[self.hit_off[t]:self.hit_off[t + 1]]
+
+    def event_tracks(self, e: int) -> list[tuple[int, ...]]:
+        return [tuple(int(h) for h in self.track_hits(t))
+                for t in range(int(self.track_off[e]), int(self.track_off[e + 1]))]
+
+
+def reconstruct(geom, events, params: Params | None = None, n_threads: int = 1,
+                all_candidates: bool = False, shuffle_seed: int = 0) -> OracleResult:
+    """Runs the oracle over a ``velo_synth.SynthEvents`` batch."""
+    lib = _load()
+    params = params or Params()
+    gc, keep = _geo_c(geom)
+    pc = params._c()
+    oc = _Opts(n_threads, 1 if all_candidates else 0, shuffle_seed)
+    so = np.ascontiguousarray(events.sensor_off, np.uint32)
+    col = np.ascontiguousarray(events.col, np.uint16)
+    row = np.ascontiguousarray(events.row, np.uint16)
+    r = _Result()
+    rc = lib.oracle_reconstruct(ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(oc), events.n_events,
+                                so.ctypes.data, col.ctypes.data, row.ctypes.data, ctypes.byref(r))
+    if rc != 0:
+        raise ValueError("oracle_reconstruct: bad geometry")
+    try:
+        def arr(ptr, n, dt, shape=None):
+            n = int(n)
+            if n == 0:
+                return np.zeros(shape or (0,), dt)
+            a = np.ctypeslib.as_array(ptr, shape=(n,)).astype(dt, copy=True)
+            return a.reshape(shape) if shape else a
+        ne, nc, nt, nh = int(r.n_events), int(r.n_clusters), int(r.n_tracks), int(r.n_track_hits)
+        out = OracleResult(
+            n_events=ne, cluster_off=arr(r.cluster_off, ne + 1, np.uint32),
+            cl_x=arr(r.cl_x, nc, np.float32), cl_y=arr(r.cl_y, nc, np.float32),
+            cl_key=arr(r.cl_key, nc, np.uint32), cl_npix=arr(r.cl_npix, nc, np.uint32),
+            track_off=arr(r.track_off, ne + 1, np.uint32), hit_off=arr(r.hit_off, nt + 1, np.uint32),
+            hit_ids=arr(r.hit_ids, nh, np.uint32),
+            states=arr(r.states, nt * NSTATE, np.float32, (nt, NSTATE)),
+            ndof=arr(r.ndof, nt, np.uint32), flags=arr(r.flags, nt, np.uint32),
+            seed_s=arr(r.seed_s, nt, np.float32), event_status=arr(r.event_status, ne, np.uint32),
+            pix_cluster=arr(r.pix_cluster, int(r.n_pixels), np.int32))
+    finally:
+        lib.oracle_free(ctypes.byref(r))
+    del keep
+    return out
+
+
+def fit(geom, x, y, module, params: Params | None = None):
+    """Fits one hand-made track (hits in decreasing-module order)."""
+    lib = _load()
+    params = params or Params()
+    gc, keep = _geo_c(geom)
+    pc = params._c()
+    x = np.ascontiguousarray(x, np.float32)
+    y = np.ascontiguousarray(y, np.float32)
+    m = np.ascontiguousarray(module, np.uint32)
+    st = np.zeros(NSTATE, np.float32)
+    nd = np.zeros(1, np.uint32)
+    lib.oracle_fit(ctypes.byref(gc), ctypes.byref(pc), x.ctypes.data, y.ctypes.data, m.ctypes.data,
+                   len(x), st.ctypes.data, nd.ctypes.data)
+    del keep
+    return st, int(nd[0])

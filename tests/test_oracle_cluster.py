@@ -1,0 +1,130 @@
+"""Pins for the oracle's clustering (paper section 2.3.1: clusters are the
+connected components of the fired pixels of a sensor).
+
+The oracle's flood fill is checked against scipy.ndimage.label with 8-connectivity,
+and its cluster positions against the exact (double-precision) centroid of the
+pixel centres mapped to the global frame.
+"""
+import numpy as np
+import pytest
+from scipy import ndimage
+
+import oracle
+import velo_synth
+
+
+def _one_sensor_event(geom, pixels, sensor=0):
+    lists = [[[] for _ in range(geom.n_sensors)]]
+    lists[0][sensor] = list(pixels)
+    return velo_synth.make_events(lists, geom.n_sensors)
+
+
+def _scipy_partition(pixels, n=256):
+    img = np.zeros((n, n), bool)
+    for c, r in pixels:
+        img[c, r] = True
+    lab, _ = ndimage.label(img, structure=np.ones((3, 3), int))
+    return lab
+
+
+@pytest.mark.parametrize("density", [1e-3, 1e-2, 0.05, 0.15, 0.3])
+@pytest.mark.parametrize("side", [16, 256])
+def test_components_match_scipy(geom, density, side):
+    rng = np.random.default_rng(int(density * 1e4) + side)
+    n = max(1, int(density * side * side))
+    cols = rng.integers(0, side, n)
+    rows = rng.integers(0, side, n)
+    pixels = list(zip(cols.tolist(), rows.tolist()))
+    # duplicates on purpose
+    pixels += pixels[: n // 10]
+    rng.shuffle(pixels)
+    ev = _one_sensor_event(geom, pixels, sensor=5)
+    r = oracle.reconstruct(geom, ev)
+    lab = _scipy_partition(pixels)
+    # same partition: pixel -> oracle id and pixel -> scipy label are a bijection
+    ids = r.pix_cluster
+    sc = np.array([lab[c, rr] for c, rr in pixels])
+    pairs = set(zip(ids.tolist(), sc.tolist()))
+    assert len(pairs) == len(set(ids.tolist())) == len(set(sc.tolist())) == lab.max()
+    assert int(r.cluster_off[-1]) == lab.max()
+    # canonical order: increasing smallest pixel key within the sensor
+    keys = r.cl_key.astype(np.int64)
+    assert np.all(np.diff(keys) > 0)
+    assert np.all((keys >> 16) == 5)
+    # pixel counts of distinct pixels
+    uniq = sorted(set(pixels))
+    counts = np.bincount(np.array([ids[pixels.index(p)] for p in uniq]), minlength=lab.max())
+    assert np.array_equal(counts, r.cl_npix)
+
+
+def test_hand_cases(geom):
+    # diagonal-only adjacency joins; column 255 / next column row 0 never join;
+    # (c, 255) and (c + 1, 0) have consecutive keys but are not neighbours
+    pixels = [(10, 10), (11, 11), (12, 12),      # one diagonal cluster
+              (20, 255), (21, 0),                # two clusters
+              (255, 5), (0, 5),                  # two clusters (no wrap-around)
+              (100, 100), (100, 100)]            # duplicate collapses
+    ev = _one_sensor_event(geom, pixels)
+    r = oracle.reconstruct(geom, ev)
+    assert int(r.cluster_off[-1]) == 6
+    # canonical order by smallest key: (0,5) (10,10)+ (20,255) (21,0) (100,100) (255,5)
+    assert list(r.cl_npix) == [1, 3, 1, 1, 1, 1]
+    assert r.pix_cluster[0] == r.pix_cluster[1] == r.pix_cluster[2]
+    assert r.pix_cluster[3] != r.pix_cluster[4]
+    assert r.pix_cluster[7] == r.pix_cluster[8]
+
+
+def test_empty_and_invalid(geom):
+    ev = _one_sensor_event(geom, [])
+    r = oracle.reconstruct(geom, ev)
+    assert int(r.cluster_off[-1]) == 0 and r.n_tracks == 0 and r.event_status[0] == 0
+    ev = _one_sensor_event(geom, [(3, 3), (300, 2)])
+    r = oracle.reconstruct(geom, ev)
+    assert r.event_status[0] & 1
+    assert int(r.cluster_off[-1]) == 1 and r.pix_cluster[1] == -1
+
+
+@pytest.mark.parametrize("sensor", [0, 1, 2, 3, 101, 207])
+def test_centroid_exact(geom, sensor):
+    """Float cluster positions equal the exact centroid within float rounding."""
+    rng = np.random.default_rng(sensor)
+    pixels = []
+    for _ in range(40):
+        c, rr = rng.integers(1, 254, 2)
+        k = rng.integers(1, 4)
+        blob = [(c, rr), (c + 1, rr), (c, rr + 1), (c + 1, rr + 1)][:k + 1]
+        pixels += [tuple(map(int, b)) for b in blob]
+    ev = _one_sensor_event(geom, pixels, sensor)
+    r = oracle.reconstruct(geom, ev)
+    lab = _scipy_partition(pixels)
+    for cid in range(int(r.cluster_off[-1])):
+        members = sorted({p for p, i in zip(pixels, r.pix_cluster) if i == cid})
+        cc = np.mean([m[0] for m in members]) + 0.5
+        rc = np.mean([m[1] for m in members]) + 0.5
+        pitch = float(geom.pitch)
+        lx, ly = cc * pitch, rc * pitch
+        x = geom.sensor_ox[sensor] + geom.col_dx[sensor] * lx + geom.row_dx[sensor] * ly
+        y = geom.sensor_oy[sensor] + geom.col_dy[sensor] * lx + geom.row_dy[sensor] * ly
+        assert abs(r.cl_x[cid] - x) <= 4e-6 * max(1.0, abs(x))
+        assert abs(r.cl_y[cid] - y) <= 4e-6 * max(1.0, abs(y))
+        # the cluster lies on the sensor's own area in the global frame
+        assert len({lab[m] for m in members}) == 1
+        key = (sensor << 16) | (members[0][0] * 256 + members[0][1])
+        assert r.cl_key[cid] == key
+
+
+def test_generated_event_clusters(geom, cfg0_events, cfg0_oracle):
+    """Every sensor of a generated event partitions like scipy (first 3 events)."""
+    ev, r = cfg0_events, cfg0_oracle
+    for e in range(3):
+        base = int(r.cluster_off[e])
+        for s in range(0, geom.n_sensors, 7):
+            a, b = int(ev.sensor_off[e * geom.n_sensors + s]), int(ev.sensor_off[e * geom.n_sensors + s + 1])
+            pix = list(zip(ev.col[a:b].tolist(), ev.row[a:b].tolist()))
+            if not pix:
+                continue
+            lab = _scipy_partition(pix)
+            ids = r.pix_cluster[a:b]
+            sc = np.array([lab[c, rr] for c, rr in pix])
+            assert len(set(zip(ids.tolist(), sc.tolist()))) == lab.max() == len(set(ids.tolist()))
+            assert np.all((r.cl_key[base + ids] >> 16) == s)
