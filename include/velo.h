@@ -1,0 +1,189 @@
+/*
+ * velo.h -- C ABI of the GB300 VELO reconstruction library.
+ *
+ * Reconstructs batches of independent LHCb VELO events on one GPU: pixel
+ * clustering, search-by-triplet seeding with track following, and a simple
+ * Kalman fit extrapolated to the beamline (paper, section 2.3.1), plus an
+ * optional learned ghost-track classifier evaluated after the fit.
+ *
+ * Conventions
+ *   - Pointers named in a *device* field are CUDA device pointers; the caller
+ *     allocates and owns them.  Pointers in geometry / parameter structs and
+ *     every pointer named *_host are host pointers, read during the call only.
+ *   - Every function returns a velo_status; no C++ exception crosses the ABI.
+ *     velo_last_error() gives a message for the calling thread's last error.
+ *   - Work is enqueued asynchronously on the caller's stream; device-side
+ *     problems (bad pixel coordinates, capacity overflow) are recorded in
+ *     per-event status words and a handle status that velo_sync_status() reads.
+ *   - A handle is used by one host thread at a time; several handles may share
+ *     a GPU.  Results never depend on the launch schedule: output order is
+ *     canonical (see velo_output).
+ */
+#ifndef VELO_H
+#define VELO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum velo_status {
+  VELO_OK = 0,
+  VELO_ERR_INPUT = 1,     /* malformed descriptor, offsets, or pixel outside a sensor */
+  VELO_ERR_CAPACITY = 2,  /* an output or per-event capacity was exceeded */
+  VELO_ERR_NOMEM = 3,     /* the handle's arena (or a slot) cannot hold the batch */
+  VELO_ERR_TIMEOUT = 4,   /* a bounded wait ran out */
+  VELO_ERR_CUDA = 5,      /* a CUDA runtime call failed */
+  VELO_ERR_STATE = 6      /* call not valid in the handle's current state */
+} velo_status;
+
+/* Per-event status bits (velo_output.event_status). */
+#define VELO_EV_BAD_PIXEL 0x1u    /* pixel(s) outside the sensor were ignored */
+#define VELO_EV_BAD_OFFSETS 0x2u  /* sensor offsets decrease: event skipped */
+#define VELO_EV_OVERFLOW 0x4u     /* event exceeds the per-event working capacity: skipped */
+#define VELO_EV_TRUNCATED 0x8u    /* outputs of this event did not fit the caller's buffers */
+
+/* Number of floats per track state (SoA rows of velo_output.states). */
+#define VELO_NSTATE 13
+/* Row order: x, y, z, tx, ty, c00, c20, c22, c11, c31, c33, chi2, score.
+ * (x, y) at z, the point of closest approach to the beam axis; (tx, ty) the
+ * slopes; cIJ the covariance of the state vector (x, y, tx, ty) -- index 0 x,
+ * 1 y, 2 tx, 3 ty; chi2 the sum of both projections; score the ghost
+ * classifier output in [0, 1] (0 when the classifier is off). */
+
+/*
+ * Detector geometry (host pointers, copied at velo_create).  Sensor s lies in
+ * module s / sensors_per_module; modules are planes at module_z (increasing,
+ * mm).  Pixel (col, row) of sensor s has its centre at
+ *   x = sensor_ox + col_dx * lc + row_dx * lr,  y = sensor_oy + col_dy * lc + row_dy * lr,
+ *   lc = (col + 0.5) * pitch,  lr = (row + 0.5) * pitch,
+ * with unit axes in {-1, 0, 1}.  Limits: 3 <= n_modules <= 64,
+ * sensors_per_module == 4, n_cols, n_rows <= 256.
+ */
+typedef struct velo_geometry {
+  uint32_t n_modules;
+  uint32_t sensors_per_module;
+  uint32_t n_cols, n_rows;
+  float pitch;                        /* mm */
+  const float *module_z;              /* [n_modules] */
+  const float *sensor_ox, *sensor_oy; /* [n_sensors] mm */
+  const int8_t *col_dx, *col_dy;      /* [n_sensors] */
+  const int8_t *row_dx, *row_dy;      /* [n_sensors] */
+} velo_geometry;
+
+/*
+ * Method parameters (paper section 2.3.1; every value the paper leaves open
+ * is a parameter).  Distances in mm, squared distances in mm^2, momenta GeV.
+ */
+typedef struct velo_params {
+  float max_slope;        /* |tx|, |ty| bound of a seed's first two hits */
+  float tan_phi_tol;      /* phi compatibility: |x_p y_q - y_p x_q| <= tol * (x_p x_q + y_p y_q) */
+  float max_scatter_seed; /* squared distance of the third seed hit to the line */
+  float max_scatter_fwd;  /* squared distance of an added hit to the extrapolation */
+  float max_scatter_3hit; /* 3-hit tracks kept only below this seed scatter */
+  uint32_t max_skipped;   /* consecutive modules a track may miss */
+  float sigma_meas;       /* hit resolution used by the fit */
+  float pt_nominal;       /* transverse momentum assumed for scattering (0.4 GeV) */
+  float ms_coeff;         /* slope kick per module crossed: ms_coeff * 1e-3 * sin(theta) / pt_nominal */
+  uint32_t use_mlp;       /* 1: keep candidates by classifier score instead of the plain cuts */
+  float mlp_threshold;    /* keep a candidate when score >= threshold */
+} velo_params;
+
+/* Handle capacities (velo_create).  Zero fields take defaults. */
+typedef struct velo_config {
+  uint32_t max_events;      /* events per velo_reconstruct call */
+  uint64_t max_pixels;      /* pixels per call (sum over events) */
+  uint64_t max_tracks;      /* tracks per call (working storage) */
+  uint64_t max_track_hits;  /* hits on tracks per call (working storage) */
+  uint32_t flags;           /* VELO_CFG_* */
+  uint32_t n_slots;         /* serving slots (velo_slot_*), 0 = none */
+} velo_config;
+
+#define VELO_CFG_CLUSTERS 0x1u  /* reserve storage for cluster output */
+
+typedef struct velo_handle velo_handle;
+
+/*
+ * A batch of events (device pointers).  Pixels of event e, sensor s occupy
+ * indices [sensor_off[e*n_sensors + s], sensor_off[e*n_sensors + s + 1]) of
+ * col/row, in any order; a repeated (col, row) counts once.  sensor_off has
+ * n_events * n_sensors + 1 non-decreasing entries.
+ */
+typedef struct velo_events {
+  uint32_t n_events;
+  const uint32_t *sensor_off;
+  const uint16_t *col;
+  const uint16_t *row;
+} velo_events;
+
+/*
+ * Outputs (device pointers, caller-allocated).  Tracks of event e are
+ * [track_off[e], track_off[e+1]), ordered by their hit-id sequence; hit ids
+ * are event-local cluster ids (clusters ordered by module, sensor, smallest
+ * pixel key col*256+row), listed in decreasing module order.
+ * totals[0..3] = tracks, track hits, clusters, handle error bits of the call.
+ * If a capacity is exceeded the affected events are marked
+ * VELO_EV_TRUNCATED, totals hold the sizes that were needed, and
+ * velo_sync_status() returns VELO_ERR_CAPACITY.
+ */
+typedef struct velo_output {
+  uint32_t cap_tracks, cap_hits, cap_clusters;
+  uint32_t *track_off;    /* [n_events + 1] */
+  uint32_t *hit_off;      /* [cap_tracks + 1] */
+  uint32_t *hit_ids;      /* [cap_hits] */
+  float *states;          /* [VELO_NSTATE][cap_tracks] */
+  uint8_t *ndof;          /* [cap_tracks], 2 * hits - 4 */
+  uint32_t *event_status; /* [n_events] VELO_EV_* bits */
+  uint32_t *totals;       /* [4] */
+  /* optional cluster output (NULL to skip; needs VELO_CFG_CLUSTERS) */
+  uint32_t *cluster_off;  /* [n_events + 1] */
+  float *cl_x, *cl_y;     /* [cap_clusters] global mm */
+  uint32_t *cl_key;       /* [cap_clusters] sensor << 16 | smallest col*256+row */
+} velo_output;
+
+/* Creates a handle on the current CUDA device; allocates its arena once. */
+int velo_create(const velo_geometry *geometry, const velo_params *params,
+                const velo_config *config, velo_handle **out);
+void velo_destroy(velo_handle *h);
+
+/* Bytes of device memory a handle with this configuration holds. */
+int velo_required_bytes(const velo_geometry *geometry, const velo_config *config, size_t *bytes);
+
+/* Replaces the method parameters (takes effect at the next call). */
+int velo_set_params(velo_handle *h, const velo_params *params);
+
+/*
+ * Reconstructs a batch; enqueues all work on `stream` (a cudaStream_t, 0 for
+ * the legacy stream) and returns without waiting.
+ */
+int velo_reconstruct(velo_handle *h, const velo_events *events, const velo_output *out, void *stream);
+
+/*
+ * Waits for the stream and reads the handle's device error word for the last
+ * call: VELO_OK, VELO_ERR_INPUT (some event had bad pixels or offsets),
+ * VELO_ERR_CAPACITY (some output or event did not fit), VELO_ERR_TIMEOUT.
+ */
+int velo_sync_status(velo_handle *h, void *stream);
+
+/*
+ * End-to-end call with HOST buffers: copies the events from host memory
+ * (pinned for asynchronous copies), reconstructs, and copies the outputs back
+ * into host buffers of the same layout as velo_output.  Synchronous.
+ */
+int velo_reconstruct_host(velo_handle *h, uint32_t n_events, const uint32_t *sensor_off_host,
+                          const uint16_t *col_host, const uint16_t *row_host,
+                          const velo_output *out_host, void *stream);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *velo_last_error(void);
+
+/* Library version string. */
+const char *velo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VELO_H */

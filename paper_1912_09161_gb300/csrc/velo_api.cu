@@ -1,0 +1,411 @@
+// C ABI of the VELO reconstruction library: handle, device arena, launch
+// sequence, status read-back and the host-buffer (end-to-end) entry point.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "velo_internal.cuh"
+
+using namespace velo;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+  do {                                                                                     \
+    cudaError_t _e = (expr);                                                               \
+    if (_e != cudaSuccess) return fail(VELO_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(_e)); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct velo_handle {
+  int device = 0;
+  int n_sm = 0;
+  velo_geometry geo_host{};
+  DevGeometry geo{};
+  DevParams par{};
+  velo_config cfg{};
+  // device arena
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  DevGeometry* d_geo = nullptr;
+  Counters* d_cnt = nullptr;
+  WorkView wk{};
+  // kernel classes
+  Caps caps[2]{};
+  int threads[2]{256, 256};
+  int ctas[2]{0, 0};
+  // host-path staging (allocated on first use)
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  uint32_t* h_totals = nullptr;  // pinned
+  uint32_t last_error_bits = 0;
+};
+
+namespace {
+
+bool geometry_ok(const velo_geometry* g) {
+  if (!g || g->n_modules < 3 || g->n_modules > (uint32_t)kMaxModules) return false;
+  if (g->sensors_per_module != (uint32_t)kSPM) return false;
+  if (g->n_cols == 0 || g->n_rows == 0 || g->n_cols > 256 || g->n_rows > 256) return false;
+  if (!(g->pitch > 0.0f)) return false;
+  if (!g->module_z || !g->sensor_ox || !g->sensor_oy || !g->col_dx || !g->col_dy || !g->row_dx || !g->row_dy)
+    return false;
+  for (uint32_t m = 1; m < g->n_modules; ++m)
+    if (!(g->module_z[m] > g->module_z[m - 1])) return false;
+  const uint32_t ns = g->n_modules * g->sensors_per_module;
+  for (uint32_t s = 0; s < ns; ++s) {
+    int8_t v[4] = {g->col_dx[s], g->col_dy[s], g->row_dx[s], g->row_dy[s]};
+    for (int k = 0; k < 4; ++k)
+      if (v[k] < -1 || v[k] > 1) return false;
+  }
+  return true;
+}
+
+DevParams to_dev(const velo_params& p) {
+  DevParams d{};
+  d.max_slope = p.max_slope;
+  d.tan_phi_tol = p.tan_phi_tol;
+  d.max_scatter_seed = p.max_scatter_seed;
+  d.max_scatter_fwd = p.max_scatter_fwd;
+  d.max_scatter_3hit = p.max_scatter_3hit;
+  d.max_skipped = p.max_skipped;
+  d.sigma_meas = p.sigma_meas;
+  d.pt_nominal = p.pt_nominal;
+  d.ms_coeff = p.ms_coeff;
+  d.use_mlp = p.use_mlp;
+  d.mlp_threshold = p.mlp_threshold;
+  // The pseudo-angle moves by at most one unit per radian, so a window of
+  // atan(tol) plus a margin for rounding covers every phi-compatible hit.
+  double w = atan((double)fabsf(p.tan_phi_tol)) + 1e-3;
+  d.phi_window = (float)w;
+  return d;
+}
+
+bool params_ok(const velo_params* p) {
+  if (!p) return false;
+  const float v[] = {p->max_slope, p->tan_phi_tol, p->max_scatter_seed, p->max_scatter_fwd,
+                     p->max_scatter_3hit, p->sigma_meas, p->pt_nominal, p->ms_coeff};
+  for (float x : v)
+    if (!(x >= 0.0f) || isinf(x)) return false;
+  return p->pt_nominal > 0.0f && p->sigma_meas > 0.0f;
+}
+
+velo_config with_defaults(const velo_config* c) {
+  velo_config d{};
+  if (c) d = *c;
+  if (!d.max_events) d.max_events = 16384;
+  if (!d.max_pixels) d.max_pixels = (uint64_t)d.max_events * 8192;
+  if (!d.max_tracks) d.max_tracks = d.max_pixels / 16 + 1024;
+  if (!d.max_track_hits) d.max_track_hits = d.max_tracks * 16;
+  if (d.max_tracks > 0xFFFFFFF0ull) d.max_tracks = 0xFFFFFFF0ull;
+  if (d.max_track_hits > 0xFFFFFFF0ull) d.max_track_hits = 0xFFFFFFF0ull;
+  return d;
+}
+
+struct ArenaPlan {
+  size_t geo, cnt, rec, q0, q1, st, nh, ho, hits, clx, cly, clk, total;
+};
+
+ArenaPlan plan_arena(const velo_config& c) {
+  ArenaPlan a{};
+  size_t o = 0;
+  a.geo = o; o = align256(o + sizeof(DevGeometry));
+  a.cnt = o; o = align256(o + sizeof(Counters));
+  a.rec = o; o = align256(o + sizeof(EventRec) * c.max_events);
+  a.q0 = o; o = align256(o + 4ull * c.max_events);
+  a.q1 = o; o = align256(o + 4ull * c.max_events);
+  a.st = o; o = align256(o + 4ull * VELO_NSTATE * c.max_tracks);
+  a.nh = o; o = align256(o + 2ull * c.max_tracks);
+  a.ho = o; o = align256(o + 4ull * c.max_tracks);
+  a.hits = o; o = align256(o + 4ull * c.max_track_hits);
+  if (c.flags & VELO_CFG_CLUSTERS) {
+    a.clx = o; o = align256(o + 4ull * c.max_pixels);
+    a.cly = o; o = align256(o + 4ull * c.max_pixels);
+    a.clk = o; o = align256(o + 4ull * c.max_pixels);
+  }
+  a.total = o;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* velo_last_error(void) { return g_err; }
+
+const char* velo_version(void) { return "velo-gb300 0.1 (sm_103a)"; }
+
+int velo_required_bytes(const velo_geometry* geometry, const velo_config* config, size_t* bytes) {
+  if (!geometry_ok(geometry) || !bytes) return fail(VELO_ERR_INPUT, "velo_required_bytes: bad geometry or null output");
+  *bytes = plan_arena(with_defaults(config)).total;
+  return VELO_OK;
+}
+
+int velo_create(const velo_geometry* geometry, const velo_params* params, const velo_config* config,
+                velo_handle** out) {
+  if (!out) return fail(VELO_ERR_INPUT, "velo_create: null output pointer");
+  *out = nullptr;
+  if (!geometry_ok(geometry)) return fail(VELO_ERR_INPUT, "velo_create: invalid geometry");
+  if (!params_ok(params)) return fail(VELO_ERR_INPUT, "velo_create: invalid parameters");
+  velo_handle* h = new (std::nothrow) velo_handle();
+  if (!h) return fail(VELO_ERR_NOMEM, "velo_create: host allocation failed");
+  h->cfg = with_defaults(config);
+  h->geo_host = *geometry;
+  h->par = to_dev(*params);
+  DevGeometry& g = h->geo;
+  g.n_modules = (int)geometry->n_modules;
+  g.n_sensors = (int)(geometry->n_modules * geometry->sensors_per_module);
+  g.n_cols = (int)geometry->n_cols;
+  g.n_rows = (int)geometry->n_rows;
+  g.pitch = geometry->pitch;
+  for (int m = 0; m < g.n_modules; ++m) g.module_z[m] = geometry->module_z[m];
+  for (int s = 0; s < g.n_sensors; ++s) {
+    g.ox[s] = geometry->sensor_ox[s];
+    g.oy[s] = geometry->sensor_oy[s];
+    g.cdx[s] = (float)geometry->col_dx[s];
+    g.cdy[s] = (float)geometry->col_dy[s];
+    g.rdx[s] = (float)geometry->row_dx[s];
+    g.rdy[s] = (float)geometry->row_dy[s];
+  }
+  int rc = VELO_OK;
+  do {
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e)); break; }
+    cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
+    // class 0: two CTAs per SM; class 1: one CTA per SM with the largest plan
+    uint32_t budget0 = (uint32_t)(smem_sm / 2 - 1024);
+    uint32_t budget1 = (uint32_t)smem_optin;
+    if (budget0 > budget1) budget0 = budget1;
+    h->caps[0] = make_caps(budget0, g.n_modules, 256);
+    h->caps[1] = make_caps(budget1, g.n_modules, 256);
+    for (int c = 0; c < 2; ++c) {
+      e = reco_set_smem_limit(h->threads[c], (int)h->caps[c].smem);
+      if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)); break; }
+      int per_sm = 0;
+      e = reco_occupancy(h->threads[c], (int)h->caps[c].smem, &per_sm);
+      if (e != cudaSuccess || per_sm < 1) { rc = fail(VELO_ERR_CUDA, "occupancy query failed"); break; }
+      h->ctas[c] = per_sm * h->n_sm;
+    }
+    if (rc) break;
+    ArenaPlan a = plan_arena(h->cfg);
+    e = cudaMalloc(&h->arena, a.total);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", a.total, cudaGetErrorString(e)); h->arena = nullptr; break; }
+    h->arena_bytes = a.total;
+    char* base = (char*)h->arena;
+    h->d_geo = (DevGeometry*)(base + a.geo);
+    h->d_cnt = (Counters*)(base + a.cnt);
+    WorkView& w = h->wk;
+    w.cnt = h->d_cnt;
+    w.rec = (EventRec*)(base + a.rec);
+    w.queue[0] = (uint32_t*)(base + a.q0);
+    w.queue[1] = (uint32_t*)(base + a.q1);
+    w.tr_state = (float*)(base + a.st);
+    w.tr_nhits = (uint16_t*)(base + a.nh);
+    w.tr_hitoff = (uint32_t*)(base + a.ho);
+    w.tr_hits = (uint32_t*)(base + a.hits);
+    w.cap_tracks = (uint32_t)h->cfg.max_tracks;
+    w.cap_hits = (uint32_t)h->cfg.max_track_hits;
+    if (h->cfg.flags & VELO_CFG_CLUSTERS) {
+      w.cl_x = (float*)(base + a.clx);
+      w.cl_y = (float*)(base + a.cly);
+      w.cl_key = (uint32_t*)(base + a.clk);
+    }
+    w.cap_pixels = h->cfg.max_pixels;
+    e = cudaMemcpy(h->d_geo, &h->geo, sizeof(DevGeometry), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaMemcpy(geometry): %s", cudaGetErrorString(e)); break; }
+    e = cudaMallocHost(&h->h_totals, 4 * sizeof(uint32_t));
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)); h->h_totals = nullptr; break; }
+  } while (0);
+  if (rc != VELO_OK) {
+    velo_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return VELO_OK;
+}
+
+void velo_destroy(velo_handle* h) {
+  if (!h) return;
+  if (h->arena) cudaFree(h->arena);
+  if (h->stage) cudaFree(h->stage);
+  if (h->h_totals) cudaFreeHost(h->h_totals);
+  delete h;
+}
+
+int velo_set_params(velo_handle* h, const velo_params* params) {
+  if (!h) return fail(VELO_ERR_INPUT, "velo_set_params: null handle");
+  if (!params_ok(params)) return fail(VELO_ERR_INPUT, "velo_set_params: invalid parameters");
+  h->par = to_dev(*params);
+  return VELO_OK;
+}
+
+int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_output* out, void* stream) {
+  if (!h || !events || !out) return fail(VELO_ERR_INPUT, "velo_reconstruct: null argument");
+  const uint32_t E = events->n_events;
+  if (E > h->cfg.max_events)
+    return fail(VELO_ERR_NOMEM, "velo_reconstruct: %u events exceed the handle's max_events %u", E, h->cfg.max_events);
+  if (!events->sensor_off || (E && (!events->col || !events->row)))
+    return fail(VELO_ERR_INPUT, "velo_reconstruct: null event arrays");
+  if (!out->track_off || !out->hit_off || !out->hit_ids || !out->states || !out->ndof || !out->event_status ||
+      !out->totals)
+    return fail(VELO_ERR_INPUT, "velo_reconstruct: null output arrays");
+  const bool want_clusters = out->cluster_off != nullptr;
+  if (want_clusters && (!out->cl_x || !out->cl_y || !out->cl_key))
+    return fail(VELO_ERR_INPUT, "velo_reconstruct: incomplete cluster outputs");
+  if (want_clusters && !(h->cfg.flags & VELO_CFG_CLUSTERS))
+    return fail(VELO_ERR_STATE, "velo_reconstruct: handle created without VELO_CFG_CLUSTERS");
+  cudaStream_t st = (cudaStream_t)stream;
+  EventsView ev{E, events->sensor_off, events->col, events->row};
+  WorkView wk = h->wk;
+  if (!want_clusters) {
+    wk.cl_x = nullptr;
+    wk.cl_y = nullptr;
+    wk.cl_key = nullptr;
+  }
+  CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
+  CUDA_TRY(launch_prep(ev, wk, h->caps[0], h->geo.n_sensors, h->cfg.max_pixels, st));
+  if (E) {
+    CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[0], 0, h->threads[0], h->ctas[0], st));
+    CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[1], 1, h->threads[1], h->ctas[1], st));
+  }
+  CUDA_TRY(launch_scan(E, wk, *out, st));
+  CUDA_TRY(launch_emit(E, wk, *out, st));
+  CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  return VELO_OK;
+}
+
+int velo_sync_status(velo_handle* h, void* stream) {
+  if (!h) return fail(VELO_ERR_INPUT, "velo_sync_status: null handle");
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  const uint32_t err = h->h_totals[0];
+  h->last_error_bits = err;
+  if (err & kErrTimeout) return fail(VELO_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (err & kErrCapacity) return fail(VELO_ERR_CAPACITY, "an output or per-event capacity was exceeded");
+  if (err & kErrInput) return fail(VELO_ERR_INPUT, "some events had bad pixels or offsets");
+  return VELO_OK;
+}
+
+int velo_reconstruct_host(velo_handle* h, uint32_t n_events, const uint32_t* sensor_off_host,
+                          const uint16_t* col_host, const uint16_t* row_host, const velo_output* out_host,
+                          void* stream) {
+  if (!h || !sensor_off_host || !out_host) return fail(VELO_ERR_INPUT, "velo_reconstruct_host: null argument");
+  if (n_events > h->cfg.max_events) return fail(VELO_ERR_NOMEM, "velo_reconstruct_host: too many events");
+  const uint32_t ns = (uint32_t)h->geo.n_sensors;
+  const size_t n_off = (size_t)n_events * ns + 1;
+  const uint64_t p0 = sensor_off_host[0], p1 = sensor_off_host[n_off - 1];
+  if (p1 < p0) return fail(VELO_ERR_INPUT, "velo_reconstruct_host: decreasing offsets");
+  const uint64_t P = p1;  // pixel arrays are indexed from 0
+  if (P > h->cfg.max_pixels) return fail(VELO_ERR_NOMEM, "velo_reconstruct_host: too many pixels");
+  const velo_config& c = h->cfg;
+  const bool clusters = out_host->cluster_off != nullptr;
+  // staging layout: inputs, then outputs at the handle's capacities
+  size_t o = 0;
+  const size_t s_off = o; o = align256(o + 4 * n_off);
+  const size_t s_col = o; o = align256(o + 2 * P);
+  const size_t s_row = o; o = align256(o + 2 * P);
+  const size_t s_toff = o; o = align256(o + 4ull * (c.max_events + 1));
+  const size_t s_hoff = o; o = align256(o + 4ull * (c.max_tracks + 1));
+  const size_t s_hids = o; o = align256(o + 4ull * c.max_track_hits);
+  const size_t s_st = o; o = align256(o + 4ull * VELO_NSTATE * c.max_tracks);
+  const size_t s_ndof = o; o = align256(o + c.max_tracks);
+  const size_t s_evs = o; o = align256(o + 4ull * c.max_events);
+  const size_t s_tot = o; o = align256(o + 16);
+  size_t s_coff = 0, s_cx = 0, s_cy = 0, s_ck = 0;
+  if (clusters) {
+    s_coff = o; o = align256(o + 4ull * (c.max_events + 1));
+    s_cx = o; o = align256(o + 4ull * c.max_pixels);
+    s_cy = o; o = align256(o + 4ull * c.max_pixels);
+    s_ck = o; o = align256(o + 4ull * c.max_pixels);
+  }
+  if (o > h->stage_bytes) {
+    if (h->stage) cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&h->stage, o);
+    if (e != cudaSuccess) { h->stage = nullptr; return fail(VELO_ERR_NOMEM, "staging cudaMalloc: %s", cudaGetErrorString(e)); }
+    h->stage_bytes = o;
+  }
+  char* b = (char*)h->stage;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemcpyAsync(b + s_off, sensor_off_host, 4 * n_off, cudaMemcpyHostToDevice, st));
+  if (P) {
+    CUDA_TRY(cudaMemcpyAsync(b + s_col, col_host, 2 * P, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(b + s_row, row_host, 2 * P, cudaMemcpyHostToDevice, st));
+  }
+  velo_events ev{n_events, (const uint32_t*)(b + s_off), (const uint16_t*)(b + s_col), (const uint16_t*)(b + s_row)};
+  velo_output od{};
+  od.cap_tracks = (uint32_t)c.max_tracks;
+  od.cap_hits = (uint32_t)c.max_track_hits;
+  od.cap_clusters = (uint32_t)(c.max_pixels > 0xFFFFFFFFull ? 0xFFFFFFFFull : c.max_pixels);
+  od.track_off = (uint32_t*)(b + s_toff);
+  od.hit_off = (uint32_t*)(b + s_hoff);
+  od.hit_ids = (uint32_t*)(b + s_hids);
+  od.states = (float*)(b + s_st);
+  od.ndof = (uint8_t*)(b + s_ndof);
+  od.event_status = (uint32_t*)(b + s_evs);
+  od.totals = (uint32_t*)(b + s_tot);
+  if (clusters) {
+    od.cluster_off = (uint32_t*)(b + s_coff);
+    od.cl_x = (float*)(b + s_cx);
+    od.cl_y = (float*)(b + s_cy);
+    od.cl_key = (uint32_t*)(b + s_ck);
+  }
+  int rc = velo_reconstruct(h, &ev, &od, stream);
+  if (rc != VELO_OK) return rc;
+  uint32_t tot[4];
+  CUDA_TRY(cudaMemcpyAsync(tot, od.totals, sizeof(tot), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  const uint32_t nt = tot[0], nh = tot[1], nc = tot[2];
+  memcpy(out_host->totals, tot, sizeof(tot));
+  if (nt > out_host->cap_tracks || nh > out_host->cap_hits || (clusters && nc > out_host->cap_clusters) ||
+      nt > od.cap_tracks || nh > od.cap_hits) {
+    CUDA_TRY(cudaMemcpyAsync(out_host->event_status, od.event_status, 4ull * n_events, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return fail(VELO_ERR_CAPACITY, "velo_reconstruct_host: outputs need %u tracks, %u hits, %u clusters", nt, nh, nc);
+  }
+  CUDA_TRY(cudaMemcpyAsync(out_host->track_off, od.track_off, 4ull * (n_events + 1), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaMemcpyAsync(out_host->hit_off, od.hit_off, 4ull * (nt + 1), cudaMemcpyDeviceToHost, st));
+  if (nh) CUDA_TRY(cudaMemcpyAsync(out_host->hit_ids, od.hit_ids, 4ull * nh, cudaMemcpyDeviceToHost, st));
+  if (nt) {
+    CUDA_TRY(cudaMemcpy2DAsync(out_host->states, 4ull * out_host->cap_tracks, od.states, 4ull * od.cap_tracks,
+                               4ull * nt, VELO_NSTATE, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(out_host->ndof, od.ndof, nt, cudaMemcpyDeviceToHost, st));
+  }
+  CUDA_TRY(cudaMemcpyAsync(out_host->event_status, od.event_status, 4ull * n_events, cudaMemcpyDeviceToHost, st));
+  if (clusters) {
+    CUDA_TRY(cudaMemcpyAsync(out_host->cluster_off, od.cluster_off, 4ull * (n_events + 1), cudaMemcpyDeviceToHost, st));
+    if (nc) {
+      CUDA_TRY(cudaMemcpyAsync(out_host->cl_x, od.cl_x, 4ull * nc, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaMemcpyAsync(out_host->cl_y, od.cl_y, 4ull * nc, cudaMemcpyDeviceToHost, st));
+      CUDA_TRY(cudaMemcpyAsync(out_host->cl_key, od.cl_key, 4ull * nc, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  h->last_error_bits = tot[3];
+  if (tot[3] & kErrCapacity) return fail(VELO_ERR_CAPACITY, "a per-event capacity was exceeded");
+  if (tot[3] & kErrInput) return fail(VELO_ERR_INPUT, "some events had bad pixels or offsets");
+  return VELO_OK;
+}
+
+}  // extern "C"

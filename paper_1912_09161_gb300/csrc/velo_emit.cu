@@ -1,0 +1,167 @@
+// Batch-level kernels around the per-event reconstruction:
+//   prep  -- validates each event's sensor offsets and queues it for the
+//            kernel class whose shared-memory plan holds its pixels;
+//   scan  -- exclusive scan of the per-event track / hit / cluster counts;
+//   emit  -- copies every event's results from scratch to the caller's
+//            compact, canonically ordered output arrays.
+// Only the raw input goes in and only tracks, states (and optionally
+// clusters) come out (paper section 2.2: raw data in, selected objects out).
+#include <stdint.h>
+
+#include "velo_internal.cuh"
+
+namespace velo {
+
+// One warp per event: offsets must not decrease; pixels must fit the
+// working storage; events are queued by size class.
+__global__ void prep_kernel(EventsView ev, WorkView wk, uint32_t maxp_small, int ns, uint64_t cap_pixels) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ev.n_events; e += warps) {
+    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
+    bool bad = false;
+    for (int s = lane; s < ns; s += 32) bad |= so[s + 1] < so[s];
+    bad = __any_sync(0xFFFFFFFFu, bad);
+    if (lane == 0) {
+      const uint32_t p0 = so[0], p1 = so[ns];
+      if (!bad && p1 > cap_pixels) bad = true;
+      if (bad) {
+        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_BAD_OFFSETS, 0, 0, p0, 0};
+        atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+      } else {
+        const int cls = (p1 - p0) > maxp_small ? 1 : 0;
+        const uint32_t pos = atomicAdd(&wk.cnt->queue_len[cls], 1u);
+        wk.queue[cls][pos] = e;
+      }
+    }
+  }
+}
+
+cudaError_t launch_prep(const EventsView& ev, const WorkView& wk, const Caps& small, int n_sensors,
+                        uint64_t cap_pixels, cudaStream_t st) {
+  if (ev.n_events == 0) return cudaSuccess;
+  const int threads = 256;
+  int blocks = (int)((ev.n_events * 32ull + threads - 1) / threads);
+  if (blocks > 4096) blocks = 4096;
+  prep_kernel<<<blocks, threads, 0, st>>>(ev, wk, small.maxp, n_sensors, cap_pixels);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// scan: one block; each thread scans a contiguous run of events
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ void warp_scan3(uint32_t& a, uint32_t& b, uint32_t& c) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t na = __shfl_up_sync(0xFFFFFFFFu, a, o);
+    uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, b, o);
+    uint32_t nc = __shfl_up_sync(0xFFFFFFFFu, c, o);
+    if (lane >= o) { a += na; b += nb; c += nc; }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t n_events, WorkView wk, velo_output out) {
+  __shared__ uint32_t s_w[3][kScanThreads / 32];
+  const uint32_t tid = threadIdx.x;
+  const uint32_t per = (n_events + kScanThreads - 1) / kScanThreads;
+  const uint32_t b = tid * per, e = min(n_events, b + per);
+  uint32_t st = 0, sh = 0, sc = 0;
+  for (uint32_t i = b; i < e; ++i) {
+    const EventRec r = wk.rec[i];
+    st += r.n_tracks; sh += r.n_hits; sc += r.n_clusters;
+  }
+  uint32_t it = st, ih = sh, ic = sc;
+  warp_scan3(it, ih, ic);
+  if ((tid & 31) == 31) { s_w[0][tid >> 5] = it; s_w[1][tid >> 5] = ih; s_w[2][tid >> 5] = ic; }
+  __syncthreads();
+  if (tid < 32) {
+    uint32_t a = s_w[0][tid], bb = s_w[1][tid], c = s_w[2][tid];
+    warp_scan3(a, bb, c);
+    s_w[0][tid] = a; s_w[1][tid] = bb; s_w[2][tid] = c;
+  }
+  __syncthreads();
+  const uint32_t w = tid >> 5;
+  uint32_t bt = (w ? s_w[0][w - 1] : 0u) + it - st;
+  uint32_t bh = (w ? s_w[1][w - 1] : 0u) + ih - sh;
+  uint32_t bc = (w ? s_w[2][w - 1] : 0u) + ic - sc;
+  for (uint32_t i = b; i < e; ++i) {
+    EventRec r = wk.rec[i];
+    out.track_off[i] = bt;
+    if (out.cluster_off) out.cluster_off[i] = bc;
+    r.pad = bh;  // output hit base of the event
+    wk.rec[i].pad = bh;
+    bt += r.n_tracks; bh += r.n_hits; bc += r.n_clusters;
+  }
+  if (tid == kScanThreads - 1) {
+    const uint32_t tt = s_w[0][31], th = s_w[1][31], tc = s_w[2][31];
+    out.track_off[n_events] = tt;
+    if (out.cluster_off) out.cluster_off[n_events] = tc;
+    if (tt <= out.cap_tracks) out.hit_off[tt] = th <= out.cap_hits ? th : 0u;
+    uint32_t err = wk.cnt->error;
+    if (tt > out.cap_tracks || th > out.cap_hits || (out.cluster_off && tc > out.cap_clusters)) {
+      err |= kErrCapacity;
+      atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+    }
+    out.totals[0] = tt;
+    out.totals[1] = th;
+    out.totals[2] = tc;
+    out.totals[3] = err;
+  }
+}
+
+cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st) {
+  scan_kernel<<<1, kScanThreads, 0, st>>>(n_events, wk, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// emit: one block per event (grid-stride)
+// ---------------------------------------------------------------------------
+__global__ void emit_kernel(uint32_t n_events, WorkView wk, velo_output out) {
+  for (uint32_t e = blockIdx.x; e < n_events; e += gridDim.x) {
+    const EventRec r = wk.rec[e];
+    const uint32_t o0 = out.track_off[e], h0 = r.pad;
+    uint32_t status = r.status;
+    const bool fits = (uint64_t)o0 + r.n_tracks <= out.cap_tracks && (uint64_t)h0 + r.n_hits <= out.cap_hits;
+    if (fits) {
+      const size_t scap = wk.cap_tracks, ocap = out.cap_tracks;
+      for (uint32_t j = 0; j < VELO_NSTATE; ++j)
+        for (uint32_t k = threadIdx.x; k < r.n_tracks; k += blockDim.x)
+          out.states[j * ocap + o0 + k] = wk.tr_state[j * scap + r.track_base + k];
+      for (uint32_t k = threadIdx.x; k < r.n_tracks; k += blockDim.x) {
+        const uint32_t nh = wk.tr_nhits[r.track_base + k];
+        out.ndof[o0 + k] = (uint8_t)(2 * nh - 4);
+        out.hit_off[o0 + k] = h0 + wk.tr_hitoff[r.track_base + k];
+      }
+      for (uint32_t k = threadIdx.x; k < r.n_hits; k += blockDim.x)
+        out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k];
+    } else if (r.n_tracks) {
+      status |= VELO_EV_TRUNCATED;
+    }
+    if (out.cluster_off && wk.cl_x) {
+      const uint32_t c0 = out.cluster_off[e];
+      if ((uint64_t)c0 + r.n_clusters <= out.cap_clusters) {
+        for (uint32_t k = threadIdx.x; k < r.n_clusters; k += blockDim.x) {
+          out.cl_x[c0 + k] = wk.cl_x[r.pix_base + k];
+          out.cl_y[c0 + k] = wk.cl_y[r.pix_base + k];
+          out.cl_key[c0 + k] = wk.cl_key[r.pix_base + k];
+        }
+      } else if (r.n_clusters) {
+        status |= VELO_EV_TRUNCATED;
+      }
+    }
+    if (threadIdx.x == 0) out.event_status[e] = status;
+  }
+}
+
+cudaError_t launch_emit(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st) {
+  if (n_events == 0) return cudaSuccess;
+  int blocks = (int)(n_events < 152u * 16u ? n_events : 152u * 16u);
+  emit_kernel<<<blocks, 128, 0, st>>>(n_events, wk, out);
+  return cudaGetLastError();
+}
+
+}  // namespace velo

@@ -1,0 +1,109 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "velo.h"
+
+namespace velo {
+
+constexpr int kMaxModules = 64;
+constexpr int kSPM = 4;                          // sensors per module
+constexpr int kMaxSensors = kMaxModules * kSPM;  // 256
+constexpr int kNB = 32;                          // phi bins per module
+constexpr uint32_t kNone16 = 0xFFFFu;
+constexpr int kMlpIn = 10, kMlpH = 32;
+constexpr int kMlpParams = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1441
+
+// Device copy of the geometry (in the handle's arena).
+struct DevGeometry {
+  int n_modules, n_sensors, n_cols, n_rows;
+  float pitch;
+  float module_z[kMaxModules];
+  float ox[kMaxSensors], oy[kMaxSensors];
+  float cdx[kMaxSensors], cdy[kMaxSensors], rdx[kMaxSensors], rdy[kMaxSensors];
+};
+
+// Parameters passed by value to the kernels.
+struct DevParams {
+  float max_slope, tan_phi_tol, max_scatter_seed, max_scatter_fwd, max_scatter_3hit;
+  uint32_t max_skipped;
+  float sigma_meas, pt_nominal, ms_coeff;
+  uint32_t use_mlp;
+  float mlp_threshold;
+  float phi_window;  // half-width of the phi window in pseudo-angle units (>= atan(tol))
+};
+
+// Per-event working capacities of one kernel class (shared memory plan).
+struct Caps {
+  uint32_t maxp;   // pixels (also provisional hit slots)
+  uint32_t maxt;   // tracks
+  uint32_t maxch;  // hit-chain entries
+  uint32_t smem;   // bytes of dynamic shared memory
+};
+
+// Per-event record written by the reconstruction kernel.
+struct EventRec {
+  uint32_t n_tracks, n_hits, n_clusters, status;
+  uint32_t track_base, hit_base, pix_base, pad;
+};
+
+// Handle-level error bits (device word).
+enum : uint32_t {
+  kErrInput = 1u,
+  kErrCapacity = 2u,
+  kErrTimeout = 4u,
+};
+
+// Device counters, reset before every batch.
+struct Counters {
+  uint32_t ticket[2];      // persistent-kernel tickets per class
+  uint32_t queue_len[2];   // events in each class queue
+  uint32_t track_cursor;   // scratch bump allocators
+  uint32_t hit_cursor;
+  uint32_t error;          // kErr* bits
+  uint32_t pad[9];
+};
+
+// Device views.
+struct EventsView {
+  uint32_t n_events;
+  const uint32_t* sensor_off;
+  const uint16_t* col;
+  const uint16_t* row;
+};
+
+struct WorkView {
+  Counters* cnt;
+  EventRec* rec;           // [max_events]
+  uint32_t* queue[2];      // [max_events] each
+  // scratch tracks (SoA), bump-allocated per event
+  float* tr_state;         // [VELO_NSTATE][cap_tracks]
+  uint16_t* tr_nhits;      // [cap_tracks]
+  uint32_t* tr_hitoff;     // [cap_tracks] offset of the first hit, relative to the event's hit base
+  uint32_t* tr_hits;       // [cap_hits] event-local canonical ids
+  uint32_t cap_tracks, cap_hits;
+  // scratch clusters (indexed by global pixel position), may be null
+  float* cl_x;
+  float* cl_y;
+  uint32_t* cl_key;
+  uint64_t cap_pixels;
+  // classifier weights (bf16 bits) and feature normalisation, may be null
+  const uint16_t* mlp_w;
+  const float* mlp_norm;   // [2 * kMlpIn] mean, inverse std
+};
+
+// Kernel launchers (velo_reco.cu / velo_emit.cu).
+Caps make_caps(uint32_t smem_budget, uint32_t n_modules, uint32_t n_threads);
+cudaError_t launch_prep(const EventsView& ev, const WorkView& wk, const Caps& small, int n_sensors,
+                        uint64_t cap_pixels, cudaStream_t st);
+cudaError_t launch_reco(const DevGeometry* geo, const DevParams& par, const EventsView& ev,
+                        const WorkView& wk, const Caps& caps, int cls, int n_threads, int n_ctas,
+                        cudaStream_t st);
+cudaError_t reco_set_smem_limit(int n_threads, int bytes);
+cudaError_t reco_occupancy(int n_threads, int smem, int* blocks_per_sm);
+cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
+cudaError_t launch_emit(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
+
+}  // namespace velo

@@ -1,0 +1,361 @@
+"""ctypes binding of the C ABI in ``include/velo.h`` (argument marshalling only).
+
+Every step of the reconstruction runs in the CUDA library
+``libvelo_gb300.so``; this module only lays out the C structs, passes device
+pointers of torch tensors (torch provides device memory and streams) and turns
+status codes into exceptions.  There is no CPU fallback: if the library is
+missing or fails to load, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+
+import numpy as np
+
+from . import _build
+
+NSTATE = 13
+STATE_NAMES = ("x", "y", "z", "tx", "ty", "c00", "c20", "c22", "c11", "c31", "c33", "chi2", "score")
+
+VELO_OK, VELO_ERR_INPUT, VELO_ERR_CAPACITY, VELO_ERR_NOMEM, VELO_ERR_TIMEOUT, VELO_ERR_CUDA, VELO_ERR_STATE = range(7)
+EV_BAD_PIXEL, EV_BAD_OFFSETS, EV_OVERFLOW, EV_TRUNCATED = 1, 2, 4, 8
+CFG_CLUSTERS = 1
+
+EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
+            "velo_sync_status", "velo_reconstruct_host", "velo_last_error", "velo_version")
+
+
+class VeloError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class velo_geometry(ctypes.Structure):
+    _fields_ = [("n_modules", ctypes.c_uint32), ("sensors_per_module", ctypes.c_uint32),
+                ("n_cols", ctypes.c_uint32), ("n_rows", ctypes.c_uint32), ("pitch", ctypes.c_float),
+                ("module_z", ctypes.c_void_p), ("sensor_ox", ctypes.c_void_p), ("sensor_oy", ctypes.c_void_p),
+                ("col_dx", ctypes.c_void_p), ("col_dy", ctypes.c_void_p),
+                ("row_dx", ctypes.c_void_p), ("row_dy", ctypes.c_void_p)]
+
+
+class velo_params(ctypes.Structure):
+    _fields_ = [("max_slope", ctypes.c_float), ("tan_phi_tol", ctypes.c_float),
+                ("max_scatter_seed", ctypes.c_float), ("max_scatter_fwd", ctypes.c_float),
+                ("max_scatter_3hit", ctypes.c_float), ("max_skipped", ctypes.c_uint32),
+                ("sigma_meas", ctypes.c_float), ("pt_nominal", ctypes.c_float),
+                ("ms_coeff", ctypes.c_float), ("use_mlp", ctypes.c_uint32),
+                ("mlp_threshold", ctypes.c_float)]
+
+
+class velo_config(ctypes.Structure):
+    _fields_ = [("max_events", ctypes.c_uint32), ("max_pixels", ctypes.c_uint64),
+                ("max_tracks", ctypes.c_uint64), ("max_track_hits", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("n_slots", ctypes.c_uint32)]
+
+
+class velo_events(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint32), ("sensor_off", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("row", ctypes.c_void_p)]
+
+
+class velo_output(ctypes.Structure):
+    _fields_ = [("cap_tracks", ctypes.c_uint32), ("cap_hits", ctypes.c_uint32),
+                ("cap_clusters", ctypes.c_uint32), ("track_off", ctypes.c_void_p),
+                ("hit_off", ctypes.c_void_p), ("hit_ids", ctypes.c_void_p), ("states", ctypes.c_void_p),
+                ("ndof", ctypes.c_void_p), ("event_status", ctypes.c_void_p), ("totals", ctypes.c_void_p),
+                ("cluster_off", ctypes.c_void_p), ("cl_x", ctypes.c_void_p), ("cl_y", ctypes.c_void_p),
+                ("cl_key", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(build: bool = True) -> ctypes.CDLL:
+    """Loads (building first if needed) the CUDA library; raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"VELO CUDA library not built: {_build.LIB}")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    lib.velo_create.argtypes = [P(velo_geometry), P(velo_params), P(velo_config), P(vp)]
+    lib.velo_destroy.argtypes = [vp]
+    lib.velo_destroy.restype = None
+    lib.velo_required_bytes.argtypes = [P(velo_geometry), P(velo_config), P(ctypes.c_size_t)]
+    lib.velo_set_params.argtypes = [vp, P(velo_params)]
+    lib.velo_reconstruct.argtypes = [vp, P(velo_events), P(velo_output), vp]
+    lib.velo_sync_status.argtypes = [vp, vp]
+    lib.velo_reconstruct_host.argtypes = [vp, ctypes.c_uint32, vp, vp, vp, P(velo_output), vp]
+    lib.velo_last_error.restype = ctypes.c_char_p
+    lib.velo_version.restype = ctypes.c_char_p
+    for name in ("velo_create", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
+                 "velo_sync_status", "velo_reconstruct_host"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != VELO_OK:
+        msg = load_library(False).velo_last_error().decode(errors="replace")
+        raise VeloError(rc, f"{what}: {msg}")
+
+
+@dataclasses.dataclass
+class Params:
+    """Method parameters (mm, GeV); the defaults are the frozen readings."""
+    max_slope: float = 0.4
+    tan_phi_tol: float = math.tan(0.05)
+    max_scatter_seed: float = 0.1
+    max_scatter_fwd: float = 0.1
+    max_scatter_3hit: float = 0.02
+    max_skipped: int = 1
+    sigma_meas: float = 0.055 / math.sqrt(12.0)
+    pt_nominal: float = 0.4
+    ms_coeff: float = 1.0
+    use_mlp: int = 0
+    mlp_threshold: float = 0.5
+
+    def to_c(self) -> velo_params:
+        p = velo_params()
+        for name, _ in velo_params._fields_:
+            setattr(p, name, getattr(self, name))
+        return p
+
+
+def _geometry_c(g):
+    keep = [np.ascontiguousarray(g.module_z, np.float32), np.ascontiguousarray(g.sensor_ox, np.float32),
+            np.ascontiguousarray(g.sensor_oy, np.float32), np.ascontiguousarray(g.col_dx, np.int8),
+            np.ascontiguousarray(g.col_dy, np.int8), np.ascontiguousarray(g.row_dx, np.int8),
+            np.ascontiguousarray(g.row_dy, np.int8)]
+    c = velo_geometry(g.n_modules, g.sensors_per_module, g.n_cols, g.n_rows, g.pitch,
+                      *[a.ctypes.data for a in keep])
+    return c, keep
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+@dataclasses.dataclass
+class DeviceEvents:
+    """Raw pixels of a batch resident on the device (torch tensors)."""
+    n_events: int
+    sensor_off: object   # int32 view of uint32 [n_events * n_sensors + 1]
+    col: object          # int16 view of uint16 [n_pixels]
+    row: object
+
+    def to_c(self) -> velo_events:
+        return velo_events(self.n_events, _ptr(self.sensor_off), _ptr(self.col), _ptr(self.row))
+
+    @property
+    def nbytes(self) -> int:
+        return sum(int(t.numel() * t.element_size()) for t in (self.sensor_off, self.col, self.row))
+
+
+def upload_events(events, device="cuda") -> DeviceEvents:
+    """Copies a ``velo_synth.SynthEvents``-like batch (numpy) to the device."""
+    import torch
+    so = torch.from_numpy(np.ascontiguousarray(events.sensor_off, np.uint32).view(np.int32)).to(device)
+    col = torch.from_numpy(np.ascontiguousarray(events.col, np.uint16).view(np.int16)).to(device)
+    row = torch.from_numpy(np.ascontiguousarray(events.row, np.uint16).view(np.int16)).to(device)
+    return DeviceEvents(int(events.n_events), so, col, row)
+
+
+@dataclasses.dataclass
+class DeviceOutput:
+    """Caller-owned output buffers on the device (torch tensors)."""
+    cap_tracks: int
+    cap_hits: int
+    cap_clusters: int
+    track_off: object
+    hit_off: object
+    hit_ids: object
+    states: object
+    ndof: object
+    event_status: object
+    totals: object
+    cluster_off: object = None
+    cl_x: object = None
+    cl_y: object = None
+    cl_key: object = None
+
+    def to_c(self) -> velo_output:
+        return velo_output(self.cap_tracks, self.cap_hits, self.cap_clusters, _ptr(self.track_off),
+                           _ptr(self.hit_off), _ptr(self.hit_ids), _ptr(self.states), _ptr(self.ndof),
+                           _ptr(self.event_status), _ptr(self.totals), _ptr(self.cluster_off),
+                           _ptr(self.cl_x), _ptr(self.cl_y), _ptr(self.cl_key))
+
+    def to_host(self, n_events: int) -> "HostResult":
+        tot = self.totals.cpu().numpy().view(np.uint32)
+        nt, nh, nc = int(tot[0]), int(tot[1]), int(tot[2])
+        nt_c, nh_c = min(nt, self.cap_tracks), min(nh, self.cap_hits)
+        res = HostResult(
+            n_events=n_events, totals=tot.copy(),
+            track_off=self.track_off[: n_events + 1].cpu().numpy().view(np.uint32).copy(),
+            hit_off=self.hit_off[: nt_c + 1].cpu().numpy().view(np.uint32).copy(),
+            hit_ids=self.hit_ids[:nh_c].cpu().numpy().view(np.uint32).copy(),
+            states=self.states[:, :nt_c].cpu().numpy().T.copy(),
+            ndof=self.ndof[:nt_c].cpu().numpy().copy(),
+            event_status=self.event_status[:n_events].cpu().numpy().view(np.uint32).copy())
+        if self.cluster_off is not None:
+            nc_c = min(nc, self.cap_clusters)
+            res.cluster_off = self.cluster_off[: n_events + 1].cpu().numpy().view(np.uint32).copy()
+            res.cl_x = self.cl_x[:nc_c].cpu().numpy().copy()
+            res.cl_y = self.cl_y[:nc_c].cpu().numpy().copy()
+            res.cl_key = self.cl_key[:nc_c].cpu().numpy().view(np.uint32).copy()
+        return res
+
+
+@dataclasses.dataclass
+class HostResult:
+    n_events: int
+    totals: np.ndarray
+    track_off: np.ndarray
+    hit_off: np.ndarray
+    hit_ids: np.ndarray
+    states: np.ndarray       # float32 [n_tracks, 13]
+    ndof: np.ndarray
+    event_status: np.ndarray
+    cluster_off: np.ndarray | None = None
+    cl_x: np.ndarray | None = None
+    cl_y: np.ndarray | None = None
+    cl_key: np.ndarray | None = None
+
+    @property
+    def n_tracks(self) -> int:
+        return int(self.track_off[-1])
+
+    def track_hits(self, t: int) -> np.ndarray:
+        return self.hit_ids[self.hit_off[t]:self.hit_off[t + 1]]
+
+    def event_tracks(self, e: int) -> list[tuple[int, ...]]:
+        return [tuple(int(h) for h in self.track_hits(t))
+                for t in range(int(self.track_off[e]), int(self.track_off[e + 1]))]
+
+
+def alloc_output(n_events: int, cap_tracks: int, cap_hits: int, cap_clusters: int = 0,
+                 device="cuda") -> DeviceOutput:
+    import torch
+    i32 = dict(dtype=torch.int32, device=device)
+    out = DeviceOutput(
+        cap_tracks, cap_hits, cap_clusters,
+        track_off=torch.zeros(n_events + 1, **i32), hit_off=torch.zeros(cap_tracks + 1, **i32),
+        hit_ids=torch.zeros(max(cap_hits, 1), **i32),
+        states=torch.zeros((NSTATE, max(cap_tracks, 1)), dtype=torch.float32, device=device),
+        ndof=torch.zeros(max(cap_tracks, 1), dtype=torch.uint8, device=device),
+        event_status=torch.zeros(max(n_events, 1), **i32), totals=torch.zeros(4, **i32))
+    if cap_clusters:
+        out.cluster_off = torch.zeros(n_events + 1, **i32)
+        out.cl_x = torch.zeros(cap_clusters, dtype=torch.float32, device=device)
+        out.cl_y = torch.zeros(cap_clusters, dtype=torch.float32, device=device)
+        out.cl_key = torch.zeros(cap_clusters, **i32)
+    return out
+
+
+def suggested_caps(n_events: int, n_pixels: int) -> tuple[int, int, int]:
+    """Output capacities that hold nominal-occupancy batches with margin."""
+    cap_tracks = n_pixels // 16 + 1024
+    return cap_tracks, cap_tracks * 16, n_pixels + 1024
+
+
+# --- thin functions with the C names ------------------------------------------------
+def velo_create(geometry, params: Params, config: velo_config):
+    lib = load_library()
+    gc, keep = _geometry_c(geometry)
+    h = ctypes.c_void_p()
+    _check(lib.velo_create(ctypes.byref(gc), ctypes.byref(params.to_c()), ctypes.byref(config),
+                           ctypes.byref(h)), "velo_create")
+    del keep
+    return h
+
+
+def velo_destroy(h):
+    load_library(False).velo_destroy(h)
+
+
+def velo_required_bytes(geometry, config: velo_config) -> int:
+    lib = load_library()
+    gc, keep = _geometry_c(geometry)
+    n = ctypes.c_size_t()
+    _check(lib.velo_required_bytes(ctypes.byref(gc), ctypes.byref(config), ctypes.byref(n)), "velo_required_bytes")
+    del keep
+    return int(n.value)
+
+
+def velo_set_params(h, params: Params):
+    _check(load_library(False).velo_set_params(h, ctypes.byref(params.to_c())), "velo_set_params")
+
+
+def velo_reconstruct(h, events: DeviceEvents, out: DeviceOutput, stream: int = 0):
+    ec, oc = events.to_c(), out.to_c()
+    _check(load_library(False).velo_reconstruct(h, ctypes.byref(ec), ctypes.byref(oc), ctypes.c_void_p(stream)),
+           "velo_reconstruct")
+
+
+def velo_sync_status(h, stream: int = 0) -> int:
+    return int(load_library(False).velo_sync_status(h, ctypes.c_void_p(stream)))
+
+
+def velo_reconstruct_host(h, n_events: int, sensor_off: np.ndarray, col: np.ndarray, row: np.ndarray,
+                          out_c: velo_output, stream: int = 0) -> int:
+    return int(load_library(False).velo_reconstruct_host(
+        h, n_events, sensor_off.ctypes.data, col.ctypes.data, row.ctypes.data, ctypes.byref(out_c),
+        ctypes.c_void_p(stream)))
+
+
+def velo_version() -> str:
+    return load_library().velo_version().decode()
+
+
+class Reconstructor:
+    """Owns a handle; convenience wrapper over the C entry points."""
+
+    def __init__(self, geometry, params: Params | None = None, max_events: int = 16384,
+                 max_pixels: int | None = None, max_tracks: int = 0, max_track_hits: int = 0,
+                 clusters: bool = False):
+        self.geometry = geometry
+        self.params = params or Params()
+        self.config = velo_config(max_events, max_pixels or max_events * 8192, max_tracks, max_track_hits,
+                                  CFG_CLUSTERS if clusters else 0, 0)
+        self.handle = velo_create(geometry, self.params, self.config)
+
+    def close(self):
+        if self.handle:
+            velo_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params: Params):
+        self.params = params
+        velo_set_params(self.handle, params)
+
+    def reconstruct(self, events: DeviceEvents, out: DeviceOutput, stream: int = 0):
+        velo_reconstruct(self.handle, events, out, stream)
+
+    def sync_status(self, stream: int = 0) -> int:
+        return velo_sync_status(self.handle, stream)
+
+    def run(self, events: DeviceEvents, clusters: bool = False, stream: int = 0, check: bool = True) -> HostResult:
+        """Reconstructs and copies the result to host numpy arrays."""
+        n_pix = int(events.col.numel())
+        ct, ch, cc = suggested_caps(events.n_events, n_pix)
+        out = alloc_output(events.n_events, ct, ch, cc if clusters else 0, device=events.col.device)
+        self.reconstruct(events, out, stream)
+        rc = self.sync_status(stream)
+        if check and rc not in (VELO_OK, VELO_ERR_INPUT):
+            _check(rc, "velo_sync_status")
+        return out.to_host(events.n_events)
