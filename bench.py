@@ -1,0 +1,324 @@
+#!/usr/bin/env python
+"""Throughput benchmark: VELO reconstruction of 10,000 nominal events on GB300.
+
+One step = one call of the library's ``velo_reconstruct`` over the whole
+batch (clustering, triplet seeding and following, cuts, fit, output
+compaction) with the raw pixels already resident in device memory.  Prints
+one JSON line (see the keys below).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: 10,000 synthetic events (seed 1; each rank r of a multi-GPU run
+takes seed 1 + 100 r, so per-GPU work is fixed: weak scaling).
+``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VELO events/sec on 1 GB300 (fraction of HBM roofline); p99 latency; ghost rate"
+UNIT = "events/s"
+N_EVENTS = 10_000
+WORKLOAD = "10,000 nominal VELO events (Poisson(7.6) pp vertices x Poisson(20) tracks, ~4.5k pixels/event), seed 1"
+REF_SAMPLE = 2000           # events per oracle step of the reference arm
+CPU_SAMPLE = 10000          # events of the CPU-baseline sample (the whole batch)
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "reco_kernel_nominal_10k.md")
+KERNELS_PER_STEP = 5        # prep, reconstruct (two size classes), scan, emit
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def _max_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _measured_peak_hbm() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _profile_traffic(kernel_src: str) -> float | None:
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (its sha256 prefix is recorded in the summary)."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
+    m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    return float(m_tr.group(1))
+
+
+def _algorithmic_bytes(stats: dict, n_sensors: int, cls: int) -> float:
+    """Bytes the reconstruction kernel must move for the events it processed:
+    raw pixels (col, row: 4 B each) and sensor offsets (4 B x (n_sensors + 1))
+    in; per track 13 state floats + hit count (2 B) + hit offset (4 B), and
+    4 B per track hit out."""
+    return (4.0 * stats["pixels"][cls] + 4.0 * (n_sensors + 1) * stats["events"][cls]
+            + 58.0 * stats["tracks"][cls] + 4.0 * stats["hits"][cls])
+
+
+def run_reference(args):
+    rank, ws, _, dist = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import velo_synth
+    geom = velo_synth.geometry()
+    ev = velo_synth.generate(velo_synth.config(1, n_events=REF_SAMPLE))
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.reconstruct(geom, ev, n_threads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.reconstruct(geom, ev, n_threads=cores)
+    dt = time.perf_counter() - t0
+    value = REF_SAMPLE * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "sample_events_per_step": REF_SAMPLE},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"first {REF_SAMPLE} events of the 10,000-event workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(geom, ev) -> dict:
+    import oracle
+    cores = os.cpu_count() or 1
+    sub = ev.subset(0, min(CPU_SAMPLE, ev.n_events))
+    t0 = time.perf_counter()
+    oracle.reconstruct(geom, sub, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n_events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sub.n_events} of the 10,000 events, all host cores ({dt:.1f} s)"}
+
+
+def run_ours(args):
+    import torch
+    import velo_synth
+    import paper_1912_09161_gb300 as V
+
+    rank, ws, local, dist = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    geom = velo_synth.geometry()
+    ev = velo_synth.generate(velo_synth.config(1, seed=1 + 100 * rank))
+    V.load_library()
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
+    d = V.upload_events(ev, dev)
+    ct, ch, cc = V.suggested_caps(ev.n_events, ev.n_pixels)
+    out = V.alloc_output(ev.n_events, ct, ch, 0, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    rec.set_timing(True)
+
+    for _ in range(args.warmup):
+        rec.reconstruct(d, out, sptr)
+    rc = rec.sync_status(sptr)
+    if rc != V.velo.VELO_OK:
+        raise SystemExit(f"velo_sync_status returned {rc}")
+
+    times, reco_ms, reco_bytes = [], [], []
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clocks:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            rec.reconstruct(d, out, sptr)
+            ends[k].record(stream)
+            st = rec.stats()
+            reco_ms.append(st["ms"][1])
+            reco_bytes.append(_algorithmic_bytes(st, geom.n_sensors, 0))
+        torch.cuda.synchronize(dev)
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    rc = rec.sync_status(sptr)
+    total_s = _max_over_ranks(sum(step_ms) / 1e3, dist)
+    value = ws * ev.n_events * args.steps / total_s
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = _e2e(V, rec, ev, dev, args, dist, ws)
+
+    desc = rec.describe()
+    peak, peak_kind = _measured_peak_hbm()
+    achieved = sum(reco_bytes) / (sum(reco_ms) / 1e3) / 1e9
+    traffic = _profile_traffic(os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", "velo_reco.cu"))
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_events": ev.n_events, "pixels_per_event": ev.n_pixels / ev.n_events,
+                   "l2": "flushed between steps (256 MiB device write, untimed); inputs 190 MB > L2",
+                   "parallelism": f"events sharded over {ws} GPU(s), no collective",
+                   "launch": desc, "status": rc},
+        "roofline": {"bound": "hbm", "kernel": "reco_kernel class 0 (two CTAs per SM)",
+                     "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel_ms_per_step": statistics.mean(reco_ms)},
+        "e2e": e2e,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clocks.summary(),
+    }
+    if ws == 1:
+        line["cpu_baseline"] = cpu_baseline(geom, ev)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _e2e(V, rec, ev, dev, args, dist, ws) -> dict:
+    import torch
+    ns = ev.n_sensors
+    so = torch.from_numpy(ev.sensor_off.view(np.int32)).pin_memory()
+    col = torch.from_numpy(ev.col.view(np.int16)).pin_memory()
+    row = torch.from_numpy(ev.row.view(np.int16)).pin_memory()
+    ct, ch, _ = V.suggested_caps(ev.n_events, ev.n_pixels)
+    host = V.alloc_output(ev.n_events, ct, ch, 0, device="cpu")
+    for name in ("track_off", "hit_off", "hit_ids", "states", "ndof", "event_status", "totals"):
+        setattr(host, name, getattr(host, name).pin_memory())
+    oc = host.to_c()
+    sptr = torch.cuda.current_stream(dev).cuda_stream
+    args_c = (rec.handle, ev.n_events, so.numpy(), col.numpy(), row.numpy(), oc, sptr)
+    for _ in range(max(1, args.warmup // 2)):
+        V.velo.velo_reconstruct_host(*args_c)
+    _barrier(dist)
+    t0 = time.perf_counter()
+    n = max(1, args.steps // 2)
+    for _ in range(n):
+        rc = V.velo.velo_reconstruct_host(*args_c)
+    dt = _max_over_ranks(time.perf_counter() - t0, dist)
+    tot = host.totals.numpy().view(np.uint32)
+    nt, nh = int(tot[0]), int(tot[1])
+    h2d = int(so.numel() * 4 + col.numel() * 2 + row.numel() * 2)
+    d2h = 4 * (ev.n_events + 1) + 4 * (nt + 1) + 4 * nh + 52 * nt + nt + 4 * ev.n_events + 16
+    return {"value": ws * ev.n_events * n / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "status": rc, "api": "velo_reconstruct_host (pinned host buffers)"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

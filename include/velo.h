@@ -176,6 +176,26 @@ int velo_reconstruct_host(velo_handle *h, uint32_t n_events, const uint32_t *sen
                           const uint16_t *col_host, const uint16_t *row_host,
                           const velo_output *out_host, void *stream);
 
+/* Per-call statistics (velo_get_stats).  Kernel class 0 runs events whose
+ * working set fits two CTAs per SM, class 1 the larger ones. */
+typedef struct velo_stats {
+  uint32_t events[2];   /* events reconstructed by each class */
+  uint32_t tracks[2];   /* tracks written by each class */
+  uint32_t hits[2];     /* track hits written by each class */
+  uint64_t pixels[2];   /* raw pixels read by each class */
+  float ms[5];          /* device time of prep, class 0, class 1, scan, emit */
+} velo_stats;
+
+/* Turns per-kernel timing (CUDA events on the call's stream) on or off. */
+int velo_set_timing(velo_handle *h, int on);
+
+/* Waits for the last call and returns its statistics; timing must be on. */
+int velo_get_stats(velo_handle *h, velo_stats *out);
+
+/* Writes a JSON description of the handle (per kernel class: threads, CTAs,
+ * shared memory, per-event capacities; arena bytes) into buf[0, n). */
+int velo_describe(const velo_handle *h, char *buf, size_t n);
+
 /* Thread-local message of the last failing call on this thread. */
 const char *velo_last_error(void);
 

@@ -56,6 +56,10 @@ struct velo_handle {
   size_t stage_bytes = 0;
   uint32_t* h_totals = nullptr;  // pinned
   uint32_t last_error_bits = 0;
+  // optional per-kernel timing of the last call
+  bool timing = false;
+  cudaEvent_t ev[6]{};
+  Counters* h_cnt = nullptr;  // pinned copy of the counters of the last call
 };
 
 namespace {
@@ -236,6 +240,13 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaMemcpy(geometry): %s", cudaGetErrorString(e)); break; }
     e = cudaMallocHost(&h->h_totals, 4 * sizeof(uint32_t));
     if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)); h->h_totals = nullptr; break; }
+    e = cudaMallocHost(&h->h_cnt, sizeof(Counters));
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMallocHost: %s", cudaGetErrorString(e)); h->h_cnt = nullptr; break; }
+    for (auto& ev : h->ev) {
+      e = cudaEventCreate(&ev);
+      if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); ev = nullptr; break; }
+    }
+    if (rc) break;
   } while (0);
   if (rc != VELO_OK) {
     velo_destroy(h);
@@ -247,10 +258,46 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
 
 void velo_destroy(velo_handle* h) {
   if (!h) return;
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->h_cnt) cudaFreeHost(h->h_cnt);
   if (h->arena) cudaFree(h->arena);
   if (h->stage) cudaFree(h->stage);
   if (h->h_totals) cudaFreeHost(h->h_totals);
   delete h;
+}
+
+int velo_describe(const velo_handle* h, char* buf, size_t n) {
+  if (!h || !buf || n == 0) return fail(VELO_ERR_INPUT, "velo_describe: null argument");
+  snprintf(buf, n,
+           "{\"sms\": %d, \"arena_bytes\": %zu, \"classes\": ["
+           "{\"threads\": %d, \"ctas\": %d, \"smem\": %u, \"max_pixels\": %u, \"max_tracks\": %u, \"max_chain\": %u}, "
+           "{\"threads\": %d, \"ctas\": %d, \"smem\": %u, \"max_pixels\": %u, \"max_tracks\": %u, \"max_chain\": %u}]}",
+           h->n_sm, h->arena_bytes, h->threads[0], h->ctas[0], h->caps[0].smem, h->caps[0].maxp, h->caps[0].maxt,
+           h->caps[0].maxch, h->threads[1], h->ctas[1], h->caps[1].smem, h->caps[1].maxp, h->caps[1].maxt,
+           h->caps[1].maxch);
+  return VELO_OK;
+}
+
+int velo_set_timing(velo_handle* h, int on) {
+  if (!h) return fail(VELO_ERR_INPUT, "velo_set_timing: null handle");
+  h->timing = on != 0;
+  return VELO_OK;
+}
+
+int velo_get_stats(velo_handle* h, velo_stats* out) {
+  if (!h || !out) return fail(VELO_ERR_INPUT, "velo_get_stats: null argument");
+  if (!h->timing) return fail(VELO_ERR_STATE, "velo_get_stats: timing is off (velo_set_timing)");
+  CUDA_TRY(cudaEventSynchronize(h->ev[5]));
+  for (int k = 0; k < 5; ++k) CUDA_TRY(cudaEventElapsedTime(&out->ms[k], h->ev[k], h->ev[k + 1]));
+  const Counters& c = *h->h_cnt;
+  for (int k = 0; k < 2; ++k) {
+    out->events[k] = c.cls_events[k];
+    out->tracks[k] = c.cls_tracks[k];
+    out->hits[k] = c.cls_hits[k];
+    out->pixels[k] = c.cls_pixels[k];
+  }
+  return VELO_OK;
 }
 
 int velo_set_params(velo_handle* h, const velo_params* params) {
@@ -283,15 +330,21 @@ int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_outpu
     wk.cl_y = nullptr;
     wk.cl_key = nullptr;
   }
+  const bool tm = h->timing;
   CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[0], st));
   CUDA_TRY(launch_prep(ev, wk, h->caps[0], h->geo.n_sensors, h->cfg.max_pixels, st));
-  if (E) {
-    CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[0], 0, h->threads[0], h->ctas[0], st));
-    CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[1], 1, h->threads[1], h->ctas[1], st));
-  }
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[1], st));
+  if (E) CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[0], 0, h->threads[0], h->ctas[0], st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[2], st));
+  if (E) CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[1], 1, h->threads[1], h->ctas[1], st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[3], st));
   CUDA_TRY(launch_scan(E, wk, *out, st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[4], st));
   CUDA_TRY(launch_emit(E, wk, *out, st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[5], st));
   CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (tm) CUDA_TRY(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   return VELO_OK;
 }
 

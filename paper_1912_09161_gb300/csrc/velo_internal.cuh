@@ -63,7 +63,11 @@ struct Counters {
   uint32_t track_cursor;   // scratch bump allocators
   uint32_t hit_cursor;
   uint32_t error;          // kErr* bits
-  uint32_t pad[9];
+  uint32_t pad0;
+  uint32_t cls_events[2];  // events completed per class
+  uint32_t cls_tracks[2];  // tracks written per class
+  uint32_t cls_hits[2];    // track hits written per class
+  unsigned long long cls_pixels[2];  // raw pixels read per class
 };
 
 // Device views.

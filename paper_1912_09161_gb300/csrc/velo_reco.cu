@@ -62,13 +62,17 @@ __device__ __forceinline__ int phi_bin(float pa) {
 struct Layout {
   uint32_t z, soff, ccnt, cbase, bins, misc, scan;  // fixed part
   uint32_t hx, hy, sorted, hsen, used;              // per provisional hit slot
-  uint32_t uni;                                     // union region
-  // pixel phase (in the union region)
-  uint32_t pk, par;
-  // track phase (in the union region)
-  uint32_t t_last, t_prev, t_a, t_b, t_head, t_n, t_skip, t_act, t_seed, t_key, t_rank, t_hoff, chain;
+  uint32_t uni, uni_bytes;                          // union region
+  // track phase (in the union region); r0/r1 hold the cached slopes during
+  // the rounds and the canonical key / rank afterwards, r2 the hit offsets
+  uint32_t t_last, t_prev, t_a, t_b, t_head, t_n, t_skip, t_act, t_seed, t_r0, t_r1, t_r2, chain;
   uint32_t total;
 };
+
+// Clustering scratch: during clustering every warp owns an equal slice of the
+// union region (accumulators, then staged pixels of a large sensor).
+constexpr uint32_t kAccBytes = 8 * 64;
+constexpr uint32_t kMinSliceBytes = kAccBytes + 6 * 128;
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
@@ -86,13 +90,8 @@ __host__ __device__ inline Layout make_layout(uint32_t maxp, uint32_t maxt, uint
   L.hy = o; o = align16(o + 4 * maxp);
   L.sorted = o; o = align16(o + 2 * maxp);
   L.hsen = o; o = align16(o + maxp);
-  L.used = o; o = align16(o + maxp);
+  L.used = o; o = align16(o + 8 * ((maxp + 31) / 32));  // two bitmaps
   L.uni = o;
-  // pixel phase
-  uint32_t p = o;
-  L.pk = p; p = align16(p + 4 * maxp);
-  L.par = p; p = align16(p + 2 * maxp);
-  // track phase
   uint32_t t = o;
   L.t_last = t; t = align16(t + 2 * maxt);
   L.t_prev = t; t = align16(t + 2 * maxt);
@@ -103,31 +102,37 @@ __host__ __device__ inline Layout make_layout(uint32_t maxp, uint32_t maxt, uint
   L.t_skip = t; t = align16(t + maxt);
   L.t_act = t; t = align16(t + maxt);
   L.t_seed = t; t = align16(t + 4 * maxt);
-  L.t_key = t; t = align16(t + 4 * maxt);
-  L.t_rank = t; t = align16(t + 4 * maxt);
-  L.t_hoff = t; t = align16(t + 4 * maxt);
+  L.t_r0 = t; t = align16(t + 4 * maxt);
+  L.t_r1 = t; t = align16(t + 4 * maxt);
+  L.t_r2 = t; t = align16(t + 4 * maxt);
   L.chain = t; t = align16(t + 4 * maxch);
-  L.total = p > t ? p : t;
+  const uint32_t min_uni = 16 * kMinSliceBytes;  // up to 16 warps
+  L.uni_bytes = (t - o) > min_uni ? (t - o) : min_uni;
+  L.total = o + L.uni_bytes;
   return L;
+}
+
+__host__ __device__ inline uint32_t caps_maxt(uint32_t maxp) { return maxp / 16 + 64; }
+__host__ __device__ inline uint32_t caps_maxch(uint32_t maxp) {
+  uint32_t c = maxp * 3 / 5 + 256;
+  return c > 65535u ? 65535u : c;
 }
 
 Caps make_caps(uint32_t smem_budget, uint32_t n_modules, uint32_t n_threads) {
   (void)n_modules;
   (void)n_threads;
-  // Largest pixel capacity whose plan fits the budget, with track storage
-  // sized as one track per 8 pixels and one chain entry per pixel.
+  // Largest pixel capacity whose plan fits the budget.  Track and chain
+  // storage follow the occupancy of nominal events with a factor ~2 margin;
+  // an event that runs out is retried in the larger class.
   Caps c{};
-  uint32_t lo = 64, hi = 65535;
+  uint32_t lo = 64, hi = 65504;
   while (lo < hi) {
     uint32_t mid = (lo + hi + 1) / 2;
-    uint32_t maxt = mid / 8 + 64, maxch = mid + 256;
-    if (maxch > 65535) maxch = 65535;
-    if (maxt > 65535) maxt = 65535;
-    if (make_layout(mid, maxt, maxch).total <= smem_budget) lo = mid; else hi = mid - 1;
+    if (make_layout(mid, caps_maxt(mid), caps_maxch(mid)).total <= smem_budget) lo = mid; else hi = mid - 1;
   }
   c.maxp = lo & ~31u;
-  c.maxt = c.maxp / 8 + 64;
-  c.maxch = c.maxp + 256 > 65535 ? 65535 : c.maxp + 256;
+  c.maxt = caps_maxt(c.maxp);
+  c.maxch = caps_maxch(c.maxp);
   c.smem = make_layout(c.maxp, c.maxt, c.maxch).total;
   return c;
 }
@@ -210,6 +215,288 @@ __device__ __forceinline__ void bin_range(const uint32_t* bins, int m, int b, ui
   e = bins[k];
 }
 
+
+// ---------------------------------------------------------------------------
+// clustering of one sensor by one warp
+// ---------------------------------------------------------------------------
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+constexpr uint32_t kInv = 0xFFFFFFFFu;
+
+struct HitStore {
+  float* hx;
+  float* hy;
+  uint8_t* hsen;
+  uint16_t* sorted;
+  uint32_t* bins;
+};
+
+struct SensorGeo {
+  float ox, oy, cdx, cdy, rdx, rdy, pitch;
+  int s, m;
+};
+
+__device__ __forceinline__ SensorGeo sensor_geo(const DevGeometry* __restrict__ geo, int s) {
+  return SensorGeo{geo->ox[s], geo->oy[s], geo->cdx[s], geo->cdy[s], geo->rdx[s], geo->rdy[s], geo->pitch,
+                   s, s / kSPM};
+}
+
+// Centroid of the pixel centres, mapped to the global frame; the hit takes
+// provisional id p and is counted in its phi bin.
+__device__ __forceinline__ void store_cluster(const HitStore& hs, const SensorGeo& g, uint32_t p, uint32_t key,
+                                              uint32_t cnt, uint32_t sc, uint32_t sr) {
+  const float lx = fmul(fadd(fdiv((float)sc, (float)cnt), 0.5f), g.pitch);
+  const float ly = fmul(fadd(fdiv((float)sr, (float)cnt), 0.5f), g.pitch);
+  const float x = fadd(fadd(g.ox, fmul(g.cdx, lx)), fmul(g.rdx, ly));
+  const float y = fadd(fadd(g.oy, fmul(g.cdy, lx)), fmul(g.rdy, ly));
+  hs.hx[p] = x;
+  hs.hy[p] = y;
+  hs.hsen[p] = (uint8_t)g.s;
+  hs.sorted[p] = (uint16_t)key;  // smallest pixel key, until the bin scatter
+  atomicAdd(&hs.bins[g.m * kNB + phi_bin(pseudo_angle(x, y))], 1u);
+}
+
+// Value held at sorted position q (element q lives in lane q % 32, register q / 32).
+template <int R>
+__device__ __forceinline__ uint32_t warp_fetch(const uint32_t (&v)[R], uint32_t q) {
+  uint32_t x = __shfl_sync(kFull, v[0], q & 31);
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    const uint32_t y = __shfl_sync(kFull, v[r], q & 31);
+    if ((q >> 5) == (uint32_t)r) x = y;
+  }
+  return x;
+}
+
+// Sensors of at most 32 * R pixels, R per lane, in registers:
+//   - bitonic sort of the keys c * 512 + r (the gap of 256 between columns
+//     keeps a column wrap from looking adjacent; invalid pixels sort last);
+//   - a repeated pixel is the one equal to its sorted predecessor;
+//   - 8-neighbours differ by 1, 511, 512 or 513: a short scan forward and
+//     backward over the sorted keys finds them;
+//   - component label = smallest sorted position, propagated over the
+//     neighbour masks until stable (so the root is the smallest key);
+//   - member sums through one packed 64-bit shared-memory add per pixel;
+//     a root's rank among the sensor's roots is a population count.
+template <int R>  // R <= 2: neighbour masks are 64-bit
+__device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
+                                       uint32_t a, uint32_t n, int ncols, int nrows, const SensorGeo& g,
+                                       const HitStore& hs, unsigned long long* acc, bool& bad) {
+  // acc: this warp's 64 packed accumulators
+  constexpr uint32_t NE = 32 * R;
+  static_assert(R == 1 || R == 2, "positions must fit a 64-bit mask");
+  const int lane = threadIdx.x & 31;
+  uint32_t k[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t idx = lane + 32 * r;
+    k[r] = kInv;
+    if (idx < n) {
+      const uint32_t c = col[a + idx], w = row[a + idx];
+      if (c < (uint32_t)ncols && w < (uint32_t)nrows) k[r] = (c << 9) | w;
+      else bad = true;
+    }
+  }
+  // bitonic sort over element index e = lane + 32 r
+#pragma unroll
+  for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
+#pragma unroll
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int rp = r ^ (int)(j >> 5);
+          if (rp > r) {
+            const uint32_t e = lane + 32u * r;
+            const bool up = (e & kk) == 0;
+            const uint32_t lo = min(k[r], k[rp]), hi = max(k[r], k[rp]);
+            k[r] = up ? lo : hi;
+            k[rp] = up ? hi : lo;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t o = __shfl_xor_sync(kFull, k[r], j);
+          const uint32_t e = lane + 32u * r;
+          const bool up = (e & kk) == 0, lower = (e & j) == 0;
+          k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
+        }
+      }
+    }
+  }
+  // repeated pixels; valid-position mask
+  uint64_t vm = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t e = lane + 32u * r;
+    const uint32_t prev = warp_fetch<R>(k, (e + NE - 1) % NE);
+    const bool ok = k[r] != kInv && !(e > 0 && prev == k[r]);
+    vm |= (uint64_t)__ballot_sync(kFull, ok) << (32 * r);
+  }
+  bool valid[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) valid[r] = (vm >> (lane + 32 * r)) & 1ull;
+  // neighbour masks (positions), scanning outward until out of reach
+  uint64_t nb[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) nb[r] = 0;
+  for (uint32_t d = 1; d < NE; ++d) {
+    bool reach = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t e = lane + 32u * r;
+      const uint32_t qf = e + d, qb = e - d;  // qb wraps when e < d
+      const uint32_t kf = warp_fetch<R>(k, qf % NE), kb = warp_fetch<R>(k, qb % NE);
+      if (!valid[r]) continue;
+      if (qf < NE && kf != kInv && kf - k[r] <= 513u) {
+        reach = true;
+        const uint32_t dl = kf - k[r];
+        if (dl == 1u || dl - 511u <= 2u) nb[r] |= 1ull << qf;
+      }
+      if (e >= d && k[r] - kb <= 513u) {
+        reach = true;
+        const uint32_t dl = k[r] - kb;
+        if (dl == 1u || dl - 511u <= 2u) nb[r] |= 1ull << qb;
+      }
+    }
+    if (!__any_sync(kFull, reach)) break;
+  }
+  uint32_t lab[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    nb[r] &= vm;
+    lab[r] = lane + 32u * r;
+  }
+  // propagate the smallest position over the neighbour masks
+  while (true) {
+    bool ch = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      uint64_t bits = nb[r];
+      uint32_t cnt = __popcll(bits);
+      cnt = __reduce_max_sync(kFull, cnt);
+      for (uint32_t it = 0; it < cnt; ++it) {
+        const uint32_t q = bits ? (uint32_t)(__ffsll((long long)bits) - 1) : (lane + 32u * r);
+        bits &= bits - 1;
+        const uint32_t lq = warp_fetch<R>(lab, q);
+        if (lq < lab[r]) { lab[r] = lq; ch = true; }
+      }
+    }
+    if (!__any_sync(kFull, ch)) break;
+  }
+  // member sums: count << 56 | sum(col) << 28 | sum(row), accumulated at the root
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[lane + 32 * r] = 0ull;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (valid[r])
+      atomicAdd(&acc[lab[r]], (1ull << 56) | ((unsigned long long)(k[r] >> 9) << 28) | (k[r] & 511u));
+  __syncwarp();
+  uint32_t nroot = 0, below = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t e = lane + 32u * r;
+    const bool root = valid[r] && lab[r] == e;
+    const uint32_t rm = __ballot_sync(kFull, root);
+    const uint32_t rank = below + __popc(rm & ((1u << lane) - 1u));
+    below += __popc(rm);
+    nroot += __popc(rm);
+    if (root) {
+      const unsigned long long v = acc[e];
+      const uint32_t key16 = ((k[r] >> 9) << 8) | (k[r] & 255u);
+      store_cluster(hs, g, a + rank, key16, (uint32_t)(v >> 56), (uint32_t)((v >> 28) & 0xFFFFFFFull),
+                    (uint32_t)(v & 0xFFFFFFFull));
+    }
+  }
+  __syncwarp();
+  return nroot;
+}
+
+// Larger sensors: pixels staged in shared memory at their event positions,
+// repeated pixels dropped, 8-neighbours joined by union-find, roots ranked.
+__device__ uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
+                                        uint32_t a, uint32_t n, int ncols, int nrows, const SensorGeo& g,
+                                        const HitStore& hs, uint32_t* k_, uint16_t* p_, bool& bad) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t c = col[a + i], w = row[a + i];
+    const bool ok = c < (uint32_t)ncols && w < (uint32_t)nrows;
+    k_[i] = ok ? ((c << 8) | w) : kInv;
+    bad |= !ok;
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t k = k_[i];
+    bool ign = (k >> 31) != 0;
+    for (uint32_t j = 0; j < i && !ign; ++j) ign = (k_[j] == k);
+    p_[i] = ign ? (uint16_t)kNone16 : (uint16_t)i;
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32)
+    if (p_[i] == kNone16) k_[i] |= 0x80000000u;
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t ki = k_[i];
+    if (ki >> 31) continue;
+    const int ci = (int)(ki >> 8), ri = (int)(ki & 255u);
+    for (uint32_t j = i + 1; j < n; ++j) {
+      const uint32_t kj = k_[j];
+      if (kj >> 31) continue;
+      const int dc = (int)(kj >> 8) - ci, dr = (int)(kj & 255u) - ri;
+      if (dc >= -1 && dc <= 1 && dr >= -1 && dr <= 1) uf_unite(p_, k_, (int)i, (int)j);
+    }
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32)
+    if (!(k_[i] >> 31)) p_[i] = (uint16_t)uf_find(p_, (int)i);
+  __syncwarp();
+  uint32_t nroot = 0;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t ki = k_[i];
+    if ((ki >> 31) || p_[i] != i) continue;
+    const uint32_t key = ki & 0xFFFFu;
+    uint32_t cnt = 0, sc = 0, sr = 0, rank = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t kj = k_[j];
+      if (kj >> 31) continue;
+      const uint32_t pj = p_[j];
+      if (pj == i) { cnt++; sc += kj >> 8; sr += kj & 255u; }
+      if (pj == j && (kj & 0xFFFFu) < key) rank++;
+    }
+    store_cluster(hs, g, a + rank, key, cnt, sc, sr);
+    nroot++;
+  }
+  nroot = __reduce_add_sync(kFull, nroot);
+  __syncwarp();
+  return nroot;
+}
+
+// Candidate hits of module m in the phi window around pa: one or two
+// contiguous ranges of the phi-binned hit list.
+struct Cand {
+  uint32_t s0, n0, s1, n1;
+  __device__ __forceinline__ uint32_t n() const { return n0 + n1; }
+  __device__ __forceinline__ uint32_t at(uint32_t k) const { return k < n0 ? s0 + k : s1 + (k - n0); }
+};
+__device__ __forceinline__ Cand window_cands(const uint32_t* bins, int m, float pa, float w) {
+  const BinWindow bw = bin_window(pa, w);
+  const int base = m * kNB;
+  const int last = bw.first + bw.count - 1;
+  Cand c;
+  c.s0 = (base + bw.first) ? bins[base + bw.first - 1] : 0u;
+  if (last < kNB) {
+    c.n0 = bins[base + last] - c.s0;
+    c.s1 = 0;
+    c.n1 = 0;
+  } else {
+    c.n0 = bins[base + kNB - 1] - c.s0;
+    c.s1 = base ? bins[base - 1] : 0u;
+    c.n1 = bins[base + last - kNB] - c.s1;
+  }
+  return c;
+}
+
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
@@ -234,9 +521,7 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
   float* hy = (float*)(smem + L.hy);
   uint16_t* sorted = (uint16_t*)(smem + L.sorted);
   uint8_t* hsen = (uint8_t*)(smem + L.hsen);
-  uint8_t* used = (uint8_t*)(smem + L.used);
-  uint32_t* pk = (uint32_t*)(smem + L.pk);
-  uint16_t* upar = (uint16_t*)(smem + L.par);
+  uint32_t* used = (uint32_t*)(smem + L.used);  // bitmap over provisional ids
   uint16_t* t_last = (uint16_t*)(smem + L.t_last);
   uint16_t* t_prev = (uint16_t*)(smem + L.t_prev);
   uint16_t* t_a = (uint16_t*)(smem + L.t_a);
@@ -246,13 +531,21 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
   uint8_t* t_skip = (uint8_t*)(smem + L.t_skip);
   uint8_t* t_act = (uint8_t*)(smem + L.t_act);
   float* t_seed = (float*)(smem + L.t_seed);
-  uint32_t* t_key = (uint32_t*)(smem + L.t_key);
-  uint32_t* t_rank = (uint32_t*)(smem + L.t_rank);
-  uint32_t* t_hoff = (uint32_t*)(smem + L.t_hoff);
+  uint32_t* t_key = (uint32_t*)(smem + L.t_r0);
+  uint32_t* t_rank = (uint32_t*)(smem + L.t_r1);
+  uint32_t* t_hoff = (uint32_t*)(smem + L.t_r2);
+  float* t_tx = (float*)(smem + L.t_r0);
+  float* t_ty = (float*)(smem + L.t_r1);
   uint32_t* chain = (uint32_t*)(smem + L.chain);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
+  const uint32_t slice = (L.uni_bytes / NW) & ~15u;
+  unsigned char* wscratch = smem + L.uni + warp * slice;
+  unsigned long long* s_acc = (unsigned long long*)wscratch;
+  uint32_t* w_pk = (uint32_t*)(wscratch + kAccBytes);
+  const uint32_t w_cap = (slice - kAccBytes) / 6;
+  uint16_t* w_par = (uint16_t*)(wscratch + kAccBytes + 4 * w_cap);
   const int nm = geo->n_modules, ns = geo->n_sensors;
   const int ncols = geo->n_cols, nrows = geo->n_rows;
   const float tol = par.tan_phi_tol, win = par.phi_window;
@@ -285,87 +578,40 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
       }
       continue;
     }
-    {
-      const uint16_t* col = ev.col + gbase;
-      const uint16_t* row = ev.row + gbase;
-      uint32_t bad = 0;
-      for (uint32_t i = tid; i < P; i += NT) {
-        uint32_t c = col[i], r = row[i];
-        bool ok = c < (uint32_t)ncols && r < (uint32_t)nrows;
-        pk[i] = ok ? ((c << 8) | r) : 0xFFFFFFFFu;
-        bad |= ok ? 0u : 1u;
-      }
-      if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(&s_misc[M_STATUS], VELO_EV_BAD_PIXEL);
-    }
     for (int k = tid; k < nm * kNB; k += NT) s_bins[k] = 0;
-    for (uint32_t i = tid; i < P; i += NT) used[i] = 0;
+    for (uint32_t i = tid; i < (P + 31) / 32; i += NT) used[i] = 0;
     __syncthreads();
 
     // ---- 2+3. cluster each sensor (one warp per sensor) -------------------
-    for (int s = warp; s < ns; s += NW) {
-      const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
-      uint32_t* k_ = pk + a;
-      uint16_t* p_ = upar + a;
-      // repeated or invalid pixels are ignored
-      for (uint32_t i = lane; i < n; i += 32) {
-        uint32_t k = k_[i];
-        bool ign = (k >> 31) != 0;
-        for (uint32_t j = 0; j < i && !ign; ++j) ign = (k_[j] == k);
-        p_[i] = ign ? (uint16_t)kNone16 : (uint16_t)i;
+    {
+      const uint16_t* col = ev.col + gbase;
+      const uint16_t* row = ev.row + gbase;
+      const HitStore hs{hx, hy, hsen, sorted, s_bins};
+      bool bad = false, big = false;
+      for (int s = warp; s < ns; s += NW) {
+        const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
+        const SensorGeo g = sensor_geo(geo, s);
+        uint32_t nroot;
+        if (n <= 32) nroot = cluster_sensor_reg<1>(col, row, a, n, ncols, nrows, g, hs, s_acc, bad);
+        else if (n <= 64) nroot = cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, hs, s_acc, bad);
+        else if (n <= w_cap) nroot = cluster_sensor_smem(col, row, a, n, ncols, nrows, g, hs, w_pk, w_par, bad);
+        else { nroot = 0; big = true; }
+        if (lane == 0) s_ccnt[s] = nroot;
       }
-      __syncwarp();
-      for (uint32_t i = lane; i < n; i += 32)
-        if (p_[i] == kNone16) k_[i] |= 0x80000000u;
-      __syncwarp();
-      // 8-connected neighbours
-      for (uint32_t i = lane; i < n; i += 32) {
-        uint32_t ki = k_[i];
-        if (ki >> 31) continue;
-        int ci = (int)(ki >> 8), ri = (int)(ki & 255u);
-        for (uint32_t j = i + 1; j < n; ++j) {
-          uint32_t kj = k_[j];
-          if (kj >> 31) continue;
-          int dc = (int)(kj >> 8) - ci, dr = (int)(kj & 255u) - ri;
-          if (dc >= -1 && dc <= 1 && dr >= -1 && dr <= 1) uf_unite(p_, k_, (int)i, (int)j);
+      if (__any_sync(kFull, bad) && lane == 0) atomicOr(&s_misc[M_STATUS], VELO_EV_BAD_PIXEL);
+      if (__syncthreads_or(big)) {  // a sensor larger than a warp's scratch
+        if (tid == 0) {
+          if (cls == 0) {
+            const uint32_t pos = atomicAdd(&wk.cnt->queue_len[1], 1u);
+            wk.queue[1][pos] = e;
+          } else {
+            wk.rec[e] = EventRec{0, 0, 0, VELO_EV_OVERFLOW | s_misc[M_STATUS], 0, 0, gbase, 0};
+            atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+          }
         }
+        continue;
       }
-      __syncwarp();
-      for (uint32_t i = lane; i < n; i += 32)
-        if (!(k_[i] >> 31)) p_[i] = (uint16_t)uf_find(p_, (int)i);
-      __syncwarp();
-      // every root: pixel sums, rank among the roots, global position, phi bin
-      const int m = s / kSPM;
-      const float ox = geo->ox[s], oy = geo->oy[s];
-      const float cdx = geo->cdx[s], cdy = geo->cdy[s], rdx = geo->rdx[s], rdy = geo->rdy[s];
-      const float pitch = geo->pitch;
-      uint32_t nroot = 0;
-      for (uint32_t i = lane; i < n; i += 32) {
-        uint32_t ki = k_[i];
-        if ((ki >> 31) || p_[i] != i) continue;
-        uint32_t key = ki & 0xFFFFu, cnt = 0, sc = 0, sr = 0, rank = 0;
-        for (uint32_t j = 0; j < n; ++j) {
-          uint32_t kj = k_[j];
-          if (kj >> 31) continue;
-          uint32_t pj = p_[j];
-          if (pj == i) { cnt++; sc += kj >> 8; sr += kj & 255u; }
-          if (pj == j && (kj & 0xFFFFu) < key) rank++;
-        }
-        float lx = fmul(fadd(fdiv((float)sc, (float)cnt), 0.5f), pitch);
-        float ly = fmul(fadd(fdiv((float)sr, (float)cnt), 0.5f), pitch);
-        float x = fadd(fadd(ox, fmul(cdx, lx)), fmul(rdx, ly));
-        float y = fadd(fadd(oy, fmul(cdy, lx)), fmul(rdy, ly));
-        uint32_t p = a + rank;
-        hx[p] = x;
-        hy[p] = y;
-        hsen[p] = (uint8_t)s;
-        sorted[p] = (uint16_t)key;  // smallest pixel key, until the bin scatter
-        atomicAdd(&s_bins[m * kNB + phi_bin(pseudo_angle(x, y))], 1u);
-        nroot++;
-      }
-      nroot = __reduce_add_sync(0xFFFFFFFFu, nroot);
-      if (lane == 0) s_ccnt[s] = nroot;
     }
-    __syncthreads();
     for (int s = tid; s < ns; s += NT) s_cbase[s] = s_ccnt[s];
     __syncthreads();
     const uint32_t ncl = block_exscan(s_cbase, ns, s_scan);
@@ -403,113 +649,109 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
     for (int i = nm - 3; i >= 0; --i) {
       bool ovf = false;           // this thread ran out of track or chain storage
       const float zi = s_z[i];
-      // phase A: extend every active track into module i
+      // phase A: extend every active track into module i (one thread per
+      // track; the straight line through its last two hits is cached)
       const uint32_t ntr = min(s_misc[M_NTR], caps.maxt);
       for (uint32_t t = tid; t < ntr; t += NT) {
-        if (t >= ntr_seeds_from) {  // mark the hits of the newest seeds
-          used[t_a[t]] = 1;
-          used[t_b[t]] = 1;
-          used[t_last[t]] = 1;
+        if (t >= ntr_seeds_from) {  // hits of the newest seeds become used
+          const uint32_t h0 = t_a[t], h1 = t_b[t], h2 = t_last[t];
+          atomicOr(&used[h0 >> 5], 1u << (h0 & 31));
+          atomicOr(&used[h1 >> 5], 1u << (h1 & 31));
+          atomicOr(&used[h2 >> 5], 1u << (h2 & 31));
         }
         if (!t_act[t]) continue;
-        const uint32_t l = t_last[t], q2 = t_prev[t];
+        const uint32_t l = t_last[t];
         const float xl = hx[l], yl = hy[l];
-        const float zl = s_z[hsen[l] / kSPM], zq = s_z[hsen[q2] / kSPM];
-        const float dzq = fsub(zq, zl);
-        const float tx = fdiv(fsub(hx[q2], xl), dzq);
-        const float ty = fdiv(fsub(hy[q2], yl), dzq);
+        const float zl = s_z[hsen[l] / kSPM];
         const float dzi = fsub(zi, zl);
-        const float xp = fadd(xl, fmul(tx, dzi));
-        const float yp = fadd(yl, fmul(ty, dzi));
-        uint32_t best = kNone16;
-        float bs = 0.0f;
-        const BinWindow w = bin_window(pseudo_angle(xl, yl), win);
-        for (int kb = 0; kb < w.count; ++kb) {
-          int b = w.first + kb;
-          if (b >= kNB) b -= kNB;
-          uint32_t k0, k1;
-          bin_range(s_bins, i, b, k0, k1);
-          for (uint32_t k = k0; k < k1; ++k) {
-            const uint32_t h = sorted[k];
-            const float xh = hx[h], yh = hy[h];
-            if (!phi_ok(xl, yl, xh, yh, tol)) continue;
-            const float dx = fsub(xh, xp), dy = fsub(yh, yp);
-            const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-            if (!(s2 < par.max_scatter_fwd)) continue;
-            if (best == kNone16 || s2 < bs || (s2 == bs && h < best)) { best = h; bs = s2; }
-          }
+        const float xp = fadd(xl, fmul(t_tx[t], dzi));
+        const float yp = fadd(yl, fmul(t_ty[t], dzi));
+        unsigned long long best = ~0ull;
+        const Cand cw = window_cands(s_bins, i, pseudo_angle(xl, yl), win);
+        for (uint32_t k = 0; k < cw.n(); ++k) {
+          const uint32_t h = sorted[cw.at(k)];
+          const float xh = hx[h], yh = hy[h];
+          if (!phi_ok(xl, yl, xh, yh, tol)) continue;
+          const float dx = fsub(xh, xp), dy = fsub(yh, yp);
+          const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
+          if (!(s2 < par.max_scatter_fwd)) continue;
+          best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | h);
         }
-        if (best != kNone16) {
-          uint32_t c = atomicAdd(&s_misc[M_NCH], 1u);
+        if (best != ~0ull) {
+          const uint32_t h = (uint32_t)(best & 0xFFFFu);
+          const uint32_t c = atomicAdd(&s_misc[M_NCH], 1u);
           if (c >= caps.maxch) {
             ovf = true;
           } else {
-            chain[c] = (best << 16) | t_head[t];
+            const float xh = hx[h], yh = hy[h];
+            const float dzq = fsub(zl, zi);
+            chain[c] = (h << 16) | t_head[t];
             t_head[t] = (uint16_t)c;
             t_prev[t] = (uint16_t)l;
-            t_last[t] = (uint16_t)best;
+            t_last[t] = (uint16_t)h;
+            t_tx[t] = fdiv(fsub(xl, xh), dzq);
+            t_ty[t] = fdiv(fsub(yl, yh), dzq);
             t_n[t] = t_n[t] + 1;
             t_skip[t] = 0;
-            used[best] = 1;
+            atomicOr(&used[h >> 5], 1u << (h & 31));
           }
         } else {
-          uint32_t sk = t_skip[t] + 1u;
+          const uint32_t sk = t_skip[t] + 1u;
           t_skip[t] = (uint8_t)min(sk, 255u);
           if (sk > par.max_skipped) t_act[t] = 0;
         }
       }
       if (__syncthreads_or(ovf)) { overflow = true; break; }
       ntr_seeds_from = ntr;
-      // phase B: seeds with the middle hit in module i + 1
+      // phase B: seeds with the middle hit b in module i + 1; GB lanes per b
+      // split the candidates a of module i + 2 and agree on the smallest
+      // (scatter, a, c)
       {
         const int mb = i + 1, ma = i + 2;
         const float za = s_z[ma], zb = s_z[mb];
         const float dzab = fsub(za, zb), dzc = fsub(zi, zb);
-        const uint32_t kb0 = mb * kNB ? s_bins[mb * kNB - 1] : 0u, kb1 = s_bins[mb * kNB + kNB - 1];
-        for (uint32_t kk = kb0 + tid; kk < kb1; kk += NT) {
-          const uint32_t b = sorted[kk];
-          if (used[b]) continue;
-          const float xb = hx[b], yb = hy[b];
-          const float pab = pseudo_angle(xb, yb);
-          const BinWindow w = bin_window(pab, win);
-          uint32_t ba = kNone16, bc = kNone16;
-          float bs = 0.0f;
-          for (int wa = 0; wa < w.count; ++wa) {
-            int binA = w.first + wa;
-            if (binA >= kNB) binA -= kNB;
-            uint32_t a0, a1;
-            bin_range(s_bins, ma, binA, a0, a1);
-            for (uint32_t ka = a0; ka < a1; ++ka) {
-              const uint32_t a = sorted[ka];
-              if (used[a]) continue;
-              const float xa = hx[a], ya = hy[a];
-              if (!phi_ok(xa, ya, xb, yb, tol)) continue;
-              const float tx = fdiv(fsub(xa, xb), dzab);
-              const float ty = fdiv(fsub(ya, yb), dzab);
-              if (fabsf(tx) > par.max_slope || fabsf(ty) > par.max_slope) continue;
-              const float xp = fadd(xb, fmul(tx, dzc));
-              const float yp = fadd(yb, fmul(ty, dzc));
-              for (int wc = 0; wc < w.count; ++wc) {
-                int binC = w.first + wc;
-                if (binC >= kNB) binC -= kNB;
-                uint32_t c0, c1;
-                bin_range(s_bins, i, binC, c0, c1);
-                for (uint32_t kc = c0; kc < c1; ++kc) {
-                  const uint32_t c = sorted[kc];
-                  if (used[c]) continue;
+        const uint32_t kb0 = s_bins[mb * kNB - 1], kb1 = s_bins[mb * kNB + kNB - 1];
+        const uint32_t nb = kb1 - kb0;
+        constexpr int GB = 4, NGB = NT / GB;
+        const int g = tid / GB, gl = tid % GB;
+        for (uint32_t base = 0; base < nb; base += NGB) {
+          const uint32_t bi = base + g;
+          unsigned long long best = ~0ull;
+          uint32_t b = kNone16;
+          if (bi < nb) {
+            b = sorted[kb0 + bi];
+            if (!((used[b >> 5] >> (b & 31)) & 1u)) {
+              const float xb = hx[b], yb = hy[b];
+              const float pab = pseudo_angle(xb, yb);
+              const Cand ca = window_cands(s_bins, ma, pab, win);
+              const Cand cc = window_cands(s_bins, i, pab, win);
+              for (uint32_t k = gl; k < ca.n(); k += GB) {
+                const uint32_t a = sorted[ca.at(k)];
+                if ((used[a >> 5] >> (a & 31)) & 1u) continue;
+                const float xa = hx[a], ya = hy[a];
+                if (!phi_ok(xa, ya, xb, yb, tol)) continue;
+                const float tx = fdiv(fsub(xa, xb), dzab);
+                const float ty = fdiv(fsub(ya, yb), dzab);
+                if (fabsf(tx) > par.max_slope || fabsf(ty) > par.max_slope) continue;
+                const float xp = fadd(xb, fmul(tx, dzc));
+                const float yp = fadd(yb, fmul(ty, dzc));
+                for (uint32_t kc = 0; kc < cc.n(); ++kc) {
+                  const uint32_t c = sorted[cc.at(kc)];
+                  if ((used[c >> 5] >> (c & 31)) & 1u) continue;
                   const float xc = hx[c], yc = hy[c];
                   if (!phi_ok(xb, yb, xc, yc, tol)) continue;
                   const float dx = fsub(xc, xp), dy = fsub(yc, yp);
                   const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
                   if (!(s2 < par.max_scatter_seed)) continue;
-                  if (ba == kNone16 || s2 < bs || (s2 == bs && (a < ba || (a == ba && c < bc)))) {
-                    ba = a; bc = c; bs = s2;
-                  }
+                  best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | (a << 16) | c);
                 }
               }
             }
           }
-          if (ba != kNone16) {
+#pragma unroll
+          for (int off = 1; off < GB; off <<= 1) best = min(best, __shfl_xor_sync(kFull, best, off));
+          if (gl == 0 && best != ~0ull) {
+            const uint32_t ba = (uint32_t)((best >> 16) & 0xFFFFu), bc = (uint32_t)(best & 0xFFFFu);
             const uint32_t t = atomicAdd(&s_misc[M_NTR], 1u);
             const uint32_t c = atomicAdd(&s_misc[M_NCH], 3u);
             if (t >= caps.maxt || c + 3 > caps.maxch) {
@@ -526,7 +768,10 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
               t_n[t] = 3;
               t_skip[t] = 0;
               t_act[t] = 1;
-              t_seed[t] = bs;
+              t_seed[t] = __uint_as_float((uint32_t)(best >> 32));
+              const float dzbc = fsub(zb, zi);
+              t_tx[t] = fdiv(fsub(hx[b], hx[bc]), dzbc);
+              t_ty[t] = fdiv(fsub(hy[b], hy[bc]), dzbc);
             }
           }
         }
@@ -549,9 +794,9 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
 
     // ---- 5. plain cuts, canonical order, fit --------------------------------
     const uint32_t ntr = s_misc[M_NTR];
-    uint32_t* seen1 = (uint32_t*)used;
+    uint32_t* seen1 = used;
     const uint32_t nwords = (P + 31) / 32;
-    uint32_t* seen2 = seen1 + nwords;
+    uint32_t* seen2 = used + nwords;
     for (uint32_t k = tid; k < 2 * nwords; k += NT) seen1[k] = 0;
     __syncthreads();
     for (uint32_t t = tid; t < ntr; t += NT) {
@@ -604,6 +849,10 @@ __global__ void __launch_bounds__(NT) reco_kernel(const DevGeometry* __restrict_
       s_misc[M_TBASE] = tb;
       s_misc[M_HBASE] = hb;
       wk.rec[e] = EventRec{nk, nh, ncl, st, tb, hb, gbase, 0};
+      atomicAdd(&wk.cnt->cls_events[cls], 1u);
+      atomicAdd(&wk.cnt->cls_tracks[cls], nk);
+      atomicAdd(&wk.cnt->cls_hits[cls], nh);
+      atomicAdd(&wk.cnt->cls_pixels[cls], (unsigned long long)P);
     }
     __syncthreads();
     if (s_misc[M_SKIP]) continue;

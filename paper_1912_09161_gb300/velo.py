@@ -25,7 +25,8 @@ EV_BAD_PIXEL, EV_BAD_OFFSETS, EV_OVERFLOW, EV_TRUNCATED = 1, 2, 4, 8
 CFG_CLUSTERS = 1
 
 EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
-            "velo_sync_status", "velo_reconstruct_host", "velo_last_error", "velo_version")
+            "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_last_error",
+            "velo_version")
 
 
 class VeloError(RuntimeError):
@@ -55,6 +56,11 @@ class velo_config(ctypes.Structure):
     _fields_ = [("max_events", ctypes.c_uint32), ("max_pixels", ctypes.c_uint64),
                 ("max_tracks", ctypes.c_uint64), ("max_track_hits", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32), ("n_slots", ctypes.c_uint32)]
+
+
+class velo_stats(ctypes.Structure):
+    _fields_ = [("events", ctypes.c_uint32 * 2), ("tracks", ctypes.c_uint32 * 2), ("hits", ctypes.c_uint32 * 2),
+                ("pixels", ctypes.c_uint64 * 2), ("ms", ctypes.c_float * 5)]
 
 
 class velo_events(ctypes.Structure):
@@ -94,6 +100,12 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.velo_reconstruct.argtypes = [vp, P(velo_events), P(velo_output), vp]
     lib.velo_sync_status.argtypes = [vp, vp]
     lib.velo_reconstruct_host.argtypes = [vp, ctypes.c_uint32, vp, vp, vp, P(velo_output), vp]
+    lib.velo_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.velo_get_stats.argtypes = [vp, P(velo_stats)]
+    lib.velo_set_timing.restype = ctypes.c_int
+    lib.velo_get_stats.restype = ctypes.c_int
+    lib.velo_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.velo_describe.restype = ctypes.c_int
     lib.velo_last_error.restype = ctypes.c_char_p
     lib.velo_version.restype = ctypes.c_char_p
     for name in ("velo_create", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
@@ -312,6 +324,24 @@ def velo_reconstruct_host(h, n_events: int, sensor_off: np.ndarray, col: np.ndar
         ctypes.c_void_p(stream)))
 
 
+def velo_set_timing(h, on: bool):
+    _check(load_library(False).velo_set_timing(h, 1 if on else 0), "velo_set_timing")
+
+
+def velo_get_stats(h) -> dict:
+    st = velo_stats()
+    _check(load_library(False).velo_get_stats(h, ctypes.byref(st)), "velo_get_stats")
+    return dict(events=list(st.events), tracks=list(st.tracks), hits=list(st.hits), pixels=list(st.pixels),
+                ms=list(st.ms))
+
+
+def velo_describe(h) -> dict:
+    import json
+    buf = ctypes.create_string_buffer(4096)
+    _check(load_library(False).velo_describe(h, buf, len(buf)), "velo_describe")
+    return json.loads(buf.value.decode())
+
+
 def velo_version() -> str:
     return load_library().velo_version().decode()
 
@@ -338,6 +368,15 @@ class Reconstructor:
             self.close()
         except Exception:
             pass
+
+    def describe(self) -> dict:
+        return velo_describe(self.handle)
+
+    def set_timing(self, on: bool = True):
+        velo_set_timing(self.handle, on)
+
+    def stats(self) -> dict:
+        return velo_get_stats(self.handle)
 
     def set_params(self, params: Params):
         self.params = params
