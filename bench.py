@@ -37,7 +37,7 @@ REF_SAMPLE = 2000           # events per oracle step of the reference arm
 CPU_SAMPLE = 10000          # events of the CPU-baseline sample (the whole batch)
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "reco_kernel_nominal_10k.md")
-KERNELS_PER_STEP = 5        # prep, reconstruct (two size classes), scan, emit
+KERNELS_BASE = 4            # clustering, retry pass of the largest class, scan, emit (+ one per class)
 
 
 def _dist():
@@ -268,7 +268,7 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel_ms_per_step": statistics.mean(reco_ms)},
         "e2e": e2e,
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": (KERNELS_BASE + len(desc["classes"])) * args.steps,
         "clocks": clocks.summary(),
     }
     if ws == 1:

@@ -176,14 +176,16 @@ int velo_reconstruct_host(velo_handle *h, uint32_t n_events, const uint32_t *sen
                           const uint16_t *col_host, const uint16_t *row_host,
                           const velo_output *out_host, void *stream);
 
-/* Per-call statistics (velo_get_stats).  Kernel class 0 runs events whose
- * working set fits two CTAs per SM, class 1 the larger ones. */
+/* Per-call statistics (velo_get_stats).  The tracking kernel runs in up to
+ * four shared-memory classes (4, 3, 2, 1 CTAs per SM); an event runs in the
+ * smallest class that holds its hits. */
 typedef struct velo_stats {
-  uint32_t events[2];   /* events reconstructed by each class */
-  uint32_t tracks[2];   /* tracks written by each class */
-  uint32_t hits[2];     /* track hits written by each class */
-  uint64_t pixels[2];   /* raw pixels read by each class */
-  float ms[5];          /* device time of prep, class 0, class 1, scan, emit */
+  uint32_t n_classes;
+  uint32_t events[4];   /* events reconstructed by each class */
+  uint32_t tracks[4];   /* tracks written by each class */
+  uint32_t hits[4];     /* track hits written by each class */
+  uint64_t pixels[4];   /* raw pixels of those events */
+  float ms[5];          /* device time: clustering, tracking (all classes), scan, emit, whole call */
 } velo_stats;
 
 /* Turns per-kernel timing (CUDA events on the call's stream) on or off. */

@@ -47,10 +47,17 @@ struct velo_handle {
   DevGeometry* d_geo = nullptr;
   Counters* d_cnt = nullptr;
   WorkView wk{};
-  // kernel classes
-  Caps caps[2]{};
-  int threads[2]{256, 256};
-  int ctas[2]{0, 0};
+  // clustering kernel
+  int cl_threads = 256;
+  // tracking-kernel classes (increasing shared-memory plans), each on its stream
+  int n_classes = 0;
+  Caps caps[kMaxClasses]{};
+  int per_sm[kMaxClasses]{};
+  int threads = 256;
+  int ctas[kMaxClasses]{};
+  cudaStream_t cls_stream[kMaxClasses]{};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kMaxClasses]{};
   // host-path staging (allocated on first use)
   void* stage = nullptr;
   size_t stage_bytes = 0;
@@ -58,7 +65,7 @@ struct velo_handle {
   uint32_t last_error_bits = 0;
   // optional per-kernel timing of the last call
   bool timing = false;
-  cudaEvent_t ev[6]{};
+  cudaEvent_t ev[5]{};
   Counters* h_cnt = nullptr;  // pinned copy of the counters of the last call
 };
 
@@ -124,7 +131,7 @@ velo_config with_defaults(const velo_config* c) {
 }
 
 struct ArenaPlan {
-  size_t geo, cnt, rec, q0, q1, st, nh, ho, hits, clx, cly, clk, total;
+  size_t geo, cnt, rec, q[kQueues], prov, pkey, cbase, st, nh, ho, hits, clx, cly, clk, total;
 };
 
 ArenaPlan plan_arena(const velo_config& c) {
@@ -133,8 +140,10 @@ ArenaPlan plan_arena(const velo_config& c) {
   a.geo = o; o = align256(o + sizeof(DevGeometry));
   a.cnt = o; o = align256(o + sizeof(Counters));
   a.rec = o; o = align256(o + sizeof(EventRec) * c.max_events);
-  a.q0 = o; o = align256(o + 4ull * c.max_events);
-  a.q1 = o; o = align256(o + 4ull * c.max_events);
+  for (int k = 0; k < kQueues; ++k) { a.q[k] = o; o = align256(o + 4ull * c.max_events); }
+  a.prov = o; o = align256(o + 8ull * c.max_pixels);
+  if (c.flags & VELO_CFG_CLUSTERS) { a.pkey = o; o = align256(o + 2ull * c.max_pixels); }
+  a.cbase = o; o = align256(o + 2ull * (kMaxSensors + 1) * c.max_events);
   a.st = o; o = align256(o + 4ull * VELO_NSTATE * c.max_tracks);
   a.nh = o; o = align256(o + 2ull * c.max_tracks);
   a.ho = o; o = align256(o + 4ull * c.max_tracks);
@@ -197,21 +206,40 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-    // class 0: two CTAs per SM; class 1: one CTA per SM with the largest plan
-    uint32_t budget0 = (uint32_t)(smem_sm / 2 - 1024);
-    uint32_t budget1 = (uint32_t)smem_optin;
-    if (budget0 > budget1) budget0 = budget1;
-    h->caps[0] = make_caps(budget0, g.n_modules, 256);
-    h->caps[1] = make_caps(budget1, g.n_modules, 256);
-    for (int c = 0; c < 2; ++c) {
-      e = reco_set_smem_limit(h->threads[c], (int)h->caps[c].smem);
-      if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e)); break; }
+    // Tracking classes: 4, 3, 2 and 1 CTAs per SM, each with the largest
+    // plan that fits its share of shared memory; an event goes to the
+    // smallest class that holds its hits.
+    e = cluster_set_smem_limit(h->cl_threads);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(cluster): %s", cudaGetErrorString(e)); break; }
+    const int per_sm_try[kMaxClasses] = {4, 3, 2, 1};
+    uint32_t prev_maxh = 0;
+    for (int k = 0; k < kMaxClasses && rc == VELO_OK; ++k) {
+      uint32_t budget = (uint32_t)(smem_sm / per_sm_try[k]) - 1024u;
+      if (budget > (uint32_t)smem_optin) budget = (uint32_t)smem_optin;
+      const Caps c = make_caps(budget, (uint32_t)g.n_modules);
+      if (c.maxh <= prev_maxh) continue;
+      e = track_set_smem_limit(h->threads, (int)c.smem);
+      if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e)); break; }
       int per_sm = 0;
-      e = reco_occupancy(h->threads[c], (int)h->caps[c].smem, &per_sm);
+      e = track_occupancy(h->threads, (int)c.smem, &per_sm);
       if (e != cudaSuccess || per_sm < 1) { rc = fail(VELO_ERR_CUDA, "occupancy query failed"); break; }
-      h->ctas[c] = per_sm * h->n_sm;
+      const int n = h->n_classes++;
+      h->caps[n] = c;
+      h->per_sm[n] = per_sm;
+      h->ctas[n] = per_sm * h->n_sm;
+      prev_maxh = c.maxh;
     }
     if (rc) break;
+    e = track_set_smem_limit(h->threads, (int)h->caps[h->n_classes - 1].smem);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e)); break; }
+    for (int k = 0; k < h->n_classes && rc == VELO_OK; ++k) {
+      e = cudaStreamCreateWithFlags(&h->cls_stream[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[k], cudaEventDisableTiming);
+      if (e != cudaSuccess) rc = fail(VELO_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
+    }
+    if (rc) break;
+    e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); break; }
     ArenaPlan a = plan_arena(h->cfg);
     e = cudaMalloc(&h->arena, a.total);
     if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", a.total, cudaGetErrorString(e)); h->arena = nullptr; break; }
@@ -222,8 +250,12 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     WorkView& w = h->wk;
     w.cnt = h->d_cnt;
     w.rec = (EventRec*)(base + a.rec);
-    w.queue[0] = (uint32_t*)(base + a.q0);
-    w.queue[1] = (uint32_t*)(base + a.q1);
+    for (int k = 0; k < kQueues; ++k) w.queue[k] = (uint32_t*)(base + a.q[k]);
+    w.n_classes = h->n_classes;
+    for (int k = 0; k < h->n_classes; ++k) w.class_maxh[k] = h->caps[k].maxh;
+    w.prov = (float2*)(base + a.prov);
+    w.prov_key = (h->cfg.flags & VELO_CFG_CLUSTERS) ? (uint16_t*)(base + a.pkey) : nullptr;
+    w.ev_cbase = (uint16_t*)(base + a.cbase);
     w.tr_state = (float*)(base + a.st);
     w.tr_nhits = (uint16_t*)(base + a.nh);
     w.tr_hitoff = (uint32_t*)(base + a.ho);
@@ -258,6 +290,11 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
 
 void velo_destroy(velo_handle* h) {
   if (!h) return;
+  for (int k = 0; k < kMaxClasses; ++k) {
+    if (h->cls_stream[k]) cudaStreamDestroy(h->cls_stream[k]);
+    if (h->join[k]) cudaEventDestroy(h->join[k]);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
   if (h->h_cnt) cudaFreeHost(h->h_cnt);
@@ -269,13 +306,15 @@ void velo_destroy(velo_handle* h) {
 
 int velo_describe(const velo_handle* h, char* buf, size_t n) {
   if (!h || !buf || n == 0) return fail(VELO_ERR_INPUT, "velo_describe: null argument");
-  snprintf(buf, n,
-           "{\"sms\": %d, \"arena_bytes\": %zu, \"classes\": ["
-           "{\"threads\": %d, \"ctas\": %d, \"smem\": %u, \"max_pixels\": %u, \"max_tracks\": %u, \"max_chain\": %u}, "
-           "{\"threads\": %d, \"ctas\": %d, \"smem\": %u, \"max_pixels\": %u, \"max_tracks\": %u, \"max_chain\": %u}]}",
-           h->n_sm, h->arena_bytes, h->threads[0], h->ctas[0], h->caps[0].smem, h->caps[0].maxp, h->caps[0].maxt,
-           h->caps[0].maxch, h->threads[1], h->ctas[1], h->caps[1].smem, h->caps[1].maxp, h->caps[1].maxt,
-           h->caps[1].maxch);
+  int w = snprintf(buf, n, "{\"sms\": %d, \"arena_bytes\": %zu, \"cluster\": {\"threads\": %d, \"smem\": %u}, \"classes\": [",
+                   h->n_sm, h->arena_bytes, h->cl_threads, cluster_smem_bytes(h->cl_threads));
+  for (int k = 0; k < h->n_classes && w > 0 && (size_t)w < n; ++k)
+    w += snprintf(buf + w, n - w,
+                  "%s{\"threads\": %d, \"ctas_per_sm\": %d, \"ctas\": %d, \"smem\": %u, \"max_hits\": %u, "
+                  "\"max_tracks\": %u, \"max_chain\": %u}",
+                  k ? ", " : "", h->threads, h->per_sm[k], h->ctas[k], h->caps[k].smem, h->caps[k].maxh,
+                  h->caps[k].maxt, h->caps[k].maxch);
+  if (w > 0 && (size_t)w < n) snprintf(buf + w, n - w, "]}");
   return VELO_OK;
 }
 
@@ -288,10 +327,12 @@ int velo_set_timing(velo_handle* h, int on) {
 int velo_get_stats(velo_handle* h, velo_stats* out) {
   if (!h || !out) return fail(VELO_ERR_INPUT, "velo_get_stats: null argument");
   if (!h->timing) return fail(VELO_ERR_STATE, "velo_get_stats: timing is off (velo_set_timing)");
-  CUDA_TRY(cudaEventSynchronize(h->ev[5]));
-  for (int k = 0; k < 5; ++k) CUDA_TRY(cudaEventElapsedTime(&out->ms[k], h->ev[k], h->ev[k + 1]));
+  CUDA_TRY(cudaEventSynchronize(h->ev[4]));
+  for (int k = 0; k < 4; ++k) CUDA_TRY(cudaEventElapsedTime(&out->ms[k], h->ev[k], h->ev[k + 1]));
+  CUDA_TRY(cudaEventElapsedTime(&out->ms[4], h->ev[0], h->ev[4]));
   const Counters& c = *h->h_cnt;
-  for (int k = 0; k < 2; ++k) {
+  out->n_classes = (uint32_t)h->n_classes;
+  for (int k = 0; k < kMaxClasses; ++k) {
     out->events[k] = c.cls_events[k];
     out->tracks[k] = c.cls_tracks[k];
     out->hits[k] = c.cls_hits[k];
@@ -333,16 +374,26 @@ int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_outpu
   const bool tm = h->timing;
   CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
   if (tm) CUDA_TRY(cudaEventRecord(h->ev[0], st));
-  CUDA_TRY(launch_prep(ev, wk, h->caps[0], h->geo.n_sensors, h->cfg.max_pixels, st));
+  CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, st));
   if (tm) CUDA_TRY(cudaEventRecord(h->ev[1], st));
-  if (E) CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[0], 0, h->threads[0], h->ctas[0], st));
+  if (E) {
+    // tracking classes run concurrently, largest plans first
+    CUDA_TRY(cudaEventRecord(h->fork, st));
+    for (int k = h->n_classes - 1; k >= 0; --k) {
+      CUDA_TRY(cudaStreamWaitEvent(h->cls_stream[k], h->fork, 0));
+      CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], h->cls_stream[k]));
+      CUDA_TRY(cudaEventRecord(h->join[k], h->cls_stream[k]));
+    }
+    for (int k = 0; k < h->n_classes; ++k) CUDA_TRY(cudaStreamWaitEvent(st, h->join[k], 0));
+    // events that ran out of track storage in their class: largest plan
+    const int big = h->n_classes - 1;
+    CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[big], big, kRetryQueue, h->threads, h->ctas[big], st));
+  }
   if (tm) CUDA_TRY(cudaEventRecord(h->ev[2], st));
-  if (E) CUDA_TRY(launch_reco(h->d_geo, h->par, ev, wk, h->caps[1], 1, h->threads[1], h->ctas[1], st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[3], st));
   CUDA_TRY(launch_scan(E, wk, *out, st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[4], st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[3], st));
   CUDA_TRY(launch_emit(E, wk, *out, st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[5], st));
+  if (tm) CUDA_TRY(cudaEventRecord(h->ev[4], st));
   CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   if (tm) CUDA_TRY(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   return VELO_OK;

@@ -1,0 +1,402 @@
+// Clustering kernel: raw pixels -> hits (paper section 2.3.1: clusters are
+// the connected components of the fired pixels of a sensor; the raw input is
+// segmented by readout unit, so sensors are decoded in parallel, section 2.3).
+//
+// One CTA per event; warps take sensors from a per-event counter.  A sensor
+// of at most 64 pixels is clustered in registers (one or two pixels per
+// lane); a larger one is staged in the warp's shared-memory slice and joined
+// by union-find.  Every cluster becomes a hit at a provisional position (the
+// sensor's pixel offset + the cluster's rank by smallest pixel key), which
+// orders hits exactly like their canonical ids; the per-sensor canonical
+// bases and the event's hit count go to global memory, and the event is
+// queued for the tracking-kernel class whose shared-memory plan holds it.
+#include <stdint.h>
+
+#include "velo_device.cuh"
+
+namespace velo {
+
+constexpr int kClusterThreads = 256;
+constexpr uint32_t kWarpStage = 1000;           // raw pixels a warp can stage for one large sensor
+constexpr uint32_t kAccBytes = 8 * 64;          // per-warp packed accumulators
+constexpr uint32_t kWarpSlice = kAccBytes + 6 * kWarpStage;
+
+struct ClusterLayout {
+  uint32_t soff, ccnt, misc, scan, warps, total;
+};
+
+__host__ __device__ inline uint32_t c_align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline ClusterLayout cluster_layout(int n_threads) {
+  ClusterLayout L;
+  uint32_t o = 0;
+  L.soff = o; o = c_align16(o + 4 * (kMaxSensors + 1));
+  L.ccnt = o; o = c_align16(o + 4 * (kMaxSensors + 1));
+  L.misc = o; o = c_align16(o + 4 * 32);
+  L.scan = o; o = c_align16(o + 4 * 32);
+  L.warps = o; o = c_align16(o + kWarpSlice * (uint32_t)(n_threads / 32));
+  L.total = o;
+  return L;
+}
+
+uint32_t cluster_smem_bytes(int n_threads) { return cluster_layout(n_threads).total; }
+
+struct SensorGeo {
+  float ox, oy, cdx, cdy, rdx, rdy, pitch;
+};
+
+__device__ __forceinline__ SensorGeo sensor_geo(const DevGeometry* __restrict__ geo, int s) {
+  return SensorGeo{geo->ox[s], geo->oy[s], geo->cdx[s], geo->cdy[s], geo->rdx[s], geo->rdy[s], geo->pitch};
+}
+
+struct HitOut {
+  float2* prov;        // event's provisional hit positions
+  uint16_t* key;       // smallest pixel key per hit, or null
+};
+
+// Centroid of the pixel centres, mapped to the global frame (evaluated left
+// to right, no contraction); written at provisional position p.
+__device__ __forceinline__ void store_cluster(const HitOut& out, const SensorGeo& g, uint32_t p, uint32_t key16,
+                                              uint32_t cnt, uint32_t sc, uint32_t sr) {
+  const float lx = fmul(fadd(fdiv((float)sc, (float)cnt), 0.5f), g.pitch);
+  const float ly = fmul(fadd(fdiv((float)sr, (float)cnt), 0.5f), g.pitch);
+  const float x = fadd(fadd(g.ox, fmul(g.cdx, lx)), fmul(g.rdx, ly));
+  const float y = fadd(fadd(g.oy, fmul(g.cdy, lx)), fmul(g.rdy, ly));
+  out.prov[p] = make_float2(x, y);
+  if (out.key) out.key[p] = (uint16_t)key16;
+}
+
+// Value held at sorted position q (element q lives in lane q % 32, register q / 32).
+template <int R>
+__device__ __forceinline__ uint32_t warp_fetch(const uint32_t (&v)[R], uint32_t q) {
+  uint32_t x = __shfl_sync(kFull, v[0], q & 31);
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    const uint32_t y = __shfl_sync(kFull, v[r], q & 31);
+    if ((q >> 5) == (uint32_t)r) x = y;
+  }
+  return x;
+}
+
+// Sensors of at most 32 * R pixels (R <= 2), R per lane, in registers:
+//   - bitonic sort of the keys c * 512 + r (the gap of 256 between columns
+//     keeps a column wrap from looking adjacent; invalid pixels sort last);
+//   - a repeated pixel is the one equal to its sorted predecessor;
+//   - 8-neighbours differ by 1, 511, 512 or 513: a short scan forward and
+//     backward over the sorted keys finds them;
+//   - component label = smallest sorted position, propagated over the
+//     neighbour masks until stable (so the root is the smallest key);
+//   - member sums through one packed 64-bit shared-memory add per pixel;
+//     a root's rank among the sensor's roots is a population count.
+template <int R>
+__device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
+                                       uint32_t a, uint32_t n, int ncols, int nrows, const SensorGeo& g,
+                                       const HitOut& out, unsigned long long* acc, bool& bad) {
+  constexpr uint32_t NE = 32 * R;
+  static_assert(R == 1 || R == 2, "positions must fit a 64-bit mask");
+  const int lane = threadIdx.x & 31;
+  uint32_t k[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t idx = lane + 32 * r;
+    k[r] = kInv;
+    if (idx < n) {
+      const uint32_t c = col[a + idx], w = row[a + idx];
+      if (c < (uint32_t)ncols && w < (uint32_t)nrows) k[r] = (c << 9) | w;
+      else bad = true;
+    }
+  }
+  // bitonic sort over element index e = lane + 32 r
+#pragma unroll
+  for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
+#pragma unroll
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int rp = r ^ (int)(j >> 5);
+          if (rp > r) {
+            const uint32_t e = lane + 32u * r;
+            const bool up = (e & kk) == 0;
+            const uint32_t lo = min(k[r], k[rp]), hi = max(k[r], k[rp]);
+            k[r] = up ? lo : hi;
+            k[rp] = up ? hi : lo;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t o = __shfl_xor_sync(kFull, k[r], j);
+          const uint32_t e = lane + 32u * r;
+          const bool up = (e & kk) == 0, lower = (e & j) == 0;
+          k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
+        }
+      }
+    }
+  }
+  // repeated pixels; valid-position mask
+  uint64_t vm = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t e = lane + 32u * r;
+    const uint32_t prev = warp_fetch<R>(k, (e + NE - 1) % NE);
+    const bool ok = k[r] != kInv && !(e > 0 && prev == k[r]);
+    vm |= (uint64_t)__ballot_sync(kFull, ok) << (32 * r);
+  }
+  bool valid[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) valid[r] = (vm >> (lane + 32 * r)) & 1ull;
+  // neighbour masks (positions), scanning outward until out of reach
+  uint64_t nb[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) nb[r] = 0;
+  for (uint32_t d = 1; d < NE; ++d) {
+    bool reach = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t e = lane + 32u * r;
+      const uint32_t qf = e + d, qb = e - d;  // qb wraps when e < d
+      const uint32_t kf = warp_fetch<R>(k, qf % NE), kb = warp_fetch<R>(k, qb % NE);
+      if (!valid[r]) continue;
+      if (qf < NE && kf != kInv && kf - k[r] <= 513u) {
+        reach = true;
+        const uint32_t dl = kf - k[r];
+        if (dl == 1u || dl - 511u <= 2u) nb[r] |= 1ull << qf;
+      }
+      if (e >= d && k[r] - kb <= 513u) {
+        reach = true;
+        const uint32_t dl = k[r] - kb;
+        if (dl == 1u || dl - 511u <= 2u) nb[r] |= 1ull << qb;
+      }
+    }
+    if (!__any_sync(kFull, reach)) break;
+  }
+  uint32_t lab[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    nb[r] &= vm;
+    lab[r] = lane + 32u * r;
+  }
+  // propagate the smallest position over the neighbour masks
+  while (true) {
+    bool ch = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      uint64_t bits = nb[r];
+      const uint32_t cnt = __reduce_max_sync(kFull, (uint32_t)__popcll(bits));
+      for (uint32_t it = 0; it < cnt; ++it) {
+        const uint32_t q = bits ? (uint32_t)(__ffsll((long long)bits) - 1) : (lane + 32u * r);
+        bits &= bits - 1;
+        const uint32_t lq = warp_fetch<R>(lab, q);
+        if (lq < lab[r]) { lab[r] = lq; ch = true; }
+      }
+    }
+    if (!__any_sync(kFull, ch)) break;
+  }
+  // member sums: count << 56 | sum(col) << 28 | sum(row), accumulated at the root
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[lane + 32 * r] = 0ull;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (valid[r])
+      atomicAdd(&acc[lab[r]], (1ull << 56) | ((unsigned long long)(k[r] >> 9) << 28) | (k[r] & 511u));
+  __syncwarp();
+  uint32_t nroot = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t e = lane + 32u * r;
+    const bool root = valid[r] && lab[r] == e;
+    const uint32_t rm = __ballot_sync(kFull, root);
+    const uint32_t rank = nroot + __popc(rm & ((1u << lane) - 1u));
+    nroot += __popc(rm);
+    if (root) {
+      const unsigned long long v = acc[e];
+      const uint32_t key16 = ((k[r] >> 9) << 8) | (k[r] & 255u);
+      store_cluster(out, g, a + rank, key16, (uint32_t)(v >> 56), (uint32_t)((v >> 28) & 0xFFFFFFFull),
+                    (uint32_t)(v & 0xFFFFFFFull));
+    }
+  }
+  __syncwarp();
+  return nroot;
+}
+
+// lock-free union-find on local indices; the root with the larger pixel key
+// is hooked under the root with the smaller key, so roots end at the
+// component's smallest key (parent pointers always lead to smaller keys)
+__device__ __forceinline__ int uf_find(const volatile uint16_t* par, int x) {
+  int p;
+  while ((p = par[x]) != x) x = p;
+  return x;
+}
+__device__ void uf_unite(uint16_t* par, const uint32_t* pk, int x, int y) {
+  const volatile uint16_t* vp = par;
+  while (true) {
+    x = uf_find(vp, x);
+    y = uf_find(vp, y);
+    if (x == y) return;
+    if ((pk[x] & 0xFFFFu) > (pk[y] & 0xFFFFu)) { const int t = x; x = y; y = t; }
+    const unsigned short old = atomicCAS((unsigned short*)&par[y], (unsigned short)y, (unsigned short)x);
+    if (old == (unsigned short)y) return;
+  }
+}
+
+// Larger sensors (n <= kWarpStage, 1000 raw pixels): pixels staged in the warp's slice,
+// repeated pixels dropped, 8-neighbours joined by union-find, roots ranked.
+__device__ uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
+                                        uint32_t a, uint32_t n, int ncols, int nrows, const SensorGeo& g,
+                                        const HitOut& out, uint32_t* k_, uint16_t* p_, bool& bad) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t c = col[a + i], w = row[a + i];
+    const bool ok = c < (uint32_t)ncols && w < (uint32_t)nrows;
+    k_[i] = ok ? ((c << 8) | w) : kInv;
+    bad |= !ok;
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t k = k_[i];
+    bool ign = (k >> 31) != 0;
+    for (uint32_t j = 0; j < i && !ign; ++j) ign = (k_[j] == k);
+    p_[i] = ign ? (uint16_t)kNone16 : (uint16_t)i;
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32)
+    if (p_[i] == kNone16) k_[i] |= 0x80000000u;
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t ki = k_[i];
+    if (ki >> 31) continue;
+    const int ci = (int)(ki >> 8), ri = (int)(ki & 255u);
+    for (uint32_t j = i + 1; j < n; ++j) {
+      const uint32_t kj = k_[j];
+      if (kj >> 31) continue;
+      const int dc = (int)(kj >> 8) - ci, dr = (int)(kj & 255u) - ri;
+      if (dc >= -1 && dc <= 1 && dr >= -1 && dr <= 1) uf_unite(p_, k_, (int)i, (int)j);
+    }
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < n; i += 32)
+    if (!(k_[i] >> 31)) p_[i] = (uint16_t)uf_find(p_, (int)i);
+  __syncwarp();
+  uint32_t nroot = 0;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t ki = k_[i];
+    if ((ki >> 31) || p_[i] != i) continue;
+    const uint32_t key = ki & 0xFFFFu;
+    uint32_t cnt = 0, sc = 0, sr = 0, rank = 0;
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t kj = k_[j];
+      if (kj >> 31) continue;
+      const uint32_t pj = p_[j];
+      if (pj == i) { cnt++; sc += kj >> 8; sr += kj & 255u; }
+      if (pj == j && (kj & 0xFFFFu) < key) rank++;
+    }
+    store_cluster(out, g, a + rank, key, cnt, sc, sr);
+    nroot++;
+  }
+  nroot = __reduce_add_sync(kFull, nroot);
+  __syncwarp();
+  return nroot;
+}
+
+enum { CM_NEXT = 0, CM_STATUS = 1 };
+
+template <int NT>
+__global__ void __launch_bounds__(NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
+                                                     WorkView wk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ClusterLayout L = cluster_layout(NT);
+  uint32_t* s_soff = (uint32_t*)(smem + L.soff);
+  uint32_t* s_cnt = (uint32_t*)(smem + L.ccnt);
+  uint32_t* s_misc = (uint32_t*)(smem + L.misc);
+  uint32_t* s_scan = (uint32_t*)(smem + L.scan);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned char* slice = smem + L.warps + warp * kWarpSlice;
+  unsigned long long* acc = (unsigned long long*)slice;
+  uint32_t* w_pk = (uint32_t*)(slice + kAccBytes);
+  uint16_t* w_par = (uint16_t*)(slice + kAccBytes + 4 * kWarpStage);
+  const int ns = geo->n_sensors, ncols = geo->n_cols, nrows = geo->n_rows;
+
+  for (uint32_t e = blockIdx.x; e < ev.n_events; e += gridDim.x) {
+    __syncthreads();
+    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
+    const uint32_t gbase = so[0];
+    bool badoff = false;
+    for (int s = tid; s <= ns; s += NT) {
+      const uint32_t v = so[s];
+      s_soff[s] = v - gbase;
+      if (s < ns && so[s + 1] < v) badoff = true;
+    }
+    if (tid < 32) s_misc[tid] = 0;
+    if (__syncthreads_or(badoff || (uint64_t)so[ns] > wk.cap_pixels)) {
+      if (tid == 0) {
+        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_BAD_OFFSETS, 0, 0, gbase, 0};
+        atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+      }
+      continue;
+    }
+    const uint16_t* col = ev.col + gbase;
+    const uint16_t* row = ev.row + gbase;
+    const HitOut out{wk.prov + gbase, wk.prov_key ? wk.prov_key + gbase : nullptr};
+    bool bad = false, big = false;
+    while (true) {
+      uint32_t s = 0;
+      if (lane == 0) s = atomicAdd(&s_misc[CM_NEXT], 1u);
+      s = __shfl_sync(kFull, s, 0);
+      if (s >= (uint32_t)ns) break;
+      const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
+      const SensorGeo g = sensor_geo(geo, (int)s);
+      uint32_t nroot;
+      if (n <= 32) nroot = cluster_sensor_reg<1>(col, row, a, n, ncols, nrows, g, out, acc, bad);
+      else if (n <= 64) nroot = cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, out, acc, bad);
+      else if (n <= kWarpStage) nroot = cluster_sensor_smem(col, row, a, n, ncols, nrows, g, out, w_pk, w_par, bad);
+      else { nroot = 0; big = true; }
+      if (lane == 0) s_cnt[s] = nroot;
+    }
+    if (__any_sync(kFull, bad) && lane == 0) atomicOr(&s_misc[CM_STATUS], VELO_EV_BAD_PIXEL);
+    if (__syncthreads_or(big)) {  // a sensor beyond the warp's staging capacity
+      if (tid == 0) {
+        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_OVERFLOW | s_misc[CM_STATUS], 0, 0, gbase, 0};
+        atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+      }
+      continue;
+    }
+    const uint32_t H = block_exscan(s_cnt, (uint32_t)ns, s_scan);
+    uint16_t* cb = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
+    if (H <= 0xFFFFu)
+      for (int s = tid; s <= ns; s += NT) cb[s] = (uint16_t)(s < ns ? s_cnt[s] : H);
+    if (tid == 0) {
+      uint32_t st = s_misc[CM_STATUS];
+      if (st & VELO_EV_BAD_PIXEL) atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+      int cls = 0;
+      while (cls < wk.n_classes && H > wk.class_maxh[cls]) ++cls;
+      if (H > 0xFFFFu || cls >= wk.n_classes) {
+        st |= VELO_EV_OVERFLOW;
+        atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+        wk.rec[e] = EventRec{0, 0, 0, st, 0, 0, gbase, 0};
+      } else {
+        wk.rec[e] = EventRec{0, 0, H, st, 0, 0, gbase, 0};
+        const uint32_t pos = atomicAdd(&wk.cnt->queue_len[cls], 1u);
+        wk.queue[cls][pos] = e;
+      }
+    }
+  }
+}
+
+cudaError_t cluster_set_smem_limit(int n_threads) {
+  if (n_threads != kClusterThreads) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(cluster_kernel<kClusterThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)cluster_smem_bytes(n_threads));
+}
+
+cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, int n_threads,
+                           cudaStream_t st) {
+  if (ev.n_events == 0) return cudaSuccess;
+  if (n_threads != kClusterThreads) return cudaErrorInvalidValue;
+  const unsigned grid = ev.n_events < 65535u * 4 ? ev.n_events : 65535u * 4;
+  cluster_kernel<kClusterThreads><<<grid, kClusterThreads, cluster_smem_bytes(n_threads), st>>>(geo, ev, wk);
+  return cudaGetLastError();
+}
+
+}  // namespace velo

@@ -1,6 +1,4 @@
-// Batch-level kernels around the per-event reconstruction:
-//   prep  -- validates each event's sensor offsets and queues it for the
-//            kernel class whose shared-memory plan holds its pixels;
+// Batch-level kernels after the per-event reconstruction:
 //   scan  -- exclusive scan of the per-event track / hit / cluster counts;
 //   emit  -- copies every event's results from scratch to the caller's
 //            compact, canonically ordered output arrays.
@@ -11,41 +9,6 @@
 #include "velo_internal.cuh"
 
 namespace velo {
-
-// One warp per event: offsets must not decrease; pixels must fit the
-// working storage; events are queued by size class.
-__global__ void prep_kernel(EventsView ev, WorkView wk, uint32_t maxp_small, int ns, uint64_t cap_pixels) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < ev.n_events; e += warps) {
-    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
-    bool bad = false;
-    for (int s = lane; s < ns; s += 32) bad |= so[s + 1] < so[s];
-    bad = __any_sync(0xFFFFFFFFu, bad);
-    if (lane == 0) {
-      const uint32_t p0 = so[0], p1 = so[ns];
-      if (!bad && p1 > cap_pixels) bad = true;
-      if (bad) {
-        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_BAD_OFFSETS, 0, 0, p0, 0};
-        atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
-      } else {
-        const int cls = (p1 - p0) > maxp_small ? 1 : 0;
-        const uint32_t pos = atomicAdd(&wk.cnt->queue_len[cls], 1u);
-        wk.queue[cls][pos] = e;
-      }
-    }
-  }
-}
-
-cudaError_t launch_prep(const EventsView& ev, const WorkView& wk, const Caps& small, int n_sensors,
-                        uint64_t cap_pixels, cudaStream_t st) {
-  if (ev.n_events == 0) return cudaSuccess;
-  const int threads = 256;
-  int blocks = (int)((ev.n_events * 32ull + threads - 1) / threads);
-  if (blocks > 4096) blocks = 4096;
-  prep_kernel<<<blocks, threads, 0, st>>>(ev, wk, small.maxp, n_sensors, cap_pixels);
-  return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // scan: one block; each thread scans a contiguous run of events
@@ -91,8 +54,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t n_events, W
     EventRec r = wk.rec[i];
     out.track_off[i] = bt;
     if (out.cluster_off) out.cluster_off[i] = bc;
-    r.pad = bh;  // output hit base of the event
-    wk.rec[i].pad = bh;
+    wk.rec[i].out_hit_base = bh;
     bt += r.n_tracks; bh += r.n_hits; bc += r.n_clusters;
   }
   if (tid == kScanThreads - 1) {
@@ -123,7 +85,7 @@ cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output
 __global__ void emit_kernel(uint32_t n_events, WorkView wk, velo_output out) {
   for (uint32_t e = blockIdx.x; e < n_events; e += gridDim.x) {
     const EventRec r = wk.rec[e];
-    const uint32_t o0 = out.track_off[e], h0 = r.pad;
+    const uint32_t o0 = out.track_off[e], h0 = r.out_hit_base;
     uint32_t status = r.status;
     const bool fits = (uint64_t)o0 + r.n_tracks <= out.cap_tracks && (uint64_t)h0 + r.n_hits <= out.cap_hits;
     if (fits) {

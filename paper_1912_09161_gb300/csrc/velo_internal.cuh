@@ -13,6 +13,9 @@ constexpr int kSPM = 4;                          // sensors per module
 constexpr int kMaxSensors = kMaxModules * kSPM;  // 256
 constexpr int kNB = 32;                          // phi bins per module
 constexpr uint32_t kNone16 = 0xFFFFu;
+constexpr int kMaxClasses = 4;                   // shared-memory classes of the tracking kernel
+constexpr int kRetryQueue = kMaxClasses;         // events that ran out of storage in their class
+constexpr int kQueues = kMaxClasses + 1;
 constexpr int kMlpIn = 10, kMlpH = 32;
 constexpr int kMlpParams = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1441
 
@@ -35,18 +38,19 @@ struct DevParams {
   float phi_window;  // half-width of the phi window in pseudo-angle units (>= atan(tol))
 };
 
-// Per-event working capacities of one kernel class (shared memory plan).
+// Per-event working capacities of one tracking-kernel class.
 struct Caps {
-  uint32_t maxp;   // pixels (also provisional hit slots)
-  uint32_t maxt;   // tracks
+  uint32_t maxh;   // hits
+  uint32_t maxt;   // track candidates
   uint32_t maxch;  // hit-chain entries
   uint32_t smem;   // bytes of dynamic shared memory
 };
 
-// Per-event record written by the reconstruction kernel.
+// Per-event record: n_clusters and status from the clustering kernel, the
+// rest from the tracking kernel.
 struct EventRec {
   uint32_t n_tracks, n_hits, n_clusters, status;
-  uint32_t track_base, hit_base, pix_base, pad;
+  uint32_t track_base, hit_base, pix_base, out_hit_base;
 };
 
 // Handle-level error bits (device word).
@@ -58,16 +62,16 @@ enum : uint32_t {
 
 // Device counters, reset before every batch.
 struct Counters {
-  uint32_t ticket[2];      // persistent-kernel tickets per class
-  uint32_t queue_len[2];   // events in each class queue
-  uint32_t track_cursor;   // scratch bump allocators
+  uint32_t ticket[kQueues];         // persistent-kernel tickets per queue
+  uint32_t queue_len[kQueues];      // events queued per class, and for retry
+  uint32_t track_cursor;            // scratch bump allocators
   uint32_t hit_cursor;
-  uint32_t error;          // kErr* bits
+  uint32_t error;                   // kErr* bits
   uint32_t pad0;
-  uint32_t cls_events[2];  // events completed per class
-  uint32_t cls_tracks[2];  // tracks written per class
-  uint32_t cls_hits[2];    // track hits written per class
-  unsigned long long cls_pixels[2];  // raw pixels read per class
+  uint32_t cls_events[kMaxClasses];  // events completed per class
+  uint32_t cls_tracks[kMaxClasses];  // tracks written per class
+  uint32_t cls_hits[kMaxClasses];    // track hits written per class
+  unsigned long long cls_pixels[kMaxClasses];  // raw pixels of the completed events
 };
 
 // Device views.
@@ -80,33 +84,45 @@ struct EventsView {
 
 struct WorkView {
   Counters* cnt;
-  EventRec* rec;           // [max_events]
-  uint32_t* queue[2];      // [max_events] each
+  EventRec* rec;                 // [max_events]
+  uint32_t* queue[kQueues];      // [max_events] each: one per class, then the retry queue
+  uint32_t class_maxh[kMaxClasses];
+  int n_classes;
+  // hits from the clustering kernel, at provisional positions (event pixel
+  // base + sensor pixel offset + rank in the sensor)
+  float2* prov;                  // [cap_pixels]
+  uint16_t* prov_key;            // [cap_pixels] smallest pixel key (cluster output only)
+  uint16_t* ev_cbase;            // [max_events][kMaxSensors + 1] canonical id of each sensor's first hit
   // scratch tracks (SoA), bump-allocated per event
-  float* tr_state;         // [VELO_NSTATE][cap_tracks]
-  uint16_t* tr_nhits;      // [cap_tracks]
-  uint32_t* tr_hitoff;     // [cap_tracks] offset of the first hit, relative to the event's hit base
-  uint32_t* tr_hits;       // [cap_hits] event-local canonical ids
+  float* tr_state;               // [VELO_NSTATE][cap_tracks]
+  uint16_t* tr_nhits;            // [cap_tracks]
+  uint32_t* tr_hitoff;           // [cap_tracks] first hit, relative to the event's hit base
+  uint32_t* tr_hits;             // [cap_hits] event-local canonical ids
   uint32_t cap_tracks, cap_hits;
-  // scratch clusters (indexed by global pixel position), may be null
+  // scratch clusters (canonical, at the event's pixel base), may be null
   float* cl_x;
   float* cl_y;
   uint32_t* cl_key;
   uint64_t cap_pixels;
   // classifier weights (bf16 bits) and feature normalisation, may be null
   const uint16_t* mlp_w;
-  const float* mlp_norm;   // [2 * kMlpIn] mean, inverse std
+  const float* mlp_norm;         // [2 * kMlpIn] mean, inverse std
 };
 
-// Kernel launchers (velo_reco.cu / velo_emit.cu).
-Caps make_caps(uint32_t smem_budget, uint32_t n_modules, uint32_t n_threads);
-cudaError_t launch_prep(const EventsView& ev, const WorkView& wk, const Caps& small, int n_sensors,
-                        uint64_t cap_pixels, cudaStream_t st);
-cudaError_t launch_reco(const DevGeometry* geo, const DevParams& par, const EventsView& ev,
-                        const WorkView& wk, const Caps& caps, int cls, int n_threads, int n_ctas,
-                        cudaStream_t st);
-cudaError_t reco_set_smem_limit(int n_threads, int bytes);
-cudaError_t reco_occupancy(int n_threads, int smem, int* blocks_per_sm);
+// Clustering kernel (velo_cluster.cu).
+uint32_t cluster_smem_bytes(int n_threads);
+cudaError_t cluster_set_smem_limit(int n_threads);
+cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, int n_threads,
+                           cudaStream_t st);
+
+// Tracking kernel (velo_track.cu).
+Caps make_caps(uint32_t smem_budget, uint32_t n_modules);
+cudaError_t track_set_smem_limit(int n_threads, int bytes);
+cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm);
+cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
+                         const Caps& caps, int cls, int queue, int n_threads, int n_ctas, cudaStream_t st);
+
+// Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
 cudaError_t launch_emit(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
 

@@ -59,8 +59,8 @@ class velo_config(ctypes.Structure):
 
 
 class velo_stats(ctypes.Structure):
-    _fields_ = [("events", ctypes.c_uint32 * 2), ("tracks", ctypes.c_uint32 * 2), ("hits", ctypes.c_uint32 * 2),
-                ("pixels", ctypes.c_uint64 * 2), ("ms", ctypes.c_float * 5)]
+    _fields_ = [("n_classes", ctypes.c_uint32), ("events", ctypes.c_uint32 * 4), ("tracks", ctypes.c_uint32 * 4),
+                ("hits", ctypes.c_uint32 * 4), ("pixels", ctypes.c_uint64 * 4), ("ms", ctypes.c_float * 5)]
 
 
 class velo_events(ctypes.Structure):
@@ -331,8 +331,9 @@ def velo_set_timing(h, on: bool):
 def velo_get_stats(h) -> dict:
     st = velo_stats()
     _check(load_library(False).velo_get_stats(h, ctypes.byref(st)), "velo_get_stats")
-    return dict(events=list(st.events), tracks=list(st.tracks), hits=list(st.hits), pixels=list(st.pixels),
-                ms=list(st.ms))
+    n = int(st.n_classes)
+    return dict(n_classes=n, events=list(st.events)[:n], tracks=list(st.tracks)[:n], hits=list(st.hits)[:n],
+                pixels=list(st.pixels)[:n], ms=list(st.ms))
 
 
 def velo_describe(h) -> dict:

@@ -94,12 +94,25 @@ def test_edge_cases(V, geom):
     ev2[17] = [(int(c), int(r)) for c, r in rng.integers(0, 40, (600, 2))]
     lists.append(ev2)
     lists.append([[(int(c), int(r))] for c, r in rng.integers(0, 256, (ns, 2))])  # one pixel per sensor
+    ev4 = [[] for _ in range(ns)]                                           # beyond the per-sensor limit
+    ev4[3] = [(int(c), int(r)) for c, r in rng.integers(0, 256, (1200, 2))]
+    lists.append(ev4)
     ev = velo_synth.make_events(lists, ns)
     orc = oracle.reconstruct(geom, ev)
     res = _run(V, geom, ev)
     assert res.event_status[1] & 1 and orc.event_status[1] & 1
-    assert res.event_status[0] == 0 and res.event_status[2] == 0
-    assert_parity(res, orc)
+    assert res.event_status[0] == 0 and res.event_status[2] == 0 and res.event_status[3] == 0
+    # a sensor of more than 1000 raw pixels is a documented capacity limit:
+    # that event alone is flagged and skipped, the others are unaffected
+    assert res.event_status[4] == 4 and res.track_off[5] == res.track_off[4]
+    assert res.cluster_off[5] == res.cluster_off[4]
+    sub = velo_synth.make_events(lists[:4], ns)
+    orc4 = oracle.reconstruct(geom, sub)
+    for e in range(4):
+        assert res.event_tracks(e) == orc4.event_tracks(e)
+        g0, g1 = int(res.cluster_off[e]), int(res.cluster_off[e + 1])
+        o0, o1 = int(orc4.cluster_off[e]), int(orc4.cluster_off[e + 1])
+        assert np.array_equal(res.cl_key[g0:g1], orc4.cl_key[o0:o1])
 
 
 def test_empty_batch(V, geom):
