@@ -132,13 +132,14 @@ def _measured_peak_hbm() -> tuple[float, str]:
 
 
 def _profile_traffic(kernel_src: str) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (its sha256 prefix is recorded in the summary)."""
+    """DRAM bytes per call of the tracking kernel from the committed ncu
+    summary, if it was taken on the current kernel source (its sha256 prefix
+    is recorded in the summary)."""
     try:
         text = open(PROFILE_SUMMARY).read()
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_tr or m_sha.group(1) != sha:
@@ -146,13 +147,21 @@ def _profile_traffic(kernel_src: str) -> float | None:
     return float(m_tr.group(1))
 
 
-def _algorithmic_bytes(stats: dict, n_sensors: int, cls: int) -> float:
-    """Bytes the reconstruction kernel must move for the events it processed:
-    raw pixels (col, row: 4 B each) and sensor offsets (4 B x (n_sensors + 1))
-    in; per track 13 state floats + hit count (2 B) + hit offset (4 B), and
-    4 B per track hit out."""
-    return (4.0 * stats["pixels"][cls] + 4.0 * (n_sensors + 1) * stats["events"][cls]
-            + 58.0 * stats["tracks"][cls] + 4.0 * stats["hits"][cls])
+def _tracking_bytes(stats: dict, n_sensors: int) -> float:
+    """Bytes the tracking kernel must move for one call: per event its hit
+    positions (8 B per hit), canonical sensor bases (2 B x (n_sensors + 1))
+    and sensor offsets (4 B x (n_sensors + 1)) in; per track 13 state floats,
+    hit count (2 B) and hit offset (4 B), and 4 B per track hit out."""
+    ev = sum(stats["events"])
+    return (8.0 * sum(stats["clusters"]) + 6.0 * (n_sensors + 1) * ev
+            + 58.0 * sum(stats["tracks"]) + 4.0 * sum(stats["hits"]))
+
+
+def _step_bytes(n_pixels: int, n_events: int, n_sensors: int, n_tracks: int, n_track_hits: int) -> float:
+    """Algorithmic bytes of one whole call: raw pixels (4 B) and sensor offsets
+    in, track offsets, hit offsets and ids, 13 state floats and ndof out."""
+    return (4.0 * n_pixels + 4.0 * (n_events * n_sensors + 1) + 4.0 * (n_events + 1)
+            + 4.0 * (n_tracks + 1) + 4.0 * n_track_hits + 53.0 * n_tracks)
 
 
 def run_reference(args):
@@ -223,7 +232,7 @@ def run_ours(args):
     if rc != V.velo.VELO_OK:
         raise SystemExit(f"velo_sync_status returned {rc}")
 
-    times, reco_ms, reco_bytes = [], [], []
+    times, reco_ms, reco_bytes, stage_ms = [], [], [], []
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
@@ -237,7 +246,8 @@ def run_ours(args):
             ends[k].record(stream)
             st = rec.stats()
             reco_ms.append(st["ms"][1])
-            reco_bytes.append(_algorithmic_bytes(st, geom.n_sensors, 0))
+            reco_bytes.append(_tracking_bytes(st, geom.n_sensors))
+            stage_ms.append(st["ms"])
         torch.cuda.synchronize(dev)
     _barrier(dist)
     torch.cuda.synchronize(dev)
@@ -252,7 +262,10 @@ def run_ours(args):
     desc = rec.describe()
     peak, peak_kind = _measured_peak_hbm()
     achieved = sum(reco_bytes) / (sum(reco_ms) / 1e3) / 1e9
-    traffic = _profile_traffic(os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", "velo_reco.cu"))
+    traffic = _profile_traffic(os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", "velo_track.cu"))
+    tot = out.totals.cpu().numpy().view(np.uint32)
+    step_bytes = _step_bytes(ev.n_pixels, ev.n_events, geom.n_sensors, int(tot[0]), int(tot[1]))
+    stage = [statistics.mean(x[k] for x in stage_ms) for k in range(4)]
     if rank != 0:
         return 0
     line = {
@@ -263,10 +276,13 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB device write, untimed); inputs 190 MB > L2",
                    "parallelism": f"events sharded over {ws} GPU(s), no collective",
                    "launch": desc, "status": rc},
-        "roofline": {"bound": "hbm", "kernel": "reco_kernel class 0 (two CTAs per SM)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "track_kernel (all shared-memory classes of one call, concurrent on their streams)",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel_ms_per_step": statistics.mean(reco_ms)},
+                     "kernel_ms_per_step": statistics.mean(reco_ms),
+                     "step_frac": step_bytes / (total_s / args.steps) / 1e9 / peak,
+                     "stage_ms": {"cluster": stage[0], "track": stage[1], "scan": stage[2], "emit": stage[3]}},
         "e2e": e2e,
         "gpu_launches": (KERNELS_BASE + len(desc["classes"])) * args.steps,
         "clocks": clocks.summary(),

@@ -184,6 +184,7 @@ typedef struct velo_stats {
   uint32_t events[4];   /* events reconstructed by each class */
   uint32_t tracks[4];   /* tracks written by each class */
   uint32_t hits[4];     /* track hits written by each class */
+  uint32_t clusters[4]; /* hits (clusters) read by each class */
   uint64_t pixels[4];   /* raw pixels of those events */
   float ms[5];          /* device time: clustering, tracking (all classes), scan, emit, whole call */
 } velo_stats;

@@ -336,6 +336,7 @@ int velo_get_stats(velo_handle* h, velo_stats* out) {
     out->events[k] = c.cls_events[k];
     out->tracks[k] = c.cls_tracks[k];
     out->hits[k] = c.cls_hits[k];
+    out->clusters[k] = c.cls_clusters[k];
     out->pixels[k] = c.cls_pixels[k];
   }
   return VELO_OK;

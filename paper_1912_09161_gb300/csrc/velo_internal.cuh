@@ -71,6 +71,7 @@ struct Counters {
   uint32_t cls_events[kMaxClasses];  // events completed per class
   uint32_t cls_tracks[kMaxClasses];  // tracks written per class
   uint32_t cls_hits[kMaxClasses];    // track hits written per class
+  uint32_t cls_clusters[kMaxClasses];  // hits (clusters) read per class
   unsigned long long cls_pixels[kMaxClasses];  // raw pixels of the completed events
 };
 

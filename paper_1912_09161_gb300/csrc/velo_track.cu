@@ -440,6 +440,7 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
       atomicAdd(&wk.cnt->cls_events[cls], 1u);
       atomicAdd(&wk.cnt->cls_tracks[cls], nk);
       atomicAdd(&wk.cnt->cls_hits[cls], nh);
+      atomicAdd(&wk.cnt->cls_clusters[cls], H);
       atomicAdd(&wk.cnt->cls_pixels[cls], (unsigned long long)(ev.sensor_off[(size_t)(e + 1) * ns] - gbase));
     }
     __syncthreads();

@@ -60,7 +60,8 @@ class velo_config(ctypes.Structure):
 
 class velo_stats(ctypes.Structure):
     _fields_ = [("n_classes", ctypes.c_uint32), ("events", ctypes.c_uint32 * 4), ("tracks", ctypes.c_uint32 * 4),
-                ("hits", ctypes.c_uint32 * 4), ("pixels", ctypes.c_uint64 * 4), ("ms", ctypes.c_float * 5)]
+                ("hits", ctypes.c_uint32 * 4), ("clusters", ctypes.c_uint32 * 4), ("pixels", ctypes.c_uint64 * 4),
+                ("ms", ctypes.c_float * 5)]
 
 
 class velo_events(ctypes.Structure):
@@ -333,7 +334,7 @@ def velo_get_stats(h) -> dict:
     _check(load_library(False).velo_get_stats(h, ctypes.byref(st)), "velo_get_stats")
     n = int(st.n_classes)
     return dict(n_classes=n, events=list(st.events)[:n], tracks=list(st.tracks)[:n], hits=list(st.hits)[:n],
-                pixels=list(st.pixels)[:n], ms=list(st.ms))
+                clusters=list(st.clusters)[:n], pixels=list(st.pixels)[:n], ms=list(st.ms))
 
 
 def velo_describe(h) -> dict:
