@@ -199,6 +199,44 @@ int velo_get_stats(velo_handle *h, velo_stats *out);
  * shared memory, per-event capacities; arena bytes) into buf[0, n). */
 int velo_describe(const velo_handle *h, char *buf, size_t n);
 
+/*
+ * Clustering with no device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when
+ * they need hits -- a host framework that owns a fixed device pool and
+ * forbids cudaMalloc after start-up, a real-time loop where an allocation
+ * could synchronize the device or fail, or a plug-in that may not create a
+ * handle (velo_create allocates an arena).  It needs no handle: the
+ * clustering kernel's working memory is a 16 MiB array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Inputs: the geometry (host pointers), a batch of events (device pointers,
+ * as velo_events) of at most 512 events and 1,500,000 pixels, and n_pixels,
+ * the batch's pixel count (sensor_off's last entry); larger batches return
+ * VELO_ERR_NOMEM without running.  Outputs (device pointers, caller-owned):
+ * the canonical cluster list exactly as velo_reconstruct writes it with
+ * cluster output on -- cluster_off [n_events + 1], cl_x, cl_y, cl_key
+ * [cap_clusters] -- plus event_status [n_events] and totals [4] (totals[2] =
+ * clusters needed; totals[3] = error bits).  Enqueued on `stream`; read
+ * errors after a stream synchronization from event_status and totals.
+ *
+ * The first call on a device (with that device current) looks up the
+ * array's device address and sets the kernel's shared-memory limit; make it
+ * before any stream capture.  Every call on a device reuses the same array
+ * and leaves its contents there (each call clears what must start at zero),
+ * so calls whose work overlaps on the GPU race and must be serialized.
+ */
+typedef struct velo_cluster_output {
+  uint32_t cap_clusters;
+  uint32_t *cluster_off;   /* [n_events + 1] */
+  float *cl_x, *cl_y;      /* [cap_clusters] */
+  uint32_t *cl_key;        /* [cap_clusters] sensor << 16 | smallest col*256+row */
+  uint32_t *event_status;  /* [n_events] VELO_EV_* bits */
+  uint32_t *totals;        /* [4] */
+} velo_cluster_output;
+
+int velo_cluster_static(const velo_geometry *geometry, const velo_events *events, uint64_t n_pixels,
+                        const velo_cluster_output *out, void *stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char *velo_last_error(void);
 

@@ -34,6 +34,11 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
+namespace velo {
+// Lets other translation units report through velo_last_error().
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
+}  // namespace velo
+
 struct velo_handle {
   int device = 0;
   int n_sm = 0;

@@ -25,8 +25,8 @@ EV_BAD_PIXEL, EV_BAD_OFFSETS, EV_OVERFLOW, EV_TRUNCATED = 1, 2, 4, 8
 CFG_CLUSTERS = 1
 
 EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
-            "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_last_error",
-            "velo_version")
+            "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_cluster_static",
+            "velo_last_error", "velo_version")
 
 
 class VeloError(RuntimeError):
@@ -62,6 +62,12 @@ class velo_stats(ctypes.Structure):
     _fields_ = [("n_classes", ctypes.c_uint32), ("events", ctypes.c_uint32 * 4), ("tracks", ctypes.c_uint32 * 4),
                 ("hits", ctypes.c_uint32 * 4), ("clusters", ctypes.c_uint32 * 4), ("pixels", ctypes.c_uint64 * 4),
                 ("ms", ctypes.c_float * 5)]
+
+
+class velo_cluster_output(ctypes.Structure):
+    _fields_ = [("cap_clusters", ctypes.c_uint32), ("cluster_off", ctypes.c_void_p), ("cl_x", ctypes.c_void_p),
+                ("cl_y", ctypes.c_void_p), ("cl_key", ctypes.c_void_p), ("event_status", ctypes.c_void_p),
+                ("totals", ctypes.c_void_p)]
 
 
 class velo_events(ctypes.Structure):
@@ -105,6 +111,9 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.velo_get_stats.argtypes = [vp, P(velo_stats)]
     lib.velo_set_timing.restype = ctypes.c_int
     lib.velo_get_stats.restype = ctypes.c_int
+    lib.velo_cluster_static.argtypes = [P(velo_geometry), P(velo_events), ctypes.c_uint64,
+                                        P(velo_cluster_output), vp]
+    lib.velo_cluster_static.restype = ctypes.c_int
     lib.velo_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.velo_describe.restype = ctypes.c_int
     lib.velo_last_error.restype = ctypes.c_char_p
@@ -342,6 +351,20 @@ def velo_describe(h) -> dict:
     buf = ctypes.create_string_buffer(4096)
     _check(load_library(False).velo_describe(h, buf, len(buf)), "velo_describe")
     return json.loads(buf.value.decode())
+
+
+def velo_cluster_static(geometry, events: DeviceEvents, out: "DeviceOutput", stream: int = 0):
+    """Clusters a batch without allocating device memory (see velo.h).
+
+    ``out`` supplies cluster_off, cl_x, cl_y, cl_key, event_status and totals."""
+    lib = load_library()
+    gc, keep = _geometry_c(geometry)
+    oc = velo_cluster_output(out.cap_clusters, _ptr(out.cluster_off), _ptr(out.cl_x), _ptr(out.cl_y),
+                             _ptr(out.cl_key), _ptr(out.event_status), _ptr(out.totals))
+    n_pixels = int(events.col.numel())
+    _check(lib.velo_cluster_static(ctypes.byref(gc), ctypes.byref(events.to_c()), n_pixels, ctypes.byref(oc),
+                                   ctypes.c_void_p(stream)), "velo_cluster_static")
+    del keep
 
 
 def velo_version() -> str:
