@@ -189,6 +189,41 @@ typedef struct velo_stats {
   float ms[5];          /* device time: clustering, tracking (all classes), scan, emit, whole call */
 } velo_stats;
 
+/*
+ * Launch schedule of the tracking kernel (paper section 2.3 maps one event to
+ * one block; the schedule only decides how blocks share the GPU).  Events run
+ * in the smallest shared-memory class that holds their hits; class_mask
+ * selects the classes by CTAs per SM: bit 0 = 8, 1 = 6, 2 = 4, 3 = 3, 4 = 2,
+ * 5 = 1 (always present); at most four classes.  concurrent = 1 runs the
+ * classes on their own streams at once, 0 one after another.  Results are
+ * identical under every schedule.  Default: {256, 0x1C, 1} (4, 3, 2, 1 CTAs per SM).
+ */
+typedef struct velo_schedule {
+  uint32_t track_threads;  /* 128 or 256 threads per tracking CTA */
+  uint32_t class_mask;
+  uint32_t concurrent;
+} velo_schedule;
+
+int velo_set_schedule(velo_handle *h, const velo_schedule *schedule);
+int velo_get_schedule(const velo_handle *h, velo_schedule *schedule);
+
+/*
+ * Times a fixed list of candidate schedules on this batch (a warm-up and two
+ * timed runs each; the outputs are the caller's and are overwritten) and
+ * keeps the fastest; returns it and its time in ms.  Synchronous.
+ */
+int velo_autotune(velo_handle *h, const velo_events *events, const velo_output *out, void *stream,
+                  velo_schedule *best, float *best_ms);
+
+/*
+ * Captures the launch sequence of velo_reconstruct into a CUDA graph per
+ * (events, outputs, stream) descriptor and replays it on later calls with
+ * the same descriptors (up to four are kept; a change of parameters,
+ * schedule or timing recaptures).  Needs a non-default stream; calls on the
+ * legacy stream launch directly.
+ */
+int velo_set_graphs(velo_handle *h, int on);
+
 /* Turns per-kernel timing (CUDA events on the call's stream) on or off. */
 int velo_set_timing(velo_handle *h, int on);
 

@@ -55,11 +55,25 @@ struct velo_handle {
   // clustering kernel
   int cl_threads = 256;
   // tracking-kernel classes (increasing shared-memory plans), each on its stream
+  velo_schedule sched{256, 0x1Cu, 1};  // 4, 3, 2, 1 CTAs per SM (bits over kPerSm), concurrent
   int n_classes = 0;
   Caps caps[kMaxClasses]{};
   int per_sm[kMaxClasses]{};
   int threads = 256;
   int ctas[kMaxClasses]{};
+  int smem_sm = 0, smem_optin = 0;
+  // captured launch sequences, replayed while the call descriptors match
+  bool use_graphs = false;
+  uint64_t version = 1;  // bumps on every change that alters the launch sequence
+  struct GraphEntry {
+    bool valid = false;
+    velo_events ev{};
+    velo_output out{};
+    uint64_t version = 0, last_use = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  } graphs[4];
+  uint64_t graph_clock = 0;
   cudaStream_t cls_stream[kMaxClasses]{};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kMaxClasses]{};
@@ -162,6 +176,139 @@ ArenaPlan plan_arena(const velo_config& c) {
   return a;
 }
 
+// CTAs per SM of the candidate classes; a schedule's class_mask selects
+// from this list (at most kMaxClasses; one CTA per SM is always included).
+constexpr int kPerSm[6] = {8, 6, 4, 3, 2, 1};
+
+int build_classes(velo_handle* h, const velo_schedule& sc) {
+  if (sc.track_threads != 128 && sc.track_threads != 256)
+    return fail(VELO_ERR_INPUT, "schedule: track_threads must be 128 or 256");
+  const int threads = (int)sc.track_threads;
+  Caps caps[kMaxClasses]{};
+  int per_sm[kMaxClasses]{}, n = 0;
+  uint32_t prev_maxh = 0;
+  const uint32_t mask = sc.class_mask | (1u << 5);
+  for (int i = 0; i < 6; ++i) {
+    if (!((mask >> i) & 1u)) continue;
+    uint32_t budget = (uint32_t)(h->smem_sm / kPerSm[i]) - 1024u;
+    if (budget > (uint32_t)h->smem_optin) budget = (uint32_t)h->smem_optin;
+    const Caps c = make_caps(budget, (uint32_t)h->geo.n_modules);
+    if (c.maxh <= prev_maxh) continue;
+    cudaError_t e = track_set_smem_limit(threads, (int)c.smem);
+    if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e));
+    int occ = 0;
+    e = track_occupancy(threads, (int)c.smem, &occ);
+    if (e != cudaSuccess || occ < 1) return fail(VELO_ERR_CUDA, "occupancy query failed");
+    if (n == kMaxClasses) return fail(VELO_ERR_INPUT, "schedule: at most %d classes", kMaxClasses);
+    caps[n] = c;
+    per_sm[n] = occ < kPerSm[i] ? occ : kPerSm[i];
+    ++n;
+    prev_maxh = c.maxh;
+  }
+  if (n == 0) return fail(VELO_ERR_INPUT, "schedule: no class");
+  cudaError_t e = track_set_smem_limit(threads, (int)caps[n - 1].smem);
+  if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e));
+  h->sched = sc;
+  h->threads = threads;
+  h->n_classes = n;
+  for (int k = 0; k < kMaxClasses; ++k) {
+    h->caps[k] = k < n ? caps[k] : Caps{};
+    h->per_sm[k] = k < n ? per_sm[k] : 0;
+    h->ctas[k] = k < n ? per_sm[k] * h->n_sm : 0;
+    h->wk.class_maxh[k] = k < n ? caps[k].maxh : 0;
+  }
+  h->wk.n_classes = n;
+  h->version++;
+  return VELO_OK;
+}
+
+// The launch sequence of one call: counters, clustering, tracking classes
+// (concurrent on their streams, largest plans first, or one after another
+// on the caller's stream), the retry pass, scan and emit.
+// Timing events are recorded as external events so that a captured graph
+// records them too.
+int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo_output& out, cudaStream_t st) {
+  const uint32_t E = ev.n_events;
+  const bool tm = h->timing;
+  CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
+  CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, st));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
+  if (E) {
+    if (h->sched.concurrent) {
+      CUDA_TRY(cudaEventRecord(h->fork, st));
+      for (int k = h->n_classes - 1; k >= 0; --k) {
+        CUDA_TRY(cudaStreamWaitEvent(h->cls_stream[k], h->fork, 0));
+        CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], h->cls_stream[k]));
+        CUDA_TRY(cudaEventRecord(h->join[k], h->cls_stream[k]));
+      }
+      for (int k = 0; k < h->n_classes; ++k) CUDA_TRY(cudaStreamWaitEvent(st, h->join[k], 0));
+    } else {
+      for (int k = h->n_classes - 1; k >= 0; --k)
+        CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], st));
+    }
+    // events that ran out of track storage in their class: largest plan
+    const int big = h->n_classes - 1;
+    CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[big], big, kRetryQueue, h->threads, h->ctas[big], st));
+  }
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  CUDA_TRY(launch_scan(E, wk, out, st));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
+  CUDA_TRY(launch_emit(E, wk, out, st));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  if (tm) CUDA_TRY(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+  return VELO_OK;
+}
+
+void drop_graphs(velo_handle* h) {
+  for (auto& g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = velo_handle::GraphEntry{};
+  }
+}
+
+// Replays the captured sequence for these descriptors, capturing it first
+// if needed (capture needs a non-default stream).
+int enqueue_graph(velo_handle* h, const velo_events& events, const velo_output& out, const EventsView& ev,
+                  const WorkView& wk, cudaStream_t st) {
+  velo_handle::GraphEntry* hit = nullptr;
+  for (auto& g : h->graphs)
+    if (g.valid && g.version == h->version && g.stream == st && !memcmp(&g.ev, &events, sizeof(events)) &&
+        !memcmp(&g.out, &out, sizeof(out)))
+      hit = &g;
+  if (!hit) {
+    velo_handle::GraphEntry* slot = &h->graphs[0];
+    for (auto& g : h->graphs)
+      if (!g.valid || g.last_use < slot->last_use) slot = &g;
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    *slot = velo_handle::GraphEntry{};
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue(h, ev, wk, out, st);
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    if (rc != VELO_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    slot->valid = true;
+    slot->ev = events;
+    slot->out = out;
+    slot->version = h->version;
+    slot->stream = st;
+    slot->exec = exec;
+    hit = slot;
+  }
+  hit->last_use = ++h->graph_clock;
+  CUDA_TRY(cudaGraphLaunch(hit->exec, st));
+  return VELO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -211,33 +358,11 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     int smem_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
-    // Tracking classes: 4, 3, 2 and 1 CTAs per SM, each with the largest
-    // plan that fits its share of shared memory; an event goes to the
-    // smallest class that holds its hits.
     e = cluster_set_smem_limit(h->cl_threads);
     if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(cluster): %s", cudaGetErrorString(e)); break; }
-    const int per_sm_try[kMaxClasses] = {4, 3, 2, 1};
-    uint32_t prev_maxh = 0;
+    h->smem_sm = smem_sm;
+    h->smem_optin = smem_optin;
     for (int k = 0; k < kMaxClasses && rc == VELO_OK; ++k) {
-      uint32_t budget = (uint32_t)(smem_sm / per_sm_try[k]) - 1024u;
-      if (budget > (uint32_t)smem_optin) budget = (uint32_t)smem_optin;
-      const Caps c = make_caps(budget, (uint32_t)g.n_modules);
-      if (c.maxh <= prev_maxh) continue;
-      e = track_set_smem_limit(h->threads, (int)c.smem);
-      if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e)); break; }
-      int per_sm = 0;
-      e = track_occupancy(h->threads, (int)c.smem, &per_sm);
-      if (e != cudaSuccess || per_sm < 1) { rc = fail(VELO_ERR_CUDA, "occupancy query failed"); break; }
-      const int n = h->n_classes++;
-      h->caps[n] = c;
-      h->per_sm[n] = per_sm;
-      h->ctas[n] = per_sm * h->n_sm;
-      prev_maxh = c.maxh;
-    }
-    if (rc) break;
-    e = track_set_smem_limit(h->threads, (int)h->caps[h->n_classes - 1].smem);
-    if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e)); break; }
-    for (int k = 0; k < h->n_classes && rc == VELO_OK; ++k) {
       e = cudaStreamCreateWithFlags(&h->cls_stream[k], cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join[k], cudaEventDisableTiming);
       if (e != cudaSuccess) rc = fail(VELO_ERR_CUDA, "stream/event creation: %s", cudaGetErrorString(e));
@@ -256,8 +381,6 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     w.cnt = h->d_cnt;
     w.rec = (EventRec*)(base + a.rec);
     for (int k = 0; k < kQueues; ++k) w.queue[k] = (uint32_t*)(base + a.q[k]);
-    w.n_classes = h->n_classes;
-    for (int k = 0; k < h->n_classes; ++k) w.class_maxh[k] = h->caps[k].maxh;
     w.prov = (float2*)(base + a.prov);
     w.prov_key = (h->cfg.flags & VELO_CFG_CLUSTERS) ? (uint16_t*)(base + a.pkey) : nullptr;
     w.ev_cbase = (uint16_t*)(base + a.cbase);
@@ -273,6 +396,8 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
       w.cl_key = (uint32_t*)(base + a.clk);
     }
     w.cap_pixels = h->cfg.max_pixels;
+    rc = build_classes(h, h->sched);
+    if (rc) break;
     e = cudaMemcpy(h->d_geo, &h->geo, sizeof(DevGeometry), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaMemcpy(geometry): %s", cudaGetErrorString(e)); break; }
     e = cudaMallocHost(&h->h_totals, 4 * sizeof(uint32_t));
@@ -295,6 +420,7 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
 
 void velo_destroy(velo_handle* h) {
   if (!h) return;
+  drop_graphs(h);
   for (int k = 0; k < kMaxClasses; ++k) {
     if (h->cls_stream[k]) cudaStreamDestroy(h->cls_stream[k]);
     if (h->join[k]) cudaEventDestroy(h->join[k]);
@@ -311,8 +437,11 @@ void velo_destroy(velo_handle* h) {
 
 int velo_describe(const velo_handle* h, char* buf, size_t n) {
   if (!h || !buf || n == 0) return fail(VELO_ERR_INPUT, "velo_describe: null argument");
-  int w = snprintf(buf, n, "{\"sms\": %d, \"arena_bytes\": %zu, \"cluster\": {\"threads\": %d, \"smem\": %u}, \"classes\": [",
-                   h->n_sm, h->arena_bytes, h->cl_threads, cluster_smem_bytes(h->cl_threads));
+  int w = snprintf(buf, n,
+                   "{\"sms\": %d, \"arena_bytes\": %zu, \"graphs\": %d, \"schedule\": {\"track_threads\": %u, "
+                   "\"class_mask\": %u, \"concurrent\": %u}, \"cluster\": {\"threads\": %d, \"smem\": %u}, \"classes\": [",
+                   h->n_sm, h->arena_bytes, h->use_graphs ? 1 : 0, h->sched.track_threads, h->sched.class_mask,
+                   h->sched.concurrent, h->cl_threads, cluster_smem_bytes(h->cl_threads));
   for (int k = 0; k < h->n_classes && w > 0 && (size_t)w < n; ++k)
     w += snprintf(buf + w, n - w,
                   "%s{\"threads\": %d, \"ctas_per_sm\": %d, \"ctas\": %d, \"smem\": %u, \"max_hits\": %u, "
@@ -326,8 +455,83 @@ int velo_describe(const velo_handle* h, char* buf, size_t n) {
 int velo_set_timing(velo_handle* h, int on) {
   if (!h) return fail(VELO_ERR_INPUT, "velo_set_timing: null handle");
   h->timing = on != 0;
+  h->version++;
   return VELO_OK;
 }
+
+int velo_set_graphs(velo_handle* h, int on) {
+  if (!h) return fail(VELO_ERR_INPUT, "velo_set_graphs: null handle");
+  h->use_graphs = on != 0;
+  if (!h->use_graphs) drop_graphs(h);
+  return VELO_OK;
+}
+
+int velo_set_schedule(velo_handle* h, const velo_schedule* sc) {
+  if (!h || !sc) return fail(VELO_ERR_INPUT, "velo_set_schedule: null argument");
+  const velo_schedule old = h->sched;
+  const int rc = build_classes(h, *sc);
+  if (rc != VELO_OK) build_classes(h, old);
+  return rc;
+}
+
+int velo_get_schedule(const velo_handle* h, velo_schedule* sc) {
+  if (!h || !sc) return fail(VELO_ERR_INPUT, "velo_get_schedule: null argument");
+  *sc = h->sched;
+  return VELO_OK;
+}
+
+int velo_autotune(velo_handle* h, const velo_events* events, const velo_output* out, void* stream,
+                  velo_schedule* best_out, float* best_ms) {
+  if (!h || !events || !out) return fail(VELO_ERR_INPUT, "velo_autotune: null argument");
+  // threads per tracking CTA, classes (bits over 8, 6, 4, 3, 2, 1 CTAs per SM), concurrency
+  //   256 threads: {4,3,2,1} concurrent and in sequence, {4,2,1}, {3,2,1}, {2,1}, {4,1}
+  //   128 threads: {8,4,2,1} concurrent and in sequence, {6,4,2,1}, {8,6,4,1}, {6,3,1}, {4,2,1}
+  static const velo_schedule cand[] = {
+      {256, 0x1Cu, 1}, {256, 0x1Cu, 0}, {256, 0x14u, 1}, {256, 0x18u, 1}, {256, 0x10u, 1}, {256, 0x04u, 1},
+      {128, 0x15u, 1}, {128, 0x15u, 0}, {128, 0x16u, 1}, {128, 0x07u, 1}, {128, 0x0Au, 1}, {128, 0x14u, 1},
+  };
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool graphs = h->use_graphs, timing = h->timing;
+  h->use_graphs = false;
+  h->timing = false;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&t0));
+  CUDA_TRY(cudaEventCreate(&t1));
+  const velo_schedule start = h->sched;
+  velo_schedule best = start;
+  float best_t = 1e30f;
+  int rc = VELO_OK;
+  for (const velo_schedule& c : cand) {
+    if (build_classes(h, c) != VELO_OK) continue;
+    float t = 1e30f;
+    for (int rep = 0; rep < 3 && rc == VELO_OK; ++rep) {
+      if (rep == 0) {  // warm-up
+        rc = velo_reconstruct(h, events, out, stream);
+        continue;
+      }
+      cudaEventRecord(t0, st);
+      rc = velo_reconstruct(h, events, out, stream);
+      cudaEventRecord(t1, st);
+      cudaEventSynchronize(t1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (ms < t) t = ms;
+    }
+    if (rc != VELO_OK) break;
+    if (t < best_t) { best_t = t; best = c; }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  h->use_graphs = graphs;
+  h->timing = timing;
+  const int rc2 = build_classes(h, rc == VELO_OK ? best : start);
+  if (rc != VELO_OK) return rc;
+  if (rc2 != VELO_OK) return rc2;
+  if (best_out) *best_out = best;
+  if (best_ms) *best_ms = best_t;
+  return VELO_OK;
+}
+
 
 int velo_get_stats(velo_handle* h, velo_stats* out) {
   if (!h || !out) return fail(VELO_ERR_INPUT, "velo_get_stats: null argument");
@@ -351,6 +555,7 @@ int velo_set_params(velo_handle* h, const velo_params* params) {
   if (!h) return fail(VELO_ERR_INPUT, "velo_set_params: null handle");
   if (!params_ok(params)) return fail(VELO_ERR_INPUT, "velo_set_params: invalid parameters");
   h->par = to_dev(*params);
+  h->version++;
   return VELO_OK;
 }
 
@@ -377,32 +582,8 @@ int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_outpu
     wk.cl_y = nullptr;
     wk.cl_key = nullptr;
   }
-  const bool tm = h->timing;
-  CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[0], st));
-  CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[1], st));
-  if (E) {
-    // tracking classes run concurrently, largest plans first
-    CUDA_TRY(cudaEventRecord(h->fork, st));
-    for (int k = h->n_classes - 1; k >= 0; --k) {
-      CUDA_TRY(cudaStreamWaitEvent(h->cls_stream[k], h->fork, 0));
-      CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], h->cls_stream[k]));
-      CUDA_TRY(cudaEventRecord(h->join[k], h->cls_stream[k]));
-    }
-    for (int k = 0; k < h->n_classes; ++k) CUDA_TRY(cudaStreamWaitEvent(st, h->join[k], 0));
-    // events that ran out of track storage in their class: largest plan
-    const int big = h->n_classes - 1;
-    CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[big], big, kRetryQueue, h->threads, h->ctas[big], st));
-  }
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[2], st));
-  CUDA_TRY(launch_scan(E, wk, *out, st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[3], st));
-  CUDA_TRY(launch_emit(E, wk, *out, st));
-  if (tm) CUDA_TRY(cudaEventRecord(h->ev[4], st));
-  CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-  if (tm) CUDA_TRY(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
-  return VELO_OK;
+  if (h->use_graphs && st != nullptr) return enqueue_graph(h, *events, *out, ev, wk, st);
+  return enqueue(h, ev, wk, *out, st);
 }
 
 int velo_sync_status(velo_handle* h, void* stream) {

@@ -26,7 +26,8 @@ CFG_CLUSTERS = 1
 
 EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
             "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_cluster_static",
-            "velo_last_error", "velo_version")
+            "velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs", "velo_last_error",
+            "velo_version")
 
 
 class VeloError(RuntimeError):
@@ -62,6 +63,13 @@ class velo_stats(ctypes.Structure):
     _fields_ = [("n_classes", ctypes.c_uint32), ("events", ctypes.c_uint32 * 4), ("tracks", ctypes.c_uint32 * 4),
                 ("hits", ctypes.c_uint32 * 4), ("clusters", ctypes.c_uint32 * 4), ("pixels", ctypes.c_uint64 * 4),
                 ("ms", ctypes.c_float * 5)]
+
+
+class velo_schedule(ctypes.Structure):
+    _fields_ = [("track_threads", ctypes.c_uint32), ("class_mask", ctypes.c_uint32), ("concurrent", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {"track_threads": self.track_threads, "class_mask": self.class_mask, "concurrent": self.concurrent}
 
 
 class velo_cluster_output(ctypes.Structure):
@@ -114,6 +122,12 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.velo_cluster_static.argtypes = [P(velo_geometry), P(velo_events), ctypes.c_uint64,
                                         P(velo_cluster_output), vp]
     lib.velo_cluster_static.restype = ctypes.c_int
+    lib.velo_set_schedule.argtypes = [vp, P(velo_schedule)]
+    lib.velo_get_schedule.argtypes = [vp, P(velo_schedule)]
+    lib.velo_autotune.argtypes = [vp, P(velo_events), P(velo_output), vp, P(velo_schedule), P(ctypes.c_float)]
+    lib.velo_set_graphs.argtypes = [vp, ctypes.c_int]
+    for name in ("velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.velo_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.velo_describe.restype = ctypes.c_int
     lib.velo_last_error.restype = ctypes.c_char_p
@@ -346,6 +360,30 @@ def velo_get_stats(h) -> dict:
                 clusters=list(st.clusters)[:n], pixels=list(st.pixels)[:n], ms=list(st.ms))
 
 
+def velo_set_schedule(h, track_threads: int, class_mask: int, concurrent: int):
+    sc = velo_schedule(track_threads, class_mask, concurrent)
+    _check(load_library(False).velo_set_schedule(h, ctypes.byref(sc)), "velo_set_schedule")
+
+
+def velo_get_schedule(h) -> dict:
+    sc = velo_schedule()
+    _check(load_library(False).velo_get_schedule(h, ctypes.byref(sc)), "velo_get_schedule")
+    return sc.as_dict()
+
+
+def velo_autotune(h, events: "DeviceEvents", out: "DeviceOutput", stream: int = 0) -> tuple[dict, float]:
+    sc = velo_schedule()
+    ms = ctypes.c_float()
+    ec, oc = events.to_c(), out.to_c()
+    _check(load_library(False).velo_autotune(h, ctypes.byref(ec), ctypes.byref(oc), ctypes.c_void_p(stream),
+                                             ctypes.byref(sc), ctypes.byref(ms)), "velo_autotune")
+    return sc.as_dict(), float(ms.value)
+
+
+def velo_set_graphs(h, on: bool):
+    _check(load_library(False).velo_set_graphs(h, 1 if on else 0), "velo_set_graphs")
+
+
 def velo_describe(h) -> dict:
     import json
     buf = ctypes.create_string_buffer(4096)
@@ -396,6 +434,19 @@ class Reconstructor:
 
     def describe(self) -> dict:
         return velo_describe(self.handle)
+
+    def set_schedule(self, track_threads: int, class_mask: int, concurrent: int):
+        velo_set_schedule(self.handle, track_threads, class_mask, concurrent)
+
+    def schedule(self) -> dict:
+        return velo_get_schedule(self.handle)
+
+    def autotune(self, events: "DeviceEvents", out: "DeviceOutput", stream: int = 0) -> tuple[dict, float]:
+        """Picks the fastest launch schedule for batches like this one."""
+        return velo_autotune(self.handle, events, out, stream)
+
+    def set_graphs(self, on: bool = True):
+        velo_set_graphs(self.handle, on)
 
     def set_timing(self, on: bool = True):
         velo_set_timing(self.handle, on)

@@ -1,0 +1,76 @@
+"""Launch schedules, CUDA-graph replay and the autotuner do not change results.
+
+The tracking kernel's shared-memory classes, threads per CTA, concurrency,
+graph capture and the autotuner's choice only decide how events share the GPU;
+every output must be bit-identical and equal to the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import velo_synth
+from parity_util import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULES = [(256, 0x1C, 1), (256, 0x1C, 0), (256, 0x10, 1), (128, 0x15, 1), (128, 0x07, 0), (128, 0x0A, 1)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1912_09161_gb300 as V
+    V.load_library()
+    geom = velo_synth.geometry()
+    # uneven occupancy: pileup uniform in [1, 20] vertices per event
+    ev = velo_synth.generate(velo_synth.config(2, n_events=400))
+    return V, torch, geom, ev
+
+
+def _flat(res):
+    out = [res.track_off, res.hit_off, res.hit_ids, res.states.view(np.uint32), res.ndof, res.event_status]
+    if res.cluster_off is not None:
+        out += [res.cluster_off, res.cl_key, res.cl_x.view(np.uint32)]
+    return out
+
+
+def test_schedules_and_graphs_identical(env):
+    V, torch, geom, ev = env
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, clusters=True)
+    stream = torch.cuda.Stream()
+    d = V.upload_events(ev)
+    ct, ch, cc = V.suggested_caps(ev.n_events, ev.n_pixels)
+    results = []
+    for graphs in (False, True):
+        rec.set_graphs(graphs)
+        for sc in SCHEDULES:
+            rec.set_schedule(*sc)
+            out = V.alloc_output(ev.n_events, ct, ch, cc)
+            for _ in range(2):   # second call replays the captured graph
+                with torch.cuda.stream(stream):
+                    rec.reconstruct(d, out, stream.cuda_stream)
+                assert rec.sync_status(stream.cuda_stream) == V.velo.VELO_OK
+            results.append(out.to_host(ev.n_events))
+    base = _flat(results[0])
+    for r in results[1:]:
+        for a, b in zip(base, _flat(r)):
+            assert np.array_equal(a, b)
+    orc = oracle.reconstruct(geom, ev.subset(0, 60), n_threads=8)
+    assert_parity(results[-1], orc, events_idx=range(60))
+    rec.close()
+
+
+def test_autotuner_keeps_results(env):
+    V, torch, geom, ev = env
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
+    d = V.upload_events(ev)
+    ct, ch, _ = V.suggested_caps(ev.n_events, ev.n_pixels)
+    before = rec.run(d)
+    out = V.alloc_output(ev.n_events, ct, ch, 0)
+    best, ms = rec.autotune(d, out)
+    assert best == rec.schedule() and ms > 0
+    after = rec.run(d)
+    for a, b in zip(_flat(before), _flat(after)):
+        assert np.array_equal(a, b)
+    rec.close()
