@@ -87,8 +87,8 @@ typedef struct velo_params {
   float sigma_meas;       /* hit resolution used by the fit */
   float pt_nominal;       /* transverse momentum assumed for scattering (0.4 GeV) */
   float ms_coeff;         /* slope kick per module crossed: ms_coeff * 1e-3 * sin(theta) / pt_nominal */
-  uint32_t use_mlp;       /* 1: keep candidates by classifier score instead of the plain cuts */
-  float mlp_threshold;    /* keep a candidate when score >= threshold */
+  uint32_t use_mlp;            /* 1: keep candidates by the ghost classifier instead of the plain cuts */
+  float mlp_logit_threshold;   /* keep a candidate when its classifier logit >= this (score = sigmoid) */
 } velo_params;
 
 /* Handle capacities (velo_create).  Zero fields take defaults. */
@@ -150,6 +150,48 @@ void velo_destroy(velo_handle *h);
 
 /* Bytes of device memory a handle with this configuration holds. */
 int velo_required_bytes(const velo_geometry *geometry, const velo_config *config, size_t *bytes);
+
+/*
+ * Ghost-track classifier weights for the handle (the paper has no classifier
+ * of its own; its HLT1 selections use MVA lines, section 2.3.6).  params_bf16:
+ * 1441 BF16 values laid out W1 [32][10], b1 [32], W2 [32][32], b2 [32],
+ * W3 [32], b3; mean / istd: standardisation of the 10 features (chi2/ndof,
+ * hits, first and last module, tx, ty, impact parameter, eta, phi, missed
+ * modules).  Host pointers, copied.  With velo_params.use_mlp = 1 every
+ * candidate is fitted and scored after the search and kept when its logit
+ * reaches mlp_logit_threshold; states row 12 then holds the score.
+ */
+int velo_set_mlp(velo_handle *h, const uint16_t *params_bf16, const float *mean, const float *istd);
+
+/*
+ * Training of the ghost-track classifier on the GPU: BF16 forward with FP32
+ * accumulation, FP32 backward, Adam (lr given per step, betas 0.9 / 0.999,
+ * eps 1e-8) on FP32 master weights; mean binary cross-entropy on the logit.
+ * Steps are deterministic (no atomics), so a run resumes bit for bit from a
+ * checkpoint of (weights, moments, step).  The paper has no counterpart; the
+ * classifier scores candidates of the section 2.3.1 search.
+ *   velo_mlp_create   -- params: 1441 FP32 initial weights (layout as
+ *                        velo_set_mlp), mean / istd: feature standardisation
+ *                        (host); max_batch: largest batch of a step.
+ *   velo_mlp_step     -- one Adam step on a batch: features [n][10] raw,
+ *                        labels [n] in {0, 1} (device pointers), async.
+ *   velo_mlp_gradient -- the batch gradient (1441, host) and mean loss, no
+ *                        update; synchronous (for gradient checks).
+ *   velo_mlp_logits   -- logits [n] (device) of features [n][10] (device).
+ *   velo_mlp_get_state / velo_mlp_set_state -- checkpoint (host arrays).
+ */
+typedef struct velo_mlp_trainer velo_mlp_trainer;
+int velo_mlp_create(const float *params, const float *mean, const float *istd, uint32_t max_batch,
+                    velo_mlp_trainer **out);
+void velo_mlp_destroy(velo_mlp_trainer *t);
+int velo_mlp_step(velo_mlp_trainer *t, const float *features, const float *labels, uint32_t n, float lr,
+                  void *stream);
+int velo_mlp_gradient(velo_mlp_trainer *t, const float *features, const float *labels, uint32_t n, float *grad,
+                      float *loss, void *stream);
+int velo_mlp_logits(velo_mlp_trainer *t, const float *features, uint32_t n, float *logits, void *stream);
+int velo_mlp_get_state(velo_mlp_trainer *t, float *params, uint16_t *params_bf16, float *m1, float *m2,
+                       uint32_t *step);
+int velo_mlp_set_state(velo_mlp_trainer *t, const float *params, const float *m1, const float *m2, uint32_t step);
 
 /* Replaces the method parameters (takes effect at the next call). */
 int velo_set_params(velo_handle *h, const velo_params *params);

@@ -51,6 +51,7 @@ struct velo_handle {
   size_t arena_bytes = 0;
   DevGeometry* d_geo = nullptr;
   Counters* d_cnt = nullptr;
+  char* d_mlp = nullptr;  // classifier weights (bf16), then mean / inverse std at kMlpNormOffset
   WorkView wk{};
   // clustering kernel
   int cl_threads = 256;
@@ -120,7 +121,7 @@ DevParams to_dev(const velo_params& p) {
   d.pt_nominal = p.pt_nominal;
   d.ms_coeff = p.ms_coeff;
   d.use_mlp = p.use_mlp;
-  d.mlp_threshold = p.mlp_threshold;
+  d.mlp_logit_threshold = p.mlp_logit_threshold;
   // The pseudo-angle moves by at most one unit per radian, so a window of
   // atan(tol) plus a margin for rounding covers every phi-compatible hit.
   double w = atan((double)fabsf(p.tan_phi_tol)) + 1e-3;
@@ -150,7 +151,7 @@ velo_config with_defaults(const velo_config* c) {
 }
 
 struct ArenaPlan {
-  size_t geo, cnt, rec, q[kQueues], prov, pkey, cbase, st, nh, ho, hits, clx, cly, clk, total;
+  size_t geo, cnt, mlp, rec, q[kQueues], prov, pkey, cbase, st, nh, ho, hits, clx, cly, clk, total;
 };
 
 ArenaPlan plan_arena(const velo_config& c) {
@@ -158,6 +159,7 @@ ArenaPlan plan_arena(const velo_config& c) {
   size_t o = 0;
   a.geo = o; o = align256(o + sizeof(DevGeometry));
   a.cnt = o; o = align256(o + sizeof(Counters));
+  a.mlp = o; o = align256(o + kMlpNormOffset + 4 * 2 * kMlpIn);
   a.rec = o; o = align256(o + sizeof(EventRec) * c.max_events);
   for (int k = 0; k < kQueues; ++k) { a.q[k] = o; o = align256(o + 4ull * c.max_events); }
   a.prov = o; o = align256(o + 8ull * c.max_pixels);
@@ -379,6 +381,7 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     h->d_cnt = (Counters*)(base + a.cnt);
     WorkView& w = h->wk;
     w.cnt = h->d_cnt;
+    h->d_mlp = base + a.mlp;
     w.rec = (EventRec*)(base + a.rec);
     for (int k = 0; k < kQueues; ++k) w.queue[k] = (uint32_t*)(base + a.q[k]);
     w.prov = (float2*)(base + a.prov);
@@ -455,6 +458,21 @@ int velo_describe(const velo_handle* h, char* buf, size_t n) {
 int velo_set_timing(velo_handle* h, int on) {
   if (!h) return fail(VELO_ERR_INPUT, "velo_set_timing: null handle");
   h->timing = on != 0;
+  h->version++;
+  return VELO_OK;
+}
+
+int velo_set_mlp(velo_handle* h, const uint16_t* params_bf16, const float* mean, const float* istd) {
+  if (!h || !params_bf16 || !mean || !istd) return fail(VELO_ERR_INPUT, "velo_set_mlp: null argument");
+  for (int i = 0; i < kMlpIn; ++i)
+    if (!isfinite(mean[i]) || !isfinite(istd[i])) return fail(VELO_ERR_INPUT, "velo_set_mlp: non-finite normalisation");
+  float norm[2 * kMlpIn];
+  memcpy(norm, mean, sizeof(float) * kMlpIn);
+  memcpy(norm + kMlpIn, istd, sizeof(float) * kMlpIn);
+  CUDA_TRY(cudaMemcpy(h->d_mlp, params_bf16, 2 * kMlpParams, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(h->d_mlp + kMlpNormOffset, norm, sizeof(norm), cudaMemcpyHostToDevice));
+  h->wk.mlp_w = (const uint16_t*)h->d_mlp;
+  h->wk.mlp_norm = (const float*)(h->d_mlp + kMlpNormOffset);
   h->version++;
   return VELO_OK;
 }

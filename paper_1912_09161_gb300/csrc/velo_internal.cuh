@@ -18,6 +18,7 @@ constexpr int kRetryQueue = kMaxClasses;         // events that ran out of stora
 constexpr int kQueues = kMaxClasses + 1;
 constexpr int kMlpIn = 10, kMlpH = 32;
 constexpr int kMlpParams = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1441
+constexpr int kMlpNormOffset = (2 * kMlpParams + 15) & ~15;  // byte offset of the float normalisation
 
 // Device copy of the geometry (in the handle's arena).
 struct DevGeometry {
@@ -34,7 +35,7 @@ struct DevParams {
   uint32_t max_skipped;
   float sigma_meas, pt_nominal, ms_coeff;
   uint32_t use_mlp;
-  float mlp_threshold;
+  float mlp_logit_threshold;  // keep a candidate when its classifier logit >= this
   float phi_window;  // half-width of the phi window in pseudo-angle units (>= atan(tol))
 };
 

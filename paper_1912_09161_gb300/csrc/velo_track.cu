@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "velo_device.cuh"
+#include "velo_mlp.cuh"
 
 namespace velo {
 
@@ -28,7 +29,7 @@ namespace velo {
 // shared-memory plan
 // ---------------------------------------------------------------------------
 struct Layout {
-  uint32_t z, cb, bins, misc, scan;      // fixed part
+  uint32_t z, cb, bins, misc, scan, mlpw, mlpn;  // fixed part (mlpw/mlpn: classifier weights)
   uint32_t hx, hy, sorted, hmod, used;   // per hit
   // track candidates; r0/r1 hold the cached slopes during the rounds and the
   // canonical key / rank afterwards, r2 the hit offsets by rank
@@ -46,6 +47,8 @@ __host__ __device__ inline Layout make_layout(uint32_t maxh, uint32_t maxt, uint
   L.bins = o; o = align16(o + 4 * nm * kNB);
   L.misc = o; o = align16(o + 4 * 32);
   L.scan = o; o = align16(o + 4 * 32);
+  L.mlpw = o; o = align16(o + 2 * kMlpParams);
+  L.mlpn = o; o = align16(o + 4 * 2 * kMlpIn);
   L.hx = o; o = align16(o + 4 * maxh);
   L.hy = o; o = align16(o + 4 * maxh);
   L.sorted = o; o = align16(o + 2 * maxh);
@@ -149,6 +152,119 @@ __device__ void defer_or_fail(const WorkView& wk, int queue, uint32_t e, uint32_
   }
 }
 
+// Hits of a candidate in stored (decreasing module) order, from its chain.
+__device__ __forceinline__ void gather_hits(const uint32_t* chain, uint32_t head, uint32_t n, uint16_t* hl) {
+  uint32_t c = head;
+  for (int k = (int)n - 1; k >= 0; --k) {
+    const uint32_t ent = chain[c];
+    hl[k] = (uint16_t)(ent >> 16);
+    c = ent & 0xFFFFu;
+  }
+}
+
+// Simple Kalman fit (paper section 2.3.1): x and y as two independent
+// (position, slope) filters from the highest-z hit toward lower z, starting
+// from the exact two-hit state; the slope variance grows by the scattering of
+// every module crossed, with the polar angle of the unweighted least-squares
+// line and the constant transverse momentum; the final state goes to the
+// closest approach to the beam axis.  out: x, y, z, tx, ty, c00, c20, c22,
+// c11, c31, c33, chi2.
+__device__ void fit_candidate(const uint16_t* hl, uint32_t n, const float* hx, const float* hy,
+                              const uint8_t* hmod, const float* s_z, float sig2, float kms, float* out) {
+  float sz = 0.0f, sx = 0.0f, sy = 0.0f;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t p = hl[k];
+    sz = fadd(sz, s_z[hmod[p]]);
+    sx = fadd(sx, hx[p]);
+    sy = fadd(sy, hy[p]);
+  }
+  const float fn = (float)n;
+  const float zm = fdiv(sz, fn), xm = fdiv(sx, fn), ym = fdiv(sy, fn);
+  float szz = 0.0f, szx = 0.0f, szy = 0.0f;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t p = hl[k];
+    const float dz = fsub(s_z[hmod[p]], zm);
+    szz = fadd(szz, fmul(dz, dz));
+    szx = fadd(szx, fmul(dz, fsub(hx[p], xm)));
+    szy = fadd(szy, fmul(dz, fsub(hy[p], ym)));
+  }
+  const float tx0 = fdiv(szx, szz), ty0 = fdiv(szy, szz);
+  const float t2 = fadd(fmul(tx0, tx0), fmul(ty0, ty0));
+  const float sin_t = __fsqrt_rn(fdiv(t2, fadd(1.0f, t2)));
+  const float sig_ms = fmul(kms, sin_t);
+  const float qn = fmul(sig_ms, sig_ms);
+  float u[2], tu[2], c00[2], c10[2], c11[2], chi2[2];
+  const uint32_t p0 = hl[0], p1 = hl[1];
+  const int m0 = hmod[p0], m1 = hmod[p1];
+  const float z0 = s_z[m0], z1 = s_z[m1];
+  const float dz1 = fsub(z1, z0);
+  const float dm1 = (float)(m0 - m1);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const float* hv = d ? hy : hx;
+    u[d] = hv[p1];
+    tu[d] = fdiv(fsub(hv[p1], hv[p0]), dz1);
+    c00[d] = sig2;
+    c10[d] = fdiv(sig2, dz1);
+    c11[d] = fdiv(fmul(2.0f, sig2), fmul(dz1, dz1));
+    c11[d] = fadd(c11[d], fmul(dm1, qn));
+    chi2[d] = 0.0f;
+  }
+  int mprev = m1;
+  float zprev = z1;
+  for (uint32_t k = 2; k < n; ++k) {
+    const uint32_t p = hl[k];
+    const int mk = hmod[p];
+    const float zk = s_z[mk];
+    const float dz = fsub(zk, zprev);
+    const float dm = (float)(mprev - mk);
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float mv = d ? hy[p] : hx[p];
+      u[d] = fadd(u[d], fmul(tu[d], dz));
+      const float c10n = fadd(c10[d], fmul(dz, c11[d]));
+      c00[d] = fadd(fadd(c00[d], fmul(dz, c10[d])), fmul(dz, c10n));
+      c10[d] = c10n;
+      c11[d] = fadd(c11[d], fmul(dm, qn));
+      const float rr = fsub(mv, u[d]);
+      const float R = fadd(sig2, c00[d]);
+      chi2[d] = fadd(chi2[d], fdiv(fmul(rr, rr), R));
+      const float k0 = fdiv(c00[d], R), k1 = fdiv(c10[d], R);
+      u[d] = fadd(u[d], fmul(k0, rr));
+      tu[d] = fadd(tu[d], fmul(k1, rr));
+      c11[d] = fsub(c11[d], fmul(k1, c10[d]));
+      c10[d] = fsub(c10[d], fmul(k1, c00[d]));
+      c00[d] = fsub(c00[d], fmul(k0, c00[d]));
+    }
+    mprev = mk;
+    zprev = zk;
+  }
+  // closest approach to the beam axis (section 2.3.1, beamline state)
+  const float tt = fadd(fmul(tu[0], tu[0]), fmul(tu[1], tu[1]));
+  float zbl = zprev;
+  if (tt >= 1e-12f) zbl = fsub(zprev, fdiv(fadd(fmul(u[0], tu[0]), fmul(u[1], tu[1])), tt));
+  const float dzb = fsub(zbl, zprev);
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    u[d] = fadd(u[d], fmul(tu[d], dzb));
+    const float c10n = fadd(c10[d], fmul(dzb, c11[d]));
+    c00[d] = fadd(fadd(c00[d], fmul(dzb, c10[d])), fmul(dzb, c10n));
+    c10[d] = c10n;
+  }
+  out[0] = u[0];
+  out[1] = u[1];
+  out[2] = zbl;
+  out[3] = tu[0];
+  out[4] = tu[1];
+  out[5] = c00[0];
+  out[6] = c10[0];
+  out[7] = c11[0];
+  out[8] = c00[1];
+  out[9] = c10[1];
+  out[10] = c11[1];
+  out[11] = fadd(chi2[0], chi2[1]);
+}
+
 enum Misc { M_EVENT = 0, M_NTR = 1, M_NCH = 2, M_KEPT = 5, M_TBASE = 7, M_HBASE = 8, M_SKIP = 10 };
 
 template <int NT>
@@ -182,6 +298,8 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
   uint32_t* t_rank = (uint32_t*)(smem + L.t_r1);
   uint32_t* t_hoff = (uint32_t*)(smem + L.t_r2);
   uint32_t* chain = (uint32_t*)(smem + L.chain);
+  uint16_t* s_mlpw = (uint16_t*)(smem + L.mlpw);
+  float* s_mlpn = (float*)(smem + L.mlpn);  // mean [10], inverse std [10]
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = NT / 32;
@@ -189,6 +307,11 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
   const float tol = par.tan_phi_tol, win = par.phi_window;
 
   for (int m = tid; m < kMaxModules; m += NT) s_z[m] = m < (int)nm ? geo->module_z[m] : 0.0f;
+  const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
+  if (use_mlp) {
+    for (int k = tid; k < kMlpParams; k += NT) s_mlpw[k] = wk.mlp_w[k];
+    for (int k = tid; k < 2 * kMlpIn; k += NT) s_mlpn[k] = wk.mlp_norm[k];
+  }
 
   while (true) {
     __syncthreads();
@@ -382,28 +505,49 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
 
     // ---- 5. plain cuts, canonical order, fit --------------------------------
     const uint32_t ntr = s_misc[M_NTR];
-    uint32_t* seen1 = used;
-    const uint32_t nwords = (H + 31) / 32;
-    uint32_t* seen2 = used + nwords;
-    for (uint32_t k = tid; k < 2 * nwords; k += NT) seen1[k] = 0;
-    __syncthreads();
-    for (uint32_t t = tid; t < ntr; t += NT) {
-      uint32_t c = t_head[t];
-      while (c != kNone16) {
-        const uint32_t ent = chain[c], h = ent >> 16, bit = 1u << (h & 31);
-        if (atomicOr(&seen1[h >> 5], bit) & bit) atomicOr(&seen2[h >> 5], bit);
-        c = ent & 0xFFFFu;
+    const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
+    const float kms = fdiv(fmul(par.ms_coeff, 0.001f), par.pt_nominal);
+    if (!use_mlp) {
+      // plain cuts: >= 4 hits, or 3 hits with a small seed scatter and no hit
+      // shared with another candidate
+      uint32_t* seen1 = used;
+      const uint32_t nwords = (H + 31) / 32;
+      uint32_t* seen2 = used + nwords;
+      for (uint32_t k = tid; k < 2 * nwords; k += NT) seen1[k] = 0;
+      __syncthreads();
+      for (uint32_t t = tid; t < ntr; t += NT) {
+        uint32_t c = t_head[t];
+        while (c != kNone16) {
+          const uint32_t ent = chain[c], h = ent >> 16, bit = 1u << (h & 31);
+          if (atomicOr(&seen1[h >> 5], bit) & bit) atomicOr(&seen2[h >> 5], bit);
+          c = ent & 0xFFFFu;
+        }
       }
-    }
-    __syncthreads();
-    for (uint32_t t = tid; t < ntr; t += NT) {
-      bool keep = t_n[t] >= 4;
-      if (t_n[t] == 3 && t_seed[t] < par.max_scatter_3hit) {
-        const uint32_t h0 = t_a[t], h1 = t_b[t], h2 = t_last[t];
-        keep = !((seen2[h0 >> 5] >> (h0 & 31)) & 1u) && !((seen2[h1 >> 5] >> (h1 & 31)) & 1u) &&
-               !((seen2[h2 >> 5] >> (h2 & 31)) & 1u);
+      __syncthreads();
+      for (uint32_t t = tid; t < ntr; t += NT) {
+        bool keep = t_n[t] >= 4;
+        if (t_n[t] == 3 && t_seed[t] < par.max_scatter_3hit) {
+          const uint32_t h0 = t_a[t], h1 = t_b[t], h2 = t_last[t];
+          keep = !((seen2[h0 >> 5] >> (h0 & 31)) & 1u) && !((seen2[h1 >> 5] >> (h1 & 31)) & 1u) &&
+                 !((seen2[h2 >> 5] >> (h2 & 31)) & 1u);
+        }
+        t_key[t] = keep ? (((uint32_t)t_a[t] << 16) | t_b[t]) : 0xFFFFFFFFu;
       }
-      t_key[t] = keep ? (((uint32_t)t_a[t] << 16) | t_b[t]) : 0xFFFFFFFFu;
+    } else {
+      // classifier: fit every candidate, keep it when its logit reaches the
+      // threshold; the logit is kept (in the seed-scatter slot) for the score
+      for (uint32_t t = tid; t < ntr; t += NT) {
+        uint16_t hl[kMaxModules];
+        const uint32_t n = t_n[t];
+        gather_hits(chain, t_head[t], n, hl);
+        float st[12];
+        fit_candidate(hl, n, hx, hy, hmod, s_z, sig2, kms, st);
+        float f[kMlpIn];
+        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, hmod[hl[0]], hmod[hl[n - 1]], f);
+        const float logit = mlp_logit(f, s_mlpw, s_mlpn, s_mlpn + kMlpIn);
+        t_seed[t] = logit;
+        t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)t_a[t] << 16) | t_b[t]) : 0xFFFFFFFFu;
+      }
     }
     __syncthreads();
     uint32_t kept_local = 0;
@@ -448,123 +592,22 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
     const uint32_t tb = s_misc[M_TBASE], hb = s_misc[M_HBASE];
 
     // fit: one thread per kept track
-    const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
-    const float kms = fdiv(fmul(par.ms_coeff, 0.001f), par.pt_nominal);
     for (uint32_t t = tid; t < ntr; t += NT) {
       if (t_key[t] == 0xFFFFFFFFu) continue;
       const uint32_t r = t_rank[t], n = t_n[t];
       uint16_t hl[kMaxModules];
-      {
-        uint32_t c = t_head[t];
-        for (int k = (int)n - 1; k >= 0; --k) {
-          const uint32_t ent = chain[c];
-          hl[k] = (uint16_t)(ent >> 16);
-          c = ent & 0xFFFFu;
-        }
-      }
+      gather_hits(chain, t_head[t], n, hl);
       // hit ids (canonical) to scratch
       const uint32_t hoff = t_hoff[r];
-      for (uint32_t k = 0; k < n; ++k) {
-        wk.tr_hits[hb + hoff + k] = hl[k];
-      }
-      // unweighted least-squares slopes (scattering angle only)
-      float sz = 0.0f, sx = 0.0f, sy = 0.0f;
-      for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t p = hl[k];
-        sz = fadd(sz, s_z[hmod[p]]);
-        sx = fadd(sx, hx[p]);
-        sy = fadd(sy, hy[p]);
-      }
-      const float fn = (float)n;
-      const float zm = fdiv(sz, fn), xm = fdiv(sx, fn), ym = fdiv(sy, fn);
-      float szz = 0.0f, szx = 0.0f, szy = 0.0f;
-      for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t p = hl[k];
-        const float dz = fsub(s_z[hmod[p]], zm);
-        szz = fadd(szz, fmul(dz, dz));
-        szx = fadd(szx, fmul(dz, fsub(hx[p], xm)));
-        szy = fadd(szy, fmul(dz, fsub(hy[p], ym)));
-      }
-      const float tx0 = fdiv(szx, szz), ty0 = fdiv(szy, szz);
-      const float t2 = fadd(fmul(tx0, tx0), fmul(ty0, ty0));
-      const float sin_t = __fsqrt_rn(fdiv(t2, fadd(1.0f, t2)));
-      const float sig_ms = fmul(kms, sin_t);
-      const float qn = fmul(sig_ms, sig_ms);
-      // two independent projections, starting from the exact two-hit state
-      float u[2], tu[2], c00[2], c10[2], c11[2], chi2[2];
-      const uint32_t p0 = hl[0], p1 = hl[1];
-      const int m0 = hmod[p0], m1 = hmod[p1];
-      const float z0 = s_z[m0], z1 = s_z[m1];
-      const float dz1 = fsub(z1, z0);
-      const float dm1 = (float)(m0 - m1);
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        const float* hv = d ? hy : hx;
-        u[d] = hv[p1];
-        tu[d] = fdiv(fsub(hv[p1], hv[p0]), dz1);
-        c00[d] = sig2;
-        c10[d] = fdiv(sig2, dz1);
-        c11[d] = fdiv(fmul(2.0f, sig2), fmul(dz1, dz1));
-        c11[d] = fadd(c11[d], fmul(dm1, qn));
-        chi2[d] = 0.0f;
-      }
-      int mprev = m1;
-      float zprev = z1;
-      for (uint32_t k = 2; k < n; ++k) {
-        const uint32_t p = hl[k];
-        const int mk = hmod[p];
-        const float zk = s_z[mk];
-        const float dz = fsub(zk, zprev);
-        const float dm = (float)(mprev - mk);
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          const float mv = d ? hy[p] : hx[p];
-          u[d] = fadd(u[d], fmul(tu[d], dz));
-          const float c10n = fadd(c10[d], fmul(dz, c11[d]));
-          c00[d] = fadd(fadd(c00[d], fmul(dz, c10[d])), fmul(dz, c10n));
-          c10[d] = c10n;
-          c11[d] = fadd(c11[d], fmul(dm, qn));
-          const float rr = fsub(mv, u[d]);
-          const float R = fadd(sig2, c00[d]);
-          chi2[d] = fadd(chi2[d], fdiv(fmul(rr, rr), R));
-          const float k0 = fdiv(c00[d], R), k1 = fdiv(c10[d], R);
-          u[d] = fadd(u[d], fmul(k0, rr));
-          tu[d] = fadd(tu[d], fmul(k1, rr));
-          c11[d] = fsub(c11[d], fmul(k1, c10[d]));
-          c10[d] = fsub(c10[d], fmul(k1, c00[d]));
-          c00[d] = fsub(c00[d], fmul(k0, c00[d]));
-        }
-        mprev = mk;
-        zprev = zk;
-      }
-      // closest approach to the beam axis (section 2.3.1, beamline state)
-      const float tt = fadd(fmul(tu[0], tu[0]), fmul(tu[1], tu[1]));
-      float zbl = zprev;
-      if (tt >= 1e-12f) zbl = fsub(zprev, fdiv(fadd(fmul(u[0], tu[0]), fmul(u[1], tu[1])), tt));
-      const float dzb = fsub(zbl, zprev);
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        u[d] = fadd(u[d], fmul(tu[d], dzb));
-        const float c10n = fadd(c10[d], fmul(dzb, c11[d]));
-        c00[d] = fadd(fadd(c00[d], fmul(dzb, c10[d])), fmul(dzb, c10n));
-        c10[d] = c10n;
-      }
+      for (uint32_t k = 0; k < n; ++k) wk.tr_hits[hb + hoff + k] = hl[k];
+      float st[12];
+      fit_candidate(hl, n, hx, hy, hmod, s_z, sig2, kms, st);
       const size_t o = (size_t)tb + r;
       const size_t cap = wk.cap_tracks;
       float* S = wk.tr_state;
-      S[0 * cap + o] = u[0];
-      S[1 * cap + o] = u[1];
-      S[2 * cap + o] = zbl;
-      S[3 * cap + o] = tu[0];
-      S[4 * cap + o] = tu[1];
-      S[5 * cap + o] = c00[0];
-      S[6 * cap + o] = c10[0];
-      S[7 * cap + o] = c11[0];
-      S[8 * cap + o] = c00[1];
-      S[9 * cap + o] = c10[1];
-      S[10 * cap + o] = c11[1];
-      S[11 * cap + o] = fadd(chi2[0], chi2[1]);
-      S[12 * cap + o] = 0.0f;
+#pragma unroll
+      for (int q = 0; q < 12; ++q) S[q * cap + o] = st[q];
+      S[12 * cap + o] = use_mlp ? 1.0f / (1.0f + expf(-t_seed[t])) : 0.0f;
       wk.tr_nhits[o] = (uint16_t)n;
       wk.tr_hitoff[o] = hoff;
     }

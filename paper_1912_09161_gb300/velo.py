@@ -26,8 +26,9 @@ CFG_CLUSTERS = 1
 
 EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
             "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_cluster_static",
-            "velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs", "velo_last_error",
-            "velo_version")
+            "velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs", "velo_set_mlp",
+            "velo_mlp_create", "velo_mlp_destroy", "velo_mlp_step", "velo_mlp_gradient", "velo_mlp_logits",
+            "velo_mlp_get_state", "velo_mlp_set_state", "velo_last_error", "velo_version")
 
 
 class VeloError(RuntimeError):
@@ -50,7 +51,7 @@ class velo_params(ctypes.Structure):
                 ("max_scatter_3hit", ctypes.c_float), ("max_skipped", ctypes.c_uint32),
                 ("sigma_meas", ctypes.c_float), ("pt_nominal", ctypes.c_float),
                 ("ms_coeff", ctypes.c_float), ("use_mlp", ctypes.c_uint32),
-                ("mlp_threshold", ctypes.c_float)]
+                ("mlp_logit_threshold", ctypes.c_float)]
 
 
 class velo_config(ctypes.Structure):
@@ -128,6 +129,18 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.velo_set_graphs.argtypes = [vp, ctypes.c_int]
     for name in ("velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.velo_set_mlp.argtypes = [vp, vp, vp, vp]
+    lib.velo_mlp_create.argtypes = [vp, vp, vp, ctypes.c_uint32, P(vp)]
+    lib.velo_mlp_destroy.argtypes = [vp]
+    lib.velo_mlp_destroy.restype = None
+    lib.velo_mlp_step.argtypes = [vp, vp, vp, ctypes.c_uint32, ctypes.c_float, vp]
+    lib.velo_mlp_gradient.argtypes = [vp, vp, vp, ctypes.c_uint32, vp, vp, vp]
+    lib.velo_mlp_logits.argtypes = [vp, vp, ctypes.c_uint32, vp, vp]
+    lib.velo_mlp_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.velo_mlp_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_uint32]
+    for name in ("velo_set_mlp", "velo_mlp_create", "velo_mlp_step", "velo_mlp_gradient", "velo_mlp_logits",
+                 "velo_mlp_get_state", "velo_mlp_set_state"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.velo_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.velo_describe.restype = ctypes.c_int
     lib.velo_last_error.restype = ctypes.c_char_p
@@ -158,7 +171,7 @@ class Params:
     pt_nominal: float = 0.4
     ms_coeff: float = 1.0
     use_mlp: int = 0
-    mlp_threshold: float = 0.5
+    mlp_logit_threshold: float = 0.0
 
     def to_c(self) -> velo_params:
         p = velo_params()
@@ -384,6 +397,14 @@ def velo_set_graphs(h, on: bool):
     _check(load_library(False).velo_set_graphs(h, 1 if on else 0), "velo_set_graphs")
 
 
+def velo_set_mlp(h, params_bf16: np.ndarray, mean: np.ndarray, istd: np.ndarray):
+    w = np.ascontiguousarray(params_bf16, np.uint16)
+    m = np.ascontiguousarray(mean, np.float32)
+    s = np.ascontiguousarray(istd, np.float32)
+    assert w.shape == (1441,) and m.shape == (10,) and s.shape == (10,)
+    _check(load_library(False).velo_set_mlp(h, w.ctypes.data, m.ctypes.data, s.ctypes.data), "velo_set_mlp")
+
+
 def velo_describe(h) -> dict:
     import json
     buf = ctypes.create_string_buffer(4096)
@@ -447,6 +468,9 @@ class Reconstructor:
 
     def set_graphs(self, on: bool = True):
         velo_set_graphs(self.handle, on)
+
+    def set_mlp(self, params_bf16: np.ndarray, mean: np.ndarray, istd: np.ndarray):
+        velo_set_mlp(self.handle, params_bf16, mean, istd)
 
     def set_timing(self, on: bool = True):
         velo_set_timing(self.handle, on)

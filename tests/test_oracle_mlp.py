@@ -1,0 +1,91 @@
+"""Pins for the ghost-classifier reference (oracle/mlp.py).
+
+* the series logarithm and arctangent against numpy's (within a few ulp);
+* the features against float64 formulas (eta = asinh(1/T), phi = atan2);
+* the float64 backward pass against central finite differences;
+* the BF16 forward against a float64 simulation of the same roundings.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.mlp as M
+
+
+def test_series_log():
+    q = np.exp(np.linspace(-20, 20, 400001)).astype(np.float32)
+    ref = np.log(q.astype(np.float64))
+    got = M.log_f32(q).astype(np.float64)
+    assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3)) < 4e-7
+    assert M.log_f32(np.float32([1.0]))[0] == 0.0
+
+
+def test_series_atan2():
+    rng = np.random.default_rng(3)
+    y = rng.normal(size=400000).astype(np.float32) * rng.choice([1e-3, 1, 1e3], 400000).astype(np.float32)
+    x = rng.normal(size=400000).astype(np.float32)
+    got = M.atan2_f32(y, x).astype(np.float64)
+    ref = np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    assert np.max(np.abs(got - ref)) < 5e-7
+    sp = M.atan2_f32(np.float32([0, 1, -1, 0, 1, -1, 0]), np.float32([1, 0, 0, -1, 1, -1, 0]))
+    assert np.allclose(sp, [0, np.pi / 2, -np.pi / 2, np.pi, np.pi / 4, -3 * np.pi / 4, 0], atol=3e-7)
+
+
+def test_features_match_float64(geom, cfg0_events):
+    r = oracle.reconstruct(geom, cfg0_events.subset(0, 20), all_candidates=True)
+    f, _, _ = M.candidate_table(geom, cfg0_events, r)
+    st = r.states.astype(np.float64)
+    T = np.hypot(st[:, 3], st[:, 4])
+    assert np.allclose(f[:, 0], st[:, 11] / r.ndof, rtol=2e-7)
+    assert np.allclose(f[:, 6], np.hypot(st[:, 0], st[:, 1]), rtol=1e-6)
+    assert np.allclose(f[:, 7], np.arcsinh(1.0 / T), rtol=1e-6)
+    dphi = f[:, 8] - np.arctan2(st[:, 4], st[:, 3])
+    dphi = (dphi + np.pi) % (2 * np.pi) - np.pi   # ty = -0.0 may give +pi against -pi
+    assert np.max(np.abs(dphi)) < 1e-6
+    nh = np.diff(r.hit_off.astype(np.int64))
+    assert np.array_equal(f[:, 1], nh) and np.all(f[:, 9] == f[:, 2] - f[:, 3] + 1 - f[:, 1])
+    assert np.all(f[:, 9] >= 0) and np.all(f[:, 2] > f[:, 3])
+
+
+def test_backward_matches_finite_differences():
+    rng = np.random.default_rng(7)
+    p = M.init_params(5).astype(np.float64)
+    p[M.N_IN * M.N_H:M.N_IN * M.N_H + M.N_H] = rng.normal(0, 0.1, M.N_H)  # non-zero biases
+    x = rng.normal(size=(64, M.N_IN))
+    y = (rng.random(64) < 0.5).astype(np.float64)
+    loss, g = M.backward64(x, y, p)
+    idx = rng.choice(M.N_PARAMS, 120, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        lp = M.bce_with_logits(M.forward64(x, p + e)[0], y)
+        lm = M.bce_with_logits(M.forward64(x, p - e)[0], y)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 + 1e-4 * abs(fd), (i, fd, g[i])
+    assert loss == pytest.approx(M.bce_with_logits(M.forward64(x, p)[0], y))
+
+
+def test_bf16_forward_matches_rounding_simulation():
+    rng = np.random.default_rng(11)
+    p = M.bf16_round(M.init_params(2))
+    f = rng.normal(size=(4000, M.N_IN)).astype(np.float32)
+    mean = np.zeros(M.N_IN, np.float32)
+    istd = np.ones(M.N_IN, np.float32)
+    got = M.forward_bf16(f, p, mean, istd).astype(np.float64)
+    # float64 sums, BF16 roundings at the same points
+    W1, b1, W2, b2, W3, b3 = M.split(p.astype(np.float64))
+    x = M.bf16_round(f).astype(np.float64)
+    h1 = M.bf16_round(np.maximum(x @ W1.T + b1, 0).astype(np.float32)).astype(np.float64)
+    h2 = M.bf16_round(np.maximum(h1 @ W2.T + b2, 0).astype(np.float32)).astype(np.float64)
+    ref = h2 @ W3 + b3[0]
+    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)
+    # float32 vs float64 accumulation may flip a BF16 rounding of an activation
+    assert np.median(rel) < 1e-6 and np.max(rel) < 2e-2
+
+
+def test_bf16_rounding():
+    v = np.float32([1.0, 1.00390625, 1.005859375, -2.5, 3.0e38])
+    b = M.bf16_round(v)
+    assert b[0] == 1.0 and b[1] == 1.0 and b[2] == np.float32(1.0078125) and b[3] == -2.5
+    assert np.all(M.bf16_bits(np.float32([1.0])) == 0x3F80)

@@ -297,3 +297,19 @@ def test_seed_middle_hit_must_be_unused():
     tracks = r.event_tracks(0)
     assert [[mods[h] for h in t] for t in tracks] == [[5, 4, 3, 2, 1]]
     assert tracks == brute_force(r.cl_x, r.cl_y, mods, g.module_z, p)
+
+
+def test_subset_metrics_consistent(geom, cfg0_events):
+    """A subset carries exactly its events' truth: metrics on a subset equal
+    the metrics of the same events generated on their own."""
+    sub = cfg0_events.subset(0, 30)
+    own = velo_synth.generate(velo_synth.config(0, n_events=30))
+    assert np.array_equal(sub.pix_label, own.pix_label) and np.array_equal(sub.part_modmask, own.part_modmask)
+    assert np.array_equal(sub.mc_particle, own.mc_particle) and np.array_equal(sub.part_vertex, own.part_vertex)
+    r = oracle.reconstruct(geom, sub)
+    a = M.summarize(sub, r.cluster_off, r.pix_cluster, r.track_off, r.hit_off, r.hit_ids)
+    b = M.summarize(own, r.cluster_off, r.pix_cluster, r.track_off, r.hit_off, r.hit_ids)
+    assert a == b and a["efficiency"] > 0.95
+    later = cfg0_events.subset(40, 70)
+    rl = oracle.reconstruct(geom, later)
+    assert M.summarize(later, rl.cluster_off, rl.pix_cluster, rl.track_off, rl.hit_off, rl.hit_ids)["efficiency"] > 0.95

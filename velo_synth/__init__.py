@@ -226,12 +226,29 @@ class SynthEvents:
         return np.diff(o)
 
     def subset(self, e0: int, e1: int) -> "SynthEvents":
-        """Events [e0, e1) with offsets rebased to zero (truth arrays kept whole)."""
+        """Events [e0, e1) with pixel offsets rebased to zero; the truth of
+        those events only, with particle, vertex and event indices renumbered."""
         s0, s1 = e0 * self.n_sensors, e1 * self.n_sensors
         p0, p1 = int(self.sensor_off[s0]), int(self.sensor_off[s1])
+        # particles, vertices and MC hits are stored in event order
+        q0, q1 = np.searchsorted(self.part_event, [e0, e1])
+        v0, v1 = np.searchsorted(self.vtx_event, [e0, e1])
+        h0, h1 = np.searchsorted(self.mc_particle, [q0, q1]) if len(self.mc_particle) else (0, 0)
+        lab = self.pix_label[p0:p1].astype(np.int64)
+        lab = np.where(lab >= 0, lab - q0, -1).astype(np.int32)
         d = dataclasses.asdict(self)
         d.update(n_events=e1 - e0, sensor_off=(self.sensor_off[s0:s1 + 1] - p0).astype(np.uint32),
-                 col=self.col[p0:p1], row=self.row[p0:p1], pix_label=self.pix_label[p0:p1])
+                 col=self.col[p0:p1], row=self.row[p0:p1], pix_label=lab,
+                 part_event=(self.part_event[q0:q1] - e0).astype(np.uint32),
+                 part_vertex=(self.part_vertex[q0:q1] - v0).astype(np.uint32),
+                 vtx_event=(self.vtx_event[v0:v1] - e0).astype(np.uint32),
+                 mc_particle=(self.mc_particle[h0:h1] - q0).astype(np.int32))
+        for name in ("part_nhits", "part_modmask", "part_p", "part_eta", "part_phi", "part_tx", "part_ty"):
+            d[name] = getattr(self, name)[q0:q1]
+        for name in ("vtx_x", "vtx_y", "vtx_z"):
+            d[name] = getattr(self, name)[v0:v1]
+        for name in ("mc_module", "mc_sensor", "mc_x", "mc_y", "mc_z"):
+            d[name] = getattr(self, name)[h0:h1]
         return SynthEvents(**d)
 
 
