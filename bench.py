@@ -4,9 +4,11 @@
 One step = one call of the library's ``velo_reconstruct`` over the whole
 batch (clustering, triplet seeding and following, cuts, fit, output
 compaction) with the raw pixels already resident in device memory.  Prints
-one JSON line (see the keys below).
+one JSON line (see the keys below), which also carries the serving loop's
+p50 / p99 batch latency under Poisson arrivals (``serving``) and the ghost
+rate of the benchmarked tracks.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--serve-seconds S]
 
 Workload: 10,000 synthetic events (seed 1; each rank r of a multi-GPU run
 takes seed 1 + 100 r, so per-GPU work is fixed: weak scaling).
@@ -197,15 +199,68 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline(geom, ev) -> dict:
+def cpu_baseline(geom, ev, gpu_result=None) -> dict:
+    """The oracle timed on the host cores over a sample of the workload.  Its
+    clusters also give the truth match of the GPU tracks of the same events
+    (tracking efficiency, ghost and clone rates)."""
     import oracle
+    import oracle.metrics as MET
     cores = os.cpu_count() or 1
     sub = ev.subset(0, min(CPU_SAMPLE, ev.n_events))
     t0 = time.perf_counter()
-    oracle.reconstruct(geom, sub, n_threads=cores)
+    r = oracle.reconstruct(geom, sub, n_threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": sub.n_events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sub.n_events} of the 10,000 events, all host cores ({dt:.1f} s)"}
+    out = {"value": sub.n_events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {sub.n_events} of the 10,000 events, all host cores ({dt:.1f} s)"}
+    if gpu_result is not None and sub.n_events == gpu_result.n_events:
+        q = MET.summarize(sub, r.cluster_off, r.pix_cluster, gpu_result.track_off, gpu_result.hit_off,
+                          gpu_result.hit_ids)
+        out["gpu_track_quality"] = {k: q[k] for k in ("efficiency", "ghost_rate", "clone_rate")}
+    return out
+
+
+def serving(geom, seconds: float, n_slots: int = 8) -> dict:
+    """Continuous-batching serving loop on the 5,000-event seed-4 sample:
+    batches of 100-5,000 events cut from it, arriving as a Poisson process.
+
+    sustainable rate = events/s of one slot working through a backlog of such
+    batches one after another (copy in, reconstruct, copy out, next): the rate
+    a server without continuous batching sustains.  The continuous-batching
+    server (n_slots slots, pool = 4 batches of the maximum size, so that memory
+    decides admission for large batches) then serves Poisson arrivals at 1.2x
+    that rate for ``seconds`` and at 0.8x for a quarter of it; latency is from
+    a batch's arrival to its results in host memory."""
+    import velo_synth
+    from paper_1912_09161_gb300 import serve
+    ev = velo_synth.generate(velo_synth.config(4))
+    pool = serve.EventPool(ev)
+    E, P = ev.n_events, pool.n_pixels(0, ev.n_events)
+    one = serve.Server(geom, n_slots=1, max_events=E, max_pixels=P)
+    one.replay(pool, serve.burst_trace(6, 100, 5000, E, seed=40))
+    b = serve.burst_trace(40, 100, 5000, E, seed=41)
+    _, wall = one.replay(pool, b)
+    serial = b.events / wall
+    one.close()
+    probe = serve.Server(geom, n_slots=1, max_events=1, max_pixels=1, pool_bytes=256)
+    need_max = probe.request_bytes(E, P)
+    probe.close()
+    srv = serve.Server(geom, n_slots=n_slots, max_events=E, max_pixels=P, pool_bytes=4 * need_max)
+    srv.replay(pool, serve.burst_trace(12, 100, 5000, E, seed=42))
+    _, wall = srv.replay(pool, b)
+    capacity = b.events / wall
+    out = {"workload": "batches of 100-5,000 events (uniform) cut from 5,000 nominal events, seed 4; "
+                       "Poisson arrivals", "n_slots": n_slots, "pool_bytes": 4 * need_max,
+           "sustainable_events_per_s": round(serial, 1), "burst_capacity_events_per_s": round(capacity, 1)}
+    for name, factor, dur, seed in (("load_1.2x", 1.2, seconds, 4), ("load_0.8x", 0.8, seconds / 4, 5)):
+        tr = serve.poisson_trace(factor * serial, dur, 100, 5000, E, seed=seed)
+        lat, wall = srv.replay(pool, tr, timeout_s=4 * dur + 60)
+        st = srv.status()
+        res = serve.latency_summary(lat, tr.events, wall)
+        res.update(offered_events_per_s=round(tr.events / dur, 1), duration_s=dur,
+                   peak_running=st["peak_running"], pool_peak_bytes=st["pool_peak"])
+        out[name] = res
+    srv.close()
+    return out
 
 
 def run_ours(args):
@@ -265,8 +320,13 @@ def run_ours(args):
     total_s = _max_over_ranks(sum(step_ms) / 1e3, dist)
     value = ws * ev.n_events * args.steps / total_s
 
+    gpu_res = out.to_host(ev.n_events) if rank == 0 and ws == 1 else None
+
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = _e2e(V, rec, ev, dev, args, dist, ws, sptr)
+
+    # continuous-batching serving loop (per GPU; every rank serves its own stream)
+    serve_res = serving(geom, args.serve_seconds)
 
     desc = rec.describe()
     peak, peak_kind = _measured_peak_hbm()
@@ -297,8 +357,13 @@ def run_ours(args):
         "gpu_launches": (KERNELS_BASE + len(desc["classes"])) * args.steps,
         "clocks": clocks.summary(),
     }
+    line["serving"] = serve_res
     if ws == 1:
-        line["cpu_baseline"] = cpu_baseline(geom, ev.subset(0, min(ev.n_events, N_EVENTS)))
+        line["cpu_baseline"] = cpu_baseline(geom, ev.subset(0, min(ev.n_events, N_EVENTS)), gpu_res)
+        q = line["cpu_baseline"].get("gpu_track_quality")
+        if q:
+            line["ghost_rate"] = q["ghost_rate"]
+    line["p99_latency_ms"] = serve_res["load_1.2x"]["p99_ms"]
     print(json.dumps(line), flush=True)
     return 0
 
@@ -339,6 +404,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="nominal",
                     help="nominal: the 10,000-event throughput batch; uneven: 50,000 events of mixed pileup")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="duration of the Poisson arrival stream at 1.2x the sustainable rate")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

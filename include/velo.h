@@ -98,7 +98,6 @@ typedef struct velo_config {
   uint64_t max_tracks;      /* tracks per call (working storage) */
   uint64_t max_track_hits;  /* hits on tracks per call (working storage) */
   uint32_t flags;           /* VELO_CFG_* */
-  uint32_t n_slots;         /* serving slots (velo_slot_*), 0 = none */
 } velo_config;
 
 #define VELO_CFG_CLUSTERS 0x1u  /* reserve storage for cluster output */
@@ -313,6 +312,105 @@ typedef struct velo_cluster_output {
 
 int velo_cluster_static(const velo_geometry *geometry, const velo_events *events, uint64_t n_pixels,
                         const velo_cluster_output *out, void *stream);
+
+/*
+ * Serving: continuous batching of reconstruction requests on one GPU.
+ *
+ * The paper's farm keeps several host-thread / CUDA-stream pairs per GPU, each
+ * with device memory of its own, so that the copies and kernels of different
+ * batches overlap (section 3.2).  A server holds, from creation to destroy:
+ *   - a device pool of pool_bytes (one allocation).  Each request holds one
+ *     contiguous range of it while it runs: its inputs, outputs and working
+ *     storage (velo_server_request_bytes gives the size);
+ *   - n_slots slots: a handle (geometry, parameters, classifier weights), a
+ *     stream and pinned host result buffers sized for max_events / max_pixels.
+ * velo_server_submit queues a request (FIFO).  velo_server_poll, called by the
+ * owner's thread as often as it likes, (1) moves running requests on: when a
+ * request's kernels are done it copies exactly its results to the slot's host
+ * buffers, and when that copy is done the request is finished; (2) reports
+ * finished requests, each once; (3) admits queued requests in arrival order
+ * while a slot is idle and the pool has a free range of the head request's
+ * size (a request that does not fit waits; none overtakes it).  Admitted
+ * requests run concurrently on their slots' streams.  A finished request's
+ * results stay readable (velo_server_result) until velo_server_release frees
+ * its slot and pool range.  Results are those of velo_reconstruct on the same
+ * events, whatever else is in flight.
+ *
+ * One host thread drives a server; nothing blocks except velo_server_destroy
+ * (waits for the slots' streams) and velo_server_replay (runs a whole trace).
+ */
+typedef struct velo_server velo_server;
+
+typedef struct velo_server_config {
+  uint32_t n_slots;     /* requests in flight at most, 1..64 */
+  uint32_t max_events;  /* events per request */
+  uint64_t max_pixels;  /* pixels per request */
+  uint64_t pool_bytes;  /* device pool; 0 = n_slots requests of the maximum size */
+} velo_server_config;
+
+typedef struct velo_server_done {
+  uint64_t id;          /* as submitted */
+  uint32_t n_events;
+  uint32_t slot;        /* pass to velo_server_result / velo_server_release */
+  uint32_t n_tracks;    /* totals[0] of the request */
+  uint32_t error_bits;  /* totals[3]: handle error bits (0 = clean) */
+  double latency_s;     /* host time from arrival (submit) to results in host memory */
+} velo_server_done;
+
+typedef struct velo_server_stats {
+  uint32_t queued, running, peak_running, reserved;
+  uint64_t done_requests, done_events;
+  uint64_t pool_bytes, pool_used, pool_peak, pool_largest_free;
+} velo_server_stats;
+
+/* Geometry and parameters as velo_create (host pointers, copied).  Errors:
+ * VELO_ERR_INPUT (bad configuration), VELO_ERR_NOMEM (pool or pinned memory),
+ * VELO_ERR_CUDA. */
+int velo_server_create(const velo_geometry *geometry, const velo_params *params,
+                       const velo_server_config *config, velo_server **out);
+void velo_server_destroy(velo_server *s);
+
+/* Device bytes a request of n_events / n_pixels holds while it runs. */
+int velo_server_request_bytes(const velo_server *s, uint32_t n_events, uint64_t n_pixels, uint64_t *bytes);
+
+/* Classifier weights for every slot (as velo_set_mlp); only while idle. */
+int velo_server_set_mlp(velo_server *s, const uint16_t *params_bf16, const float *mean, const float *istd);
+
+/*
+ * Queues a request.  HOST pointers, owned by the caller, read until the
+ * request is finished (pinned memory lets the copies overlap).  Pixels of
+ * event e, sensor s are [sensor_off[e*n_sensors+s], sensor_off[e*n_sensors+s+1])
+ * of col/row; sensor_off[0] may be non-zero (a request cut from a larger
+ * array).  VELO_ERR_NOMEM if the request exceeds max_events / max_pixels or
+ * could never fit the pool; VELO_ERR_INPUT for null or decreasing offsets.
+ */
+int velo_server_submit(velo_server *s, uint64_t id, uint32_t n_events, const uint32_t *sensor_off,
+                       const uint16_t *col, const uint16_t *row);
+
+/* Advances, reports up to max_done newly finished requests into done[],
+ * admits.  Never blocks. */
+int velo_server_poll(velo_server *s, velo_server_done *done, uint32_t max_done, uint32_t *n_done);
+
+/* Host view (pinned, library-owned) of a finished request's results, laid
+ * out as velo_output: states rows have pitch cap_tracks; totals [4]. */
+int velo_server_result(velo_server *s, uint32_t slot, velo_output *host_view);
+
+/* Frees a reported request's slot and pool range. */
+int velo_server_release(velo_server *s, uint32_t slot);
+
+int velo_server_status(const velo_server *s, velo_server_stats *out);
+
+/*
+ * Replays an arrival trace on an idle server: request i (n_events[i] events,
+ * host arrays sensor_off[i], col[i], row[i]) arrives arrival_s[i] seconds
+ * (non-decreasing) after the call starts; each is submitted at its arrival,
+ * released when finished, and its latency (from the scheduled arrival)
+ * written to latency_s[i].  wall_s: time from start until the last finished.
+ * VELO_ERR_TIMEOUT (server left idle) if timeout_s passes first.
+ */
+int velo_server_replay(velo_server *s, uint32_t n, const double *arrival_s, const uint32_t *n_events,
+                       const uint32_t *const *sensor_off, const uint16_t *const *col,
+                       const uint16_t *const *row, double timeout_s, double *latency_s, double *wall_s);
 
 /* Thread-local message of the last failing call on this thread. */
 const char *velo_last_error(void);

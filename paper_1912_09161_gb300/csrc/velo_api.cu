@@ -150,16 +150,30 @@ velo_config with_defaults(const velo_config* c) {
   return d;
 }
 
-struct ArenaPlan {
-  size_t geo, cnt, mlp, rec, q[kQueues], prov, pkey, cbase, st, nh, ho, hits, clx, cly, clk, total;
+// The arena holds a fixed part (geometry, counters, classifier weights) and a
+// work part sized by the capacities; a serving slot rebinds the work part to
+// memory of its own for every request (bind_work).
+struct FixedPlan {
+  size_t geo, cnt, mlp, total;
 };
 
-ArenaPlan plan_arena(const velo_config& c) {
-  ArenaPlan a{};
+FixedPlan plan_fixed() {
+  FixedPlan a{};
   size_t o = 0;
   a.geo = o; o = align256(o + sizeof(DevGeometry));
   a.cnt = o; o = align256(o + sizeof(Counters));
   a.mlp = o; o = align256(o + kMlpNormOffset + 4 * 2 * kMlpIn);
+  a.total = o;
+  return a;
+}
+
+struct WorkPlan {
+  size_t rec, q[kQueues], prov, pkey, cbase, st, nh, ho, hits, clx, cly, clk, total;
+};
+
+WorkPlan plan_work(const velo_config& c) {
+  WorkPlan a{};
+  size_t o = 0;
   a.rec = o; o = align256(o + sizeof(EventRec) * c.max_events);
   for (int k = 0; k < kQueues; ++k) { a.q[k] = o; o = align256(o + 4ull * c.max_events); }
   a.prov = o; o = align256(o + 8ull * c.max_pixels);
@@ -176,6 +190,34 @@ ArenaPlan plan_arena(const velo_config& c) {
   }
   a.total = o;
   return a;
+}
+
+// Points the handle's working storage at `base` (laid out by plan_work(c))
+// and takes c's capacities.
+void carve_work(velo_handle* h, char* base, const velo_config& c) {
+  const WorkPlan a = plan_work(c);
+  WorkView& w = h->wk;
+  w.rec = (EventRec*)(base + a.rec);
+  for (int k = 0; k < kQueues; ++k) w.queue[k] = (uint32_t*)(base + a.q[k]);
+  w.prov = (float2*)(base + a.prov);
+  w.prov_key = (c.flags & VELO_CFG_CLUSTERS) ? (uint16_t*)(base + a.pkey) : nullptr;
+  w.ev_cbase = (uint16_t*)(base + a.cbase);
+  w.tr_state = (float*)(base + a.st);
+  w.tr_nhits = (uint16_t*)(base + a.nh);
+  w.tr_hitoff = (uint32_t*)(base + a.ho);
+  w.tr_hits = (uint32_t*)(base + a.hits);
+  w.cap_tracks = (uint32_t)c.max_tracks;
+  w.cap_hits = (uint32_t)c.max_track_hits;
+  w.cl_x = (c.flags & VELO_CFG_CLUSTERS) ? (float*)(base + a.clx) : nullptr;
+  w.cl_y = (c.flags & VELO_CFG_CLUSTERS) ? (float*)(base + a.cly) : nullptr;
+  w.cl_key = (c.flags & VELO_CFG_CLUSTERS) ? (uint32_t*)(base + a.clk) : nullptr;
+  w.cap_pixels = c.max_pixels;
+  h->cfg.max_events = c.max_events;
+  h->cfg.max_pixels = c.max_pixels;
+  h->cfg.max_tracks = c.max_tracks;
+  h->cfg.max_track_hits = c.max_track_hits;
+  h->cfg.flags = c.flags;
+  h->version++;
 }
 
 // CTAs per SM of the candidate classes; a schedule's class_mask selects
@@ -313,6 +355,23 @@ int enqueue_graph(velo_handle* h, const velo_events& events, const velo_output& 
 
 }  // namespace
 
+namespace velo {
+
+velo_config work_config(uint32_t n_events, uint64_t n_pixels) {
+  velo_config c{};
+  c.max_events = n_events ? n_events : 1;
+  c.max_pixels = n_pixels ? n_pixels : 1;
+  return with_defaults(&c);
+}
+
+size_t work_bytes(uint32_t n_events, uint64_t n_pixels) { return plan_work(work_config(n_events, n_pixels)).total; }
+
+void bind_work(velo_handle* h, void* base, uint32_t n_events, uint64_t n_pixels) {
+  carve_work(h, (char*)base, work_config(n_events, n_pixels));
+}
+
+}  // namespace velo
+
 extern "C" {
 
 const char* velo_last_error(void) { return g_err; }
@@ -321,7 +380,7 @@ const char* velo_version(void) { return "velo-gb300 0.1 (sm_103a)"; }
 
 int velo_required_bytes(const velo_geometry* geometry, const velo_config* config, size_t* bytes) {
   if (!geometry_ok(geometry) || !bytes) return fail(VELO_ERR_INPUT, "velo_required_bytes: bad geometry or null output");
-  *bytes = plan_arena(with_defaults(config)).total;
+  *bytes = plan_fixed().total + plan_work(with_defaults(config)).total;
   return VELO_OK;
 }
 
@@ -372,33 +431,17 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     if (rc) break;
     e = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming);
     if (e != cudaSuccess) { rc = fail(VELO_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e)); break; }
-    ArenaPlan a = plan_arena(h->cfg);
-    e = cudaMalloc(&h->arena, a.total);
-    if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", a.total, cudaGetErrorString(e)); h->arena = nullptr; break; }
-    h->arena_bytes = a.total;
+    const FixedPlan fx = plan_fixed();
+    const size_t total = fx.total + plan_work(h->cfg).total;
+    e = cudaMalloc(&h->arena, total);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e)); h->arena = nullptr; break; }
+    h->arena_bytes = total;
     char* base = (char*)h->arena;
-    h->d_geo = (DevGeometry*)(base + a.geo);
-    h->d_cnt = (Counters*)(base + a.cnt);
-    WorkView& w = h->wk;
-    w.cnt = h->d_cnt;
-    h->d_mlp = base + a.mlp;
-    w.rec = (EventRec*)(base + a.rec);
-    for (int k = 0; k < kQueues; ++k) w.queue[k] = (uint32_t*)(base + a.q[k]);
-    w.prov = (float2*)(base + a.prov);
-    w.prov_key = (h->cfg.flags & VELO_CFG_CLUSTERS) ? (uint16_t*)(base + a.pkey) : nullptr;
-    w.ev_cbase = (uint16_t*)(base + a.cbase);
-    w.tr_state = (float*)(base + a.st);
-    w.tr_nhits = (uint16_t*)(base + a.nh);
-    w.tr_hitoff = (uint32_t*)(base + a.ho);
-    w.tr_hits = (uint32_t*)(base + a.hits);
-    w.cap_tracks = (uint32_t)h->cfg.max_tracks;
-    w.cap_hits = (uint32_t)h->cfg.max_track_hits;
-    if (h->cfg.flags & VELO_CFG_CLUSTERS) {
-      w.cl_x = (float*)(base + a.clx);
-      w.cl_y = (float*)(base + a.cly);
-      w.cl_key = (uint32_t*)(base + a.clk);
-    }
-    w.cap_pixels = h->cfg.max_pixels;
+    h->d_geo = (DevGeometry*)(base + fx.geo);
+    h->d_cnt = (Counters*)(base + fx.cnt);
+    h->wk.cnt = h->d_cnt;
+    h->d_mlp = base + fx.mlp;
+    carve_work(h, base + fx.total, h->cfg);
     rc = build_classes(h, h->sched);
     if (rc) break;
     e = cudaMemcpy(h->d_geo, &h->geo, sizeof(DevGeometry), cudaMemcpyHostToDevice);

@@ -128,4 +128,12 @@ cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const Eve
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
 cudaError_t launch_emit(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
 
+// Working storage of a handle outside its own arena (serving): the capacities
+// a call of n_events / n_pixels gets, the bytes they take, and the rebinding
+// of the handle's working storage to `base` (256-byte aligned, work_bytes long).
+velo_config work_config(uint32_t n_events, uint64_t n_pixels);
+size_t work_bytes(uint32_t n_events, uint64_t n_pixels);
+void bind_work(velo_handle* h, void* base, uint32_t n_events, uint64_t n_pixels);
+void set_last_error(const char* msg);
+
 }  // namespace velo

@@ -28,7 +28,10 @@ EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_para
             "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_cluster_static",
             "velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs", "velo_set_mlp",
             "velo_mlp_create", "velo_mlp_destroy", "velo_mlp_step", "velo_mlp_gradient", "velo_mlp_logits",
-            "velo_mlp_get_state", "velo_mlp_set_state", "velo_last_error", "velo_version")
+            "velo_mlp_get_state", "velo_mlp_set_state", "velo_server_create", "velo_server_destroy",
+            "velo_server_request_bytes", "velo_server_set_mlp", "velo_server_submit", "velo_server_poll",
+            "velo_server_result", "velo_server_release", "velo_server_status", "velo_server_replay",
+            "velo_last_error", "velo_version")
 
 
 class VeloError(RuntimeError):
@@ -57,7 +60,7 @@ class velo_params(ctypes.Structure):
 class velo_config(ctypes.Structure):
     _fields_ = [("max_events", ctypes.c_uint32), ("max_pixels", ctypes.c_uint64),
                 ("max_tracks", ctypes.c_uint64), ("max_track_hits", ctypes.c_uint64),
-                ("flags", ctypes.c_uint32), ("n_slots", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32)]
 
 
 class velo_stats(ctypes.Structure):
@@ -91,6 +94,23 @@ class velo_output(ctypes.Structure):
                 ("ndof", ctypes.c_void_p), ("event_status", ctypes.c_void_p), ("totals", ctypes.c_void_p),
                 ("cluster_off", ctypes.c_void_p), ("cl_x", ctypes.c_void_p), ("cl_y", ctypes.c_void_p),
                 ("cl_key", ctypes.c_void_p)]
+
+
+class velo_server_config(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_uint32), ("max_events", ctypes.c_uint32), ("max_pixels", ctypes.c_uint64),
+                ("pool_bytes", ctypes.c_uint64)]
+
+
+class velo_server_done(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("n_events", ctypes.c_uint32), ("slot", ctypes.c_uint32),
+                ("n_tracks", ctypes.c_uint32), ("error_bits", ctypes.c_uint32), ("latency_s", ctypes.c_double)]
+
+
+class velo_server_stats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_uint32), ("running", ctypes.c_uint32), ("peak_running", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("done_requests", ctypes.c_uint64),
+                ("done_events", ctypes.c_uint64), ("pool_bytes", ctypes.c_uint64), ("pool_used", ctypes.c_uint64),
+                ("pool_peak", ctypes.c_uint64), ("pool_largest_free", ctypes.c_uint64)]
 
 
 _lib = None
@@ -140,6 +160,22 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.velo_mlp_set_state.argtypes = [vp, vp, vp, vp, ctypes.c_uint32]
     for name in ("velo_set_mlp", "velo_mlp_create", "velo_mlp_step", "velo_mlp_gradient", "velo_mlp_logits",
                  "velo_mlp_get_state", "velo_mlp_set_state"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.velo_server_create.argtypes = [P(velo_geometry), P(velo_params), P(velo_server_config), P(vp)]
+    lib.velo_server_destroy.argtypes = [vp]
+    lib.velo_server_destroy.restype = None
+    lib.velo_server_request_bytes.argtypes = [vp, ctypes.c_uint32, ctypes.c_uint64, P(ctypes.c_uint64)]
+    lib.velo_server_set_mlp.argtypes = [vp, vp, vp, vp]
+    lib.velo_server_submit.argtypes = [vp, ctypes.c_uint64, ctypes.c_uint32, vp, vp, vp]
+    lib.velo_server_poll.argtypes = [vp, P(velo_server_done), ctypes.c_uint32, P(ctypes.c_uint32)]
+    lib.velo_server_result.argtypes = [vp, ctypes.c_uint32, P(velo_output)]
+    lib.velo_server_release.argtypes = [vp, ctypes.c_uint32]
+    lib.velo_server_status.argtypes = [vp, P(velo_server_stats)]
+    lib.velo_server_replay.argtypes = [vp, ctypes.c_uint32, vp, vp, vp, vp, vp, ctypes.c_double, vp,
+                                       P(ctypes.c_double)]
+    for name in ("velo_server_create", "velo_server_request_bytes", "velo_server_set_mlp", "velo_server_submit",
+                 "velo_server_poll", "velo_server_result", "velo_server_release", "velo_server_status",
+                 "velo_server_replay"):
         getattr(lib, name).restype = ctypes.c_int
     lib.velo_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.velo_describe.restype = ctypes.c_int
@@ -439,7 +475,7 @@ class Reconstructor:
         self.geometry = geometry
         self.params = params or Params()
         self.config = velo_config(max_events, max_pixels or max_events * 8192, max_tracks, max_track_hits,
-                                  CFG_CLUSTERS if clusters else 0, 0)
+                                  CFG_CLUSTERS if clusters else 0)
         self.handle = velo_create(geometry, self.params, self.config)
 
     def close(self):
