@@ -168,7 +168,7 @@ FixedPlan plan_fixed() {
 }
 
 struct WorkPlan {
-  size_t rec, q[kQueues], prov, pkey, cbase, st, nh, ho, hits, clx, cly, clk, total;
+  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, hits, xy, mod, clx, cly, clk, total;
 };
 
 WorkPlan plan_work(const velo_config& c) {
@@ -179,10 +179,12 @@ WorkPlan plan_work(const velo_config& c) {
   a.prov = o; o = align256(o + 8ull * c.max_pixels);
   if (c.flags & VELO_CFG_CLUSTERS) { a.pkey = o; o = align256(o + 2ull * c.max_pixels); }
   a.cbase = o; o = align256(o + 2ull * (kMaxSensors + 1) * c.max_events);
-  a.st = o; o = align256(o + 4ull * VELO_NSTATE * c.max_tracks);
+  a.lg = o; o = align256(o + 4ull * c.max_tracks);
   a.nh = o; o = align256(o + 2ull * c.max_tracks);
   a.ho = o; o = align256(o + 4ull * c.max_tracks);
   a.hits = o; o = align256(o + 4ull * c.max_track_hits);
+  a.xy = o; o = align256(o + 8ull * c.max_track_hits);
+  a.mod = o; o = align256(o + 1ull * c.max_track_hits);
   if (c.flags & VELO_CFG_CLUSTERS) {
     a.clx = o; o = align256(o + 4ull * c.max_pixels);
     a.cly = o; o = align256(o + 4ull * c.max_pixels);
@@ -202,10 +204,12 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
   w.prov = (float2*)(base + a.prov);
   w.prov_key = (c.flags & VELO_CFG_CLUSTERS) ? (uint16_t*)(base + a.pkey) : nullptr;
   w.ev_cbase = (uint16_t*)(base + a.cbase);
-  w.tr_state = (float*)(base + a.st);
+  w.tr_logit = (float*)(base + a.lg);
   w.tr_nhits = (uint16_t*)(base + a.nh);
   w.tr_hitoff = (uint32_t*)(base + a.ho);
   w.tr_hits = (uint32_t*)(base + a.hits);
+  w.tr_xy = (float2*)(base + a.xy);
+  w.tr_mod = (uint8_t*)(base + a.mod);
   w.cap_tracks = (uint32_t)c.max_tracks;
   w.cap_hits = (uint32_t)c.max_track_hits;
   w.cl_x = (c.flags & VELO_CFG_CLUSTERS) ? (float*)(base + a.clx) : nullptr;
@@ -236,7 +240,7 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     if (!((mask >> i) & 1u)) continue;
     uint32_t budget = (uint32_t)(h->smem_sm / kPerSm[i]) - 1024u;
     if (budget > (uint32_t)h->smem_optin) budget = (uint32_t)h->smem_optin;
-    const Caps c = make_caps(budget, (uint32_t)h->geo.n_modules);
+    const Caps c = make_caps(budget, (uint32_t)h->geo.n_modules, threads);
     if (c.maxh <= prev_maxh) continue;
     cudaError_t e = track_set_smem_limit(threads, (int)c.smem);
     if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e));
@@ -269,15 +273,18 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
 // The launch sequence of one call: counters, clustering, tracking classes
 // (concurrent on their streams, largest plans first, or one after another
 // on the caller's stream), the retry pass, scan and emit.
-// Timing events are recorded as external events so that a captured graph
-// records them too.
-int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo_output& out, cudaStream_t st) {
+// Under stream capture (capture = true) the timing events are recorded as
+// external events, so that the graph records them too; outside a capture
+// that flag is not allowed and they are recorded plainly.
+int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo_output& out, cudaStream_t st,
+            bool capture) {
+  const unsigned mark = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   const uint32_t E = ev.n_events;
   const bool tm = h->timing;
   CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
-  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[0], st, cudaEventRecordExternal));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[0], st, mark));
   CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, st));
-  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[1], st, cudaEventRecordExternal));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[1], st, mark));
   if (E) {
     if (h->sched.concurrent) {
       CUDA_TRY(cudaEventRecord(h->fork, st));
@@ -295,11 +302,11 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
     const int big = h->n_classes - 1;
     CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[big], big, kRetryQueue, h->threads, h->ctas[big], st));
   }
-  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[2], st, cudaEventRecordExternal));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[2], st, mark));
   CUDA_TRY(launch_scan(E, wk, out, st));
-  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[3], st, cudaEventRecordExternal));
-  CUDA_TRY(launch_emit(E, wk, out, st));
-  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[4], st, cudaEventRecordExternal));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[3], st, mark));
+  CUDA_TRY(launch_emit(E, h->d_geo, h->par, wk, out, st));
+  if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[4], st, mark));
   CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   if (tm) CUDA_TRY(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
   return VELO_OK;
@@ -329,7 +336,7 @@ int enqueue_graph(velo_handle* h, const velo_events& events, const velo_output& 
     *slot = velo_handle::GraphEntry{};
     cudaGraph_t graph = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue(h, ev, wk, out, st);
+    const int rc = enqueue(h, ev, wk, out, st, true);
     const cudaError_t ec = cudaStreamEndCapture(st, &graph);
     if (rc != VELO_OK) {
       if (graph) cudaGraphDestroy(graph);
@@ -644,7 +651,7 @@ int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_outpu
     wk.cl_key = nullptr;
   }
   if (h->use_graphs && st != nullptr) return enqueue_graph(h, *events, *out, ev, wk, st);
-  return enqueue(h, ev, wk, *out, st);
+  return enqueue(h, ev, wk, *out, st, false);
 }
 
 int velo_sync_status(velo_handle* h, void* stream) {

@@ -1,11 +1,13 @@
 // Batch-level kernels after the per-event reconstruction:
 //   scan  -- exclusive scan of the per-event track / hit / cluster counts;
-//   emit  -- copies every event's results from scratch to the caller's
+//   emit  -- fits every kept track (simple Kalman filter and beamline state,
+//            paper section 2.3.1) and writes the results to the caller's
 //            compact, canonically ordered output arrays.
 // Only the raw input goes in and only tracks, states (and optionally
 // clusters) come out (paper section 2.2: raw data in, selected objects out).
 #include <stdint.h>
 
+#include "velo_fit.cuh"
 #include "velo_internal.cuh"
 
 namespace velo {
@@ -80,23 +82,46 @@ cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output
 }
 
 // ---------------------------------------------------------------------------
-// emit: one block per event (grid-stride)
+// emit: one block per event (grid-stride), one thread per track
 // ---------------------------------------------------------------------------
-__global__ void emit_kernel(uint32_t n_events, WorkView wk, velo_output out) {
+constexpr int kEmitThreads = 128;
+
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
+                                                            DevParams par, WorkView wk, velo_output out) {
+  __shared__ float s_z[kMaxModules];
+  for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
+  __syncthreads();
+  const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
+  const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
+  const float kms = fit_kms(par);
   for (uint32_t e = blockIdx.x; e < n_events; e += gridDim.x) {
     const EventRec r = wk.rec[e];
     const uint32_t o0 = out.track_off[e], h0 = r.out_hit_base;
     uint32_t status = r.status;
     const bool fits = (uint64_t)o0 + r.n_tracks <= out.cap_tracks && (uint64_t)h0 + r.n_hits <= out.cap_hits;
     if (fits) {
-      const size_t scap = wk.cap_tracks, ocap = out.cap_tracks;
-      for (uint32_t j = 0; j < VELO_NSTATE; ++j)
-        for (uint32_t k = threadIdx.x; k < r.n_tracks; k += blockDim.x)
-          out.states[j * ocap + o0 + k] = wk.tr_state[j * scap + r.track_base + k];
+      const size_t ocap = out.cap_tracks;
       for (uint32_t k = threadIdx.x; k < r.n_tracks; k += blockDim.x) {
-        const uint32_t nh = wk.tr_nhits[r.track_base + k];
+        const uint32_t t = r.track_base + k;
+        const uint32_t nh = wk.tr_nhits[t];
+        const uint32_t hoff = wk.tr_hitoff[t];
+        const float2* xy = wk.tr_xy + r.hit_base + hoff;
+        const uint8_t* md = wk.tr_mod + r.hit_base + hoff;
+        float st[12];
+        fit_track(
+            nh,
+            [&](uint32_t j, float& x, float& y, int& m) {
+              const float2 v = xy[j];
+              x = v.x;
+              y = v.y;
+              m = md[j];
+            },
+            s_z, sig2, kms, st);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) out.states[q * ocap + o0 + k] = st[q];
+        out.states[12 * ocap + o0 + k] = use_mlp ? 1.0f / (1.0f + expf(-wk.tr_logit[t])) : 0.0f;
         out.ndof[o0 + k] = (uint8_t)(2 * nh - 4);
-        out.hit_off[o0 + k] = h0 + wk.tr_hitoff[r.track_base + k];
+        out.hit_off[o0 + k] = h0 + hoff;
       }
       for (uint32_t k = threadIdx.x; k < r.n_hits; k += blockDim.x)
         out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k];
@@ -119,10 +144,11 @@ __global__ void emit_kernel(uint32_t n_events, WorkView wk, velo_output out) {
   }
 }
 
-cudaError_t launch_emit(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st) {
+cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const WorkView& wk,
+                        const velo_output& out, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;
   int blocks = (int)(n_events < 152u * 16u ? n_events : 152u * 16u);
-  emit_kernel<<<blocks, 128, 0, st>>>(n_events, wk, out);
+  emit_kernel<<<blocks, kEmitThreads, 0, st>>>(n_events, geo, par, wk, out);
   return cudaGetLastError();
 }
 

@@ -95,11 +95,14 @@ struct WorkView {
   float2* prov;                  // [cap_pixels]
   uint16_t* prov_key;            // [cap_pixels] smallest pixel key (cluster output only)
   uint16_t* ev_cbase;            // [max_events][kMaxSensors + 1] canonical id of each sensor's first hit
-  // scratch tracks (SoA), bump-allocated per event
-  float* tr_state;               // [VELO_NSTATE][cap_tracks]
+  // scratch tracks (SoA), bump-allocated per event, canonical order within
+  // the event; the emit kernel fits them from their hits' positions
+  float* tr_logit;               // [cap_tracks] classifier logit (0 without the classifier)
   uint16_t* tr_nhits;            // [cap_tracks]
   uint32_t* tr_hitoff;           // [cap_tracks] first hit, relative to the event's hit base
   uint32_t* tr_hits;             // [cap_hits] event-local canonical ids
+  float2* tr_xy;                 // [cap_hits] hit positions (global x, y)
+  uint8_t* tr_mod;               // [cap_hits] hit modules
   uint32_t cap_tracks, cap_hits;
   // scratch clusters (canonical, at the event's pixel base), may be null
   float* cl_x;
@@ -118,7 +121,7 @@ cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const W
                            cudaStream_t st);
 
 // Tracking kernel (velo_track.cu).
-Caps make_caps(uint32_t smem_budget, uint32_t n_modules);
+Caps make_caps(uint32_t smem_budget, uint32_t n_modules, int n_threads);
 cudaError_t track_set_smem_limit(int n_threads, int bytes);
 cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm);
 cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
@@ -126,7 +129,8 @@ cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const Eve
 
 // Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
-cudaError_t launch_emit(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
+cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const WorkView& wk,
+                        const velo_output& out, cudaStream_t st);
 
 // Working storage of a handle outside its own arena (serving): the capacities
 // a call of n_events / n_pixels gets, the bytes they take, and the rebinding

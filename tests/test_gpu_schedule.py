@@ -74,3 +74,25 @@ def test_autotuner_keeps_results(env):
     for a, b in zip(_flat(before), _flat(after)):
         assert np.array_equal(a, b)
     rec.close()
+
+
+def test_kernel_timing_with_and_without_graphs(env):
+    """Per-kernel timing works on plain launches and on graph replays, and
+    the per-class counters cover every event exactly once."""
+    V, torch, geom, ev = env
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
+    stream = torch.cuda.Stream()
+    d = V.upload_events(ev)
+    ct, ch, _ = V.suggested_caps(ev.n_events, ev.n_pixels)
+    out = V.alloc_output(ev.n_events, ct, ch, 0)
+    rec.set_timing(True)
+    for graphs in (False, True):
+        rec.set_graphs(graphs)
+        for _ in range(2):
+            rec.reconstruct(d, out, stream.cuda_stream)
+            assert rec.sync_status(stream.cuda_stream) == V.velo.VELO_OK
+            st = rec.stats()
+            assert all(x > 0 for x in st["ms"][:2]) and st["ms"][4] >= st["ms"][1]
+            assert sum(st["events"]) == ev.n_events
+            assert sum(st["tracks"]) == int(out.totals.cpu()[0])
+    rec.close()
