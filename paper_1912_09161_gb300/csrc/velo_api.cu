@@ -80,6 +80,9 @@ struct velo_handle {
   cudaEvent_t join[kMaxClasses]{};
   // host-path staging (allocated on first use)
   void* stage = nullptr;
+  // tracking-kernel hit slots (sized at creation for the largest schedule)
+  uint16_t* trk = nullptr;
+  size_t trk_bytes = 0;
   size_t stage_bytes = 0;
   uint32_t* h_totals = nullptr;  // pinned
   uint32_t last_error_bits = 0;
@@ -228,6 +231,30 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
 // from this list (at most kMaxClasses; one CTA per SM is always included).
 constexpr int kPerSm[6] = {8, 6, 4, 3, 2, 1};
 
+// Hit-slot bytes of a class plan: kMaxModules u16 per candidate, max_tracks
+// candidates per CTA.
+size_t class_trk_bytes(const Caps& c, int ctas) { return (size_t)ctas * c.maxt * kMaxModules * sizeof(uint16_t); }
+
+// Hit slots every schedule fits in: per thread count, the four largest
+// classes over all CTA-per-SM candidates.
+size_t trk_bytes_bound(const velo_handle* h) {
+  size_t best = 0;
+  for (int threads = 128; threads <= 256; threads *= 2) {
+    size_t b[6];
+    for (int i = 0; i < 6; ++i) {
+      uint32_t budget = (uint32_t)(h->smem_sm / kPerSm[i]) - 1024u;
+      if (budget > (uint32_t)h->smem_optin) budget = (uint32_t)h->smem_optin;
+      b[i] = class_trk_bytes(make_caps(budget, (uint32_t)h->geo.n_modules, threads), kPerSm[i] * h->n_sm);
+    }
+    for (int i = 0; i < 6; ++i)
+      for (int j = i + 1; j < 6; ++j)
+        if (b[j] > b[i]) { const size_t t = b[i]; b[i] = b[j]; b[j] = t; }
+    const size_t sum = b[0] + b[1] + b[2] + b[3];
+    if (sum > best) best = sum;
+  }
+  return best;
+}
+
 int build_classes(velo_handle* h, const velo_schedule& sc) {
   if (sc.track_threads != 128 && sc.track_threads != 256)
     return fail(VELO_ERR_INPUT, "schedule: track_threads must be 128 or 256");
@@ -254,6 +281,9 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     prev_maxh = c.maxh;
   }
   if (n == 0) return fail(VELO_ERR_INPUT, "schedule: no class");
+  size_t need = 0;
+  for (int k = 0; k < n; ++k) need += class_trk_bytes(caps[k], per_sm[k] * h->n_sm);
+  if (need > h->trk_bytes) return fail(VELO_ERR_NOMEM, "schedule: hit slots need %zu bytes, have %zu", need, h->trk_bytes);
   cudaError_t e = track_set_smem_limit(threads, (int)caps[n - 1].smem);
   if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e));
   h->sched = sc;
@@ -266,6 +296,11 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     h->wk.class_maxh[k] = k < n ? caps[k].maxh : 0;
   }
   h->wk.n_classes = n;
+  size_t off = 0;
+  for (int k = 0; k < kMaxClasses; ++k) {
+    h->wk.trk_hits[k] = k < n ? h->trk + off : nullptr;
+    if (k < n) off += (size_t)h->ctas[k] * caps[k].maxt * kMaxModules;
+  }
   h->version++;
   return VELO_OK;
 }
@@ -449,6 +484,9 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     h->wk.cnt = h->d_cnt;
     h->d_mlp = base + fx.mlp;
     carve_work(h, base + fx.total, h->cfg);
+    h->trk_bytes = trk_bytes_bound(h);
+    e = cudaMalloc(&h->trk, h->trk_bytes);
+    if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", h->trk_bytes, cudaGetErrorString(e)); h->trk = nullptr; break; }
     rc = build_classes(h, h->sched);
     if (rc) break;
     e = cudaMemcpy(h->d_geo, &h->geo, sizeof(DevGeometry), cudaMemcpyHostToDevice);
@@ -484,6 +522,7 @@ void velo_destroy(velo_handle* h) {
   if (h->h_cnt) cudaFreeHost(h->h_cnt);
   if (h->arena) cudaFree(h->arena);
   if (h->stage) cudaFree(h->stage);
+  if (h->trk) cudaFree(h->trk);
   if (h->h_totals) cudaFreeHost(h->h_totals);
   delete h;
 }
@@ -498,9 +537,9 @@ int velo_describe(const velo_handle* h, char* buf, size_t n) {
   for (int k = 0; k < h->n_classes && w > 0 && (size_t)w < n; ++k)
     w += snprintf(buf + w, n - w,
                   "%s{\"threads\": %d, \"ctas_per_sm\": %d, \"ctas\": %d, \"smem\": %u, \"max_hits\": %u, "
-                  "\"max_tracks\": %u, \"max_chain\": %u}",
+                  "\"max_tracks\": %u}",
                   k ? ", " : "", h->threads, h->per_sm[k], h->ctas[k], h->caps[k].smem, h->caps[k].maxh,
-                  h->caps[k].maxt, h->caps[k].maxch);
+                  h->caps[k].maxt);
   if (w > 0 && (size_t)w < n) snprintf(buf + w, n - w, "]}");
   return VELO_OK;
 }

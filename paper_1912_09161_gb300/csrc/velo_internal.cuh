@@ -43,7 +43,6 @@ struct DevParams {
 struct Caps {
   uint32_t maxh;   // hits
   uint32_t maxt;   // track candidates
-  uint32_t maxch;  // hit-chain entries
   uint32_t smem;   // bytes of dynamic shared memory
 };
 
@@ -103,6 +102,9 @@ struct WorkView {
   uint32_t* tr_hits;             // [cap_hits] event-local canonical ids
   float2* tr_xy;                 // [cap_hits] hit positions (global x, y)
   uint8_t* tr_mod;               // [cap_hits] hit modules
+  // tracking-kernel hit slots per class: kMaxModules positions per candidate,
+  // max_tracks candidates per CTA, one region per CTA of the class
+  uint16_t* trk_hits[kMaxClasses];
   uint32_t cap_tracks, cap_hits;
   // scratch clusters (canonical, at the event's pixel base), may be null
   float* cl_x;

@@ -16,9 +16,10 @@
 //      canonically and write their hits (ids, positions, modules) to scratch;
 //      the emit kernel fits them.
 // Hits live in shared memory in (module, phi bin) order ("positions"); the
-// used flags, the windows and the hit chains of the candidates refer to
-// positions, every decision that prefers one hit to another compares
-// canonical ids.  All tracking decisions use explicit round-to-nearest IEEE
+// used flags and the windows refer to positions, every decision that prefers
+// one hit to another compares canonical ids.  Each candidate's hit positions
+// are appended to a fixed slot in global memory (the CTA's own region, reused
+// event after event), which only the cuts and the output read back.  All tracking decisions use explicit round-to-nearest IEEE
 // single-precision operations in a fixed order, so results do not depend on
 // the order of hits within a bin, the schedule, the thread count or the class
 // an event runs in.
@@ -36,19 +37,18 @@ namespace velo {
 // ---------------------------------------------------------------------------
 struct Layout {
   uint32_t z, cb, bins, wscr, misc, scan;   // fixed part
-  uint32_t pos, pid, pmod, used;            // per hit position
+  uint32_t pos, pid, used;                  // per hit position
   // per track candidate: last hit (x, y, z), slopes, seed scatter (or logit),
-  // seed hit positions, chain head, hits, skips; x / y / z hold the canonical
-  // key, rank and hit offset after the rounds
-  uint32_t t_x, t_y, t_z, t_tx, t_ty, t_seed, t_pa, t_pb, t_pc, t_head, t_n, t_skip;
+  // seed hit positions, hits, skips; x / y / z hold the canonical key, rank
+  // and hit offset after the rounds
+  uint32_t t_x, t_y, t_z, t_tx, t_ty, t_seed, t_pa, t_pb, t_pc, t_n, t_skip;
   uint32_t act0, act1;                      // active-track lists (current / next round)
-  uint32_t chain;
   uint32_t total;
 };
 
 __host__ __device__ inline uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-__host__ __device__ inline Layout make_layout(uint32_t maxh, uint32_t maxt, uint32_t maxch, uint32_t nm, uint32_t nw) {
+__host__ __device__ inline Layout make_layout(uint32_t maxh, uint32_t maxt, uint32_t nm, uint32_t nw) {
   Layout L;
   uint32_t o = 0;
   L.z = o; o = align16(o + 4 * kMaxModules);
@@ -59,7 +59,6 @@ __host__ __device__ inline Layout make_layout(uint32_t maxh, uint32_t maxt, uint
   L.scan = o; o = align16(o + 4 * 32);
   L.pos = o; o = align16(o + 8 * maxh);
   L.pid = o; o = align16(o + 2 * maxh);
-  L.pmod = o; o = align16(o + maxh);
   L.used = o; o = align16(o + 8 * ((maxh + 31) / 32));  // two bitmaps
   L.t_x = o; o = align16(o + 4 * maxt);
   L.t_y = o; o = align16(o + 4 * maxt);
@@ -70,24 +69,18 @@ __host__ __device__ inline Layout make_layout(uint32_t maxh, uint32_t maxt, uint
   L.t_pa = o; o = align16(o + 2 * maxt);
   L.t_pb = o; o = align16(o + 2 * maxt);
   L.t_pc = o; o = align16(o + 2 * maxt);
-  L.t_head = o; o = align16(o + 2 * maxt);
   L.t_n = o; o = align16(o + maxt);
   L.t_skip = o; o = align16(o + maxt);
   L.act0 = o; o = align16(o + 2 * maxt);
   L.act1 = o; o = align16(o + 2 * maxt);
-  L.chain = o; o = align16(o + 4 * maxch);
   L.total = o;
   return L;
 }
 
-// Track and chain storage per hit follow the densest events measured (0.07
-// candidates and 0.78 chain entries per hit) with margin; an event that runs
-// out is retried in the next larger class.
+// Track storage per hit follows the densest events measured (0.07
+// candidates per hit) with margin; an event that runs out is retried in the
+// next larger class.
 __host__ __device__ inline uint32_t caps_maxt(uint32_t maxh) { return maxh / 10 + 64; }
-__host__ __device__ inline uint32_t caps_maxch(uint32_t maxh) {
-  const uint32_t c = maxh / 10 * 9 + 256;
-  return c > 65535u ? 65535u : c;
-}
 
 Caps make_caps(uint32_t smem_budget, uint32_t n_modules, int n_threads) {
   const uint32_t nw = (uint32_t)n_threads / 32;
@@ -95,13 +88,12 @@ Caps make_caps(uint32_t smem_budget, uint32_t n_modules, int n_threads) {
   uint32_t lo = 32, hi = 65504;
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) / 2;
-    if (make_layout(mid, caps_maxt(mid), caps_maxch(mid), n_modules, nw).total <= smem_budget) lo = mid;
+    if (make_layout(mid, caps_maxt(mid), n_modules, nw).total <= smem_budget) lo = mid;
     else hi = mid - 1;
   }
   c.maxh = lo & ~31u;
   c.maxt = caps_maxt(c.maxh);
-  c.maxch = caps_maxch(c.maxh);
-  c.smem = make_layout(c.maxh, c.maxt, c.maxch, n_modules, nw).total;
+  c.smem = make_layout(c.maxh, c.maxt, n_modules, nw).total;
   return c;
 }
 
@@ -178,17 +170,18 @@ __device__ void defer_or_fail(const WorkView& wk, int queue, uint32_t e, uint32_
   }
 }
 
-// Hit positions of a candidate in stored (decreasing module) order.
-__device__ __forceinline__ void gather_hits(const uint32_t* chain, uint32_t head, uint32_t n, uint16_t* hl) {
-  uint32_t c = head;
-  for (int k = (int)n - 1; k >= 0; --k) {
-    const uint32_t ent = chain[c];
-    hl[k] = (uint16_t)(ent >> 16);
-    c = ent & 0xFFFFu;
+// Module of hit position p: positions of module m are [cb[4m], cb[4m + 4]).
+__device__ __forceinline__ int module_of(const uint16_t* cb, int nm, uint32_t p) {
+  int lo = 0, hi = nm - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cb[kSPM * mid] <= p) lo = mid;
+    else hi = mid - 1;
   }
+  return lo;
 }
 
-enum Misc { M_EVENT = 0, M_NTR = 1, M_NCH = 2, M_KEPT = 5, M_TBASE = 7, M_HBASE = 8, M_SKIP = 10, M_NACT = 12 };
+enum Misc { M_EVENT = 0, M_NTR = 1, M_KEPT = 5, M_TBASE = 7, M_HBASE = 8, M_SKIP = 10, M_NACT = 12 };
 
 // Phase B of round i for the middle hits of module i + 1 (positions
 // [kb0, kb1)): groups of GB lanes take the positions in turn; a group with an
@@ -199,9 +192,8 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
                                         const float2* pos, const uint16_t* pid, const uint32_t* used,
                                         const DevParams& par, const Caps& caps, uint32_t* s_misc, float* t_x,
                                         float* t_y, float* t_z, float* t_tx, float* t_ty, float* t_seed,
-                                        uint16_t* t_pa, uint16_t* t_pb, uint16_t* t_pc, uint16_t* t_head,
-                                        uint8_t* t_n, uint8_t* t_skip, uint32_t* chain, uint16_t* nxt,
-                                        uint32_t* nxt_cnt) {
+                                        uint16_t* t_pa, uint16_t* t_pb, uint16_t* t_pc, uint8_t* t_n,
+                                        uint8_t* t_skip, uint16_t* trk, uint16_t* nxt, uint32_t* nxt_cnt) {
   constexpr int NG = NT / GB;
   const int g = threadIdx.x / GB, gl = threadIdx.x % GB;
   const int ma = i + 2, mb = i + 1;
@@ -260,16 +252,15 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
     uint32_t t = 0;
     if (has && gl == 0 && best != ~0ull) {
       t = atomicAdd(&s_misc[M_NTR], 1u);
-      const uint32_t c = atomicAdd(&s_misc[M_NCH], 3u);
-      if (t >= caps.maxt || c + 3 > caps.maxch) {
+      if (t >= caps.maxt) {
         ovf = true;
       } else {
         const uint32_t pa = bpos >> 16, pc = bpos & 0xFFFFu;
-        chain[c] = (pa << 16) | kNone16;
-        chain[c + 1] = (pb << 16) | c;
-        chain[c + 2] = (pc << 16) | (c + 1);
+        uint16_t* th = trk + (size_t)t * kMaxModules;
+        th[0] = (uint16_t)pa;
+        th[1] = (uint16_t)pb;
+        th[2] = (uint16_t)pc;
         const float2 vc = pos[pc];
-        t_head[t] = (uint16_t)(c + 2);
         t_pa[t] = (uint16_t)pa;
         t_pb[t] = (uint16_t)pb;
         t_pc[t] = (uint16_t)pc;
@@ -289,13 +280,13 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
   return ovf;
 }
 
-template <int NT, int GB>
-__global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict__ geo, DevParams par,
+template <int NT, int GA, int GB>
+__global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry* __restrict__ geo, DevParams par,
                                                    EventsView ev, WorkView wk, Caps caps, int cls, int qi) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = NT / 32;
   const uint32_t nm = (uint32_t)geo->n_modules;
-  const Layout L = make_layout(caps.maxh, caps.maxt, caps.maxch, nm, NW);
+  const Layout L = make_layout(caps.maxh, caps.maxt, nm, NW);
   float* s_z = (float*)(smem + L.z);
   uint16_t* s_cb = (uint16_t*)(smem + L.cb);
   uint16_t* s_bins = (uint16_t*)(smem + L.bins);
@@ -303,7 +294,6 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
   uint32_t* s_scan = (uint32_t*)(smem + L.scan);
   float2* pos = (float2*)(smem + L.pos);
   uint16_t* pid = (uint16_t*)(smem + L.pid);
-  uint8_t* pmod = (uint8_t*)(smem + L.pmod);
   uint32_t* used = (uint32_t*)(smem + L.used);  // bitmap over positions
   float* t_x = (float*)(smem + L.t_x);
   float* t_y = (float*)(smem + L.t_y);
@@ -314,11 +304,11 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
   uint16_t* t_pa = (uint16_t*)(smem + L.t_pa);
   uint16_t* t_pb = (uint16_t*)(smem + L.t_pb);
   uint16_t* t_pc = (uint16_t*)(smem + L.t_pc);
-  uint16_t* t_head = (uint16_t*)(smem + L.t_head);
   uint8_t* t_n = (uint8_t*)(smem + L.t_n);
   uint8_t* t_skip = (uint8_t*)(smem + L.t_skip);
   uint16_t* act[2] = {(uint16_t*)(smem + L.act0), (uint16_t*)(smem + L.act1)};
-  uint32_t* chain = (uint32_t*)(smem + L.chain);
+  // this CTA's hit slots: kMaxModules positions per candidate
+  uint16_t* trk = wk.trk_hits[cls] + (size_t)blockIdx.x * caps.maxt * kMaxModules;
   uint32_t* t_key = (uint32_t*)t_x;    // after the rounds
   uint32_t* t_rank = (uint32_t*)t_y;
   uint32_t* t_hoff = (uint32_t*)t_z;   // indexed by rank
@@ -386,7 +376,6 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
           const uint32_t p = atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
           pos[p] = v;
           pid[p] = (uint16_t)k;
-          pmod[p] = (uint8_t)m;
         }
         __syncwarp();
       }
@@ -398,7 +387,6 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
     int cur = 0;              // active list of this round
     bool overflow = false;    // block-uniform (set through __syncthreads_or)
     for (int i = (int)nm - 3; i >= 0; --i) {
-      bool ovf = false;       // this thread ran out of track or chain storage
       const float zi = s_z[i];
       // phase A: hits of the newest seeds become used; every active track is
       // extended into module i by its best hit (one lane per track, the
@@ -412,19 +400,23 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
       const uint32_t nact = s_misc[M_NACT + cur];
       const uint16_t* alist = act[cur];
       uint16_t* nlist = act[cur ^ 1];
-      for (uint32_t j0 = 32u * warp; j0 < nact; j0 += NT) {
-        const uint32_t j = j0 + lane;
-        bool keep = false;
-        uint32_t t = 0;
-        if (j < nact) {
-          t = alist[j];
-          const float xl = t_x[t], yl = t_y[t], zl = t_z[t];
+      // GA lanes per track split its window and agree on the best hit
+      for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
+        const uint32_t j = j0 + lane / GA;
+        const int la = lane % GA;
+        const bool valid = j < nact;
+        const uint32_t t = valid ? alist[j] : 0u;
+        float xl = 0.0f, yl = 0.0f, zl = 0.0f, xp = 0.0f, yp = 0.0f;
+        unsigned long long best = ~0ull;
+        if (valid) {
+          xl = t_x[t];
+          yl = t_y[t];
+          zl = t_z[t];
           const float dzi = fsub(zi, zl);
-          const float xp = fadd(xl, fmul(t_tx[t], dzi));
-          const float yp = fadd(yl, fmul(t_ty[t], dzi));
-          unsigned long long best = ~0ull;
+          xp = fadd(xl, fmul(t_tx[t], dzi));
+          yp = fadd(yl, fmul(t_ty[t], dzi));
           const Cand cw = window_cands(s_bins, i, pseudo_angle(xl, yl), win);
-          for (uint32_t k = 0; k < cw.n(); ++k) {
+          for (uint32_t k = la; k < cw.n(); k += GA) {
             const uint32_t p = cw.at(k);
             const float2 v = pos[p];
             if (!phi_ok(xl, yl, v.x, v.y, tol)) continue;
@@ -433,26 +425,26 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
             if (!(s2 < par.max_scatter_fwd)) continue;
             best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)pid[p] << 16) | p);
           }
+        }
+#pragma unroll
+        for (int off = 1; off < GA; off <<= 1) best = min(best, __shfl_xor_sync(kFull, best, off));
+        bool keep = false;
+        if (valid && la == 0) {
           if (best != ~0ull) {
             const uint32_t p = (uint32_t)(best & 0xFFFFu);
-            const uint32_t c = atomicAdd(&s_misc[M_NCH], 1u);
-            if (c >= caps.maxch) {
-              ovf = true;
-            } else {
-              const float2 v = pos[p];
-              const float dzq = fsub(zl, zi);
-              chain[c] = (p << 16) | t_head[t];
-              t_head[t] = (uint16_t)c;
-              t_tx[t] = fdiv(fsub(xl, v.x), dzq);
-              t_ty[t] = fdiv(fsub(yl, v.y), dzq);
-              t_x[t] = v.x;
-              t_y[t] = v.y;
-              t_z[t] = zi;
-              t_n[t] = t_n[t] + 1;
-              t_skip[t] = 0;
-              set_bit(used, p);
-              keep = true;
-            }
+            const float2 v = pos[p];
+            const float dzq = fsub(zl, zi);
+            const uint32_t n = t_n[t];
+            trk[(size_t)t * kMaxModules + n] = (uint16_t)p;
+            t_tx[t] = fdiv(fsub(xl, v.x), dzq);
+            t_ty[t] = fdiv(fsub(yl, v.y), dzq);
+            t_x[t] = v.x;
+            t_y[t] = v.y;
+            t_z[t] = zi;
+            t_n[t] = (uint8_t)(n + 1);
+            t_skip[t] = 0;
+            set_bit(used, p);
+            keep = true;
           } else {
             const uint32_t sk = t_skip[t] + 1u;
             t_skip[t] = (uint8_t)min(sk, 255u);
@@ -461,13 +453,13 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
         }
         list_append(keep, (uint16_t)t, nlist, &s_misc[M_NACT + (cur ^ 1)]);
       }
-      if (__syncthreads_or(ovf)) { overflow = true; break; }
+      __syncthreads();
       seed_lo = seed_hi;
       if (tid == 0) s_misc[M_NACT + cur] = 0;  // read by everyone before the barrier; refilled next round
       // phase B: seeds with the middle hit b in module i + 1
-      ovf = phase_b<NT, GB>(i, s_cb[kSPM * (i + 1)], s_cb[kSPM * (i + 2)], s_z, s_bins, pos, pid, used, par, caps,
-                            s_misc, t_x, t_y, t_z, t_tx, t_ty, t_seed, t_pa, t_pb, t_pc, t_head, t_n, t_skip, chain,
-                            nlist, &s_misc[M_NACT + (cur ^ 1)]);
+      const bool ovf = phase_b<NT, GB>(i, s_cb[kSPM * (i + 1)], s_cb[kSPM * (i + 2)], s_z, s_bins, pos, pid, used, par, caps,
+                            s_misc, t_x, t_y, t_z, t_tx, t_ty, t_seed, t_pa, t_pb, t_pc, t_n, t_skip, trk, nlist,
+                            &s_misc[M_NACT + (cur ^ 1)]);
       if (__syncthreads_or(ovf)) { overflow = true; break; }
       cur ^= 1;
     }
@@ -487,11 +479,11 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
       for (uint32_t k = tid; k < 2 * nwords; k += NT) seen1[k] = 0;
       __syncthreads();
       for (uint32_t t = tid; t < ntr; t += NT) {
-        uint32_t c = t_head[t];
-        while (c != kNone16) {
-          const uint32_t ent = chain[c], p = ent >> 16, b = 1u << (p & 31);
+        const uint16_t* th = trk + (size_t)t * kMaxModules;
+        const uint32_t n = t_n[t];
+        for (uint32_t k = 0; k < n; ++k) {
+          const uint32_t p = th[k], b = 1u << (p & 31);
           if (atomicOr(&seen1[p >> 5], b) & b) atomicOr(&seen2[p >> 5], b);
-          c = ent & 0xFFFFu;
         }
       }
       __syncthreads();
@@ -508,21 +500,22 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
       const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
       const float kms = fit_kms(par);
       for (uint32_t t = tid; t < ntr; t += NT) {
-        uint16_t hl[kMaxModules];
+        const uint16_t* th = trk + (size_t)t * kMaxModules;
         const uint32_t n = t_n[t];
-        gather_hits(chain, t_head[t], n, hl);
         float st[12];
         fit_track(
             n,
             [&](uint32_t k, float& x, float& y, int& m) {
-              const float2 v = pos[hl[k]];
+              const uint32_t p = th[k];
+              const float2 v = pos[p];
               x = v.x;
               y = v.y;
-              m = pmod[hl[k]];
+              m = module_of(s_cb, (int)nm, p);
             },
             s_z, sig2, kms, st);
         float f[kMlpIn];
-        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, pmod[hl[0]], pmod[hl[n - 1]], f);
+        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, module_of(s_cb, (int)nm, th[0]),
+                     module_of(s_cb, (int)nm, th[n - 1]), f);
         const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
         t_seed[t] = logit;
         t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)pid[t_pa[t]] << 16) | pid[t_pb[t]]) : 0xFFFFFFFFu;
@@ -575,14 +568,15 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
     for (uint32_t t = tid; t < ntr; t += NT) {
       if (t_key[t] == 0xFFFFFFFFu) continue;
       const uint32_t r = t_rank[t], n = t_n[t];
-      uint16_t hl[kMaxModules];
-      gather_hits(chain, t_head[t], n, hl);
+      const uint16_t* th = trk + (size_t)t * kMaxModules;
       const uint32_t h0 = hb + t_hoff[r];
+      int m = (int)nm - 1;  // hits are stored by decreasing module
       for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t p = hl[k];
+        const uint32_t p = th[k];
+        while (s_cb[kSPM * m] > p) --m;
         wk.tr_hits[h0 + k] = pid[p];
         wk.tr_xy[h0 + k] = pos[p];
-        wk.tr_mod[h0 + k] = pmod[p];
+        wk.tr_mod[h0 + k] = (uint8_t)m;
       }
       const size_t o = (size_t)tb + r;
       wk.tr_logit[o] = use_mlp ? t_seed[t] : 0.0f;
@@ -592,14 +586,15 @@ __global__ void __launch_bounds__(NT) track_kernel(const DevGeometry* __restrict
   }
 }
 
-// Lanes per middle hit in phase B.
+// Lanes per active track in phase A and per middle hit in phase B.
+constexpr int kGroupA = 2;
 constexpr int kGroupB = 4;
 
 cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                          const Caps& caps, int cls, int queue, int n_threads, int n_ctas, cudaStream_t st) {
   switch (n_threads) {
-    case 128: track_kernel<128, kGroupB><<<n_ctas, 128, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
-    case 256: track_kernel<256, kGroupB><<<n_ctas, 256, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
+    case 128: track_kernel<128, kGroupA, kGroupB><<<n_ctas, 128, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
+    case 256: track_kernel<256, kGroupA, kGroupB><<<n_ctas, 256, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -607,16 +602,16 @@ cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const Eve
 
 cudaError_t track_set_smem_limit(int n_threads, int bytes) {
   switch (n_threads) {
-    case 128: return cudaFuncSetAttribute(track_kernel<128, kGroupB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    case 256: return cudaFuncSetAttribute(track_kernel<256, kGroupB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 128: return cudaFuncSetAttribute(track_kernel<128, kGroupA, kGroupB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 256: return cudaFuncSetAttribute(track_kernel<256, kGroupA, kGroupB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm) {
   switch (n_threads) {
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<128, kGroupB>, 128, smem);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<256, kGroupB>, 256, smem);
+    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<128, kGroupA, kGroupB>, 128, smem);
+    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<256, kGroupA, kGroupB>, 256, smem);
   }
   return cudaErrorInvalidValue;
 }
