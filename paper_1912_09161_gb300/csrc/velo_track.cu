@@ -54,7 +54,7 @@ __host__ __device__ inline Layout make_layout(uint32_t maxh, uint32_t maxt, uint
   L.z = o; o = align16(o + 4 * kMaxModules);
   L.cb = o; o = align16(o + 2 * (kMaxSensors + 1));
   L.bins = o; o = align16(o + 2 * nm * kNB);
-  L.wscr = o; o = align16(o + 4 * 32 * nw);
+  L.wscr = o; o = align16(o + 4 * kNB * nw);
   L.misc = o; o = align16(o + 4 * 32);
   L.scan = o; o = align16(o + 4 * 32);
   L.pos = o; o = align16(o + 8 * maxh);
@@ -106,7 +106,7 @@ __device__ __forceinline__ BinWindow bin_window(float pa, float w) {
   const int hi = (int)floorf((pa + w) * (kNB * 0.25f));
   int cnt = hi - lo + 1;
   if (cnt > kNB) cnt = kNB;
-  return BinWindow{((lo % kNB) + kNB) % kNB, cnt};
+  return BinWindow{lo & (kNB - 1), cnt};  // kNB is a power of two
 }
 
 // Candidate positions of module m in the phi window around pa: one or two
@@ -223,18 +223,30 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
         const float xp = fadd(vb.x, fmul(tx, dzc));
         const float yp = fadd(vb.y, fmul(ty, dzc));
         const unsigned long long ida = (unsigned long long)pid[pa] << 16;
-        for (uint32_t kc = 0; kc < cc.n(); ++kc) {
-          const uint32_t pc = cc.at(kc);
-          if (bit(used, pc)) continue;
-          const float2 vc = pos[pc];
-          if (!phi_ok(vb.x, vb.y, vc.x, vc.y, tol)) continue;
-          const float dx = fsub(vc.x, xp), dy = fsub(vc.y, yp);
-          const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-          if (!(s2 < par.max_scatter_seed)) continue;
-          const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | pid[pc];
-          if (key < best) {
-            best = key;
-            bpos = (pa << 16) | pc;
+        // candidates c four at a time: their loads are independent
+        const uint32_t nc = cc.n();
+        for (uint32_t kc = 0; kc < nc; kc += 4) {
+          uint32_t pcs[4];
+          float2 vcs[4];
+          bool ok[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            ok[u] = kc + u < nc;
+            pcs[u] = ok[u] ? cc.at(kc + u) : pb;
+            ok[u] = ok[u] && !bit(used, pcs[u]);
+            vcs[u] = pos[pcs[u]];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (!ok[u] || !phi_ok(vb.x, vb.y, vcs[u].x, vcs[u].y, tol)) continue;
+            const float dx = fsub(vcs[u].x, xp), dy = fsub(vcs[u].y, yp);
+            const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
+            if (!(s2 < par.max_scatter_seed)) continue;
+            const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | pid[pcs[u]];
+            if (key < best) {
+              best = key;
+              bpos = (pa << 16) | pcs[u];
+            }
           }
         }
       }
@@ -345,12 +357,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
       // one warp per module: its hits are the canonical ids [cb[4m], cb[4m+4]),
       // which are also its positions; count per bin, scan, scatter
       const uint32_t* so = ev.sensor_off + (size_t)e * ns;
-      uint32_t* wc = (uint32_t*)(smem + L.wscr) + 32 * warp;
+      constexpr int BPL = kNB / 32;  // bins per lane
+      uint32_t* wc = (uint32_t*)(smem + L.wscr) + kNB * warp;
       for (uint32_t m = warp; m < nm; m += NW) {
         const uint32_t s0 = kSPM * m;
         const uint32_t c0 = s_cb[s0], c1 = s_cb[s0 + 4];
         const uint32_t b1 = s_cb[s0 + 1], b2 = s_cb[s0 + 2], b3 = s_cb[s0 + 3];
-        wc[lane] = 0;
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) wc[BPL * lane + u] = 0;
         __syncwarp();
         for (uint32_t k = c0 + lane; k < c1; k += 32) {
           const uint32_t s = s0 + (k >= b1) + (k >= b2) + (k >= b3);
@@ -364,11 +378,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
           }
         }
         __syncwarp();
-        const uint32_t cnt = wc[lane];
-        const uint32_t incl = warp_incl_scan(cnt);
-        s_bins[m * kNB + lane] = (uint16_t)(c0 + incl);  // end of bin `lane`
+        uint32_t cnt[BPL], sum = 0;
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) {
+          cnt[u] = wc[BPL * lane + u];
+          sum += cnt[u];
+        }
+        uint32_t cur = c0 + warp_incl_scan(sum) - sum;  // start of this lane's first bin
         __syncwarp();
-        wc[lane] = c0 + incl - cnt;                      // cursor
+#pragma unroll
+        for (int u = 0; u < BPL; ++u) {
+          wc[BPL * lane + u] = cur;                          // cursor
+          cur += cnt[u];
+          s_bins[m * kNB + BPL * lane + u] = (uint16_t)cur;  // end of the bin
+        }
         __syncwarp();
         for (uint32_t k = c0 + lane; k < c1; k += 32) {
           const uint32_t s = s0 + (k >= b1) + (k >= b2) + (k >= b3);
@@ -416,14 +439,27 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
           xp = fadd(xl, fmul(t_tx[t], dzi));
           yp = fadd(yl, fmul(t_ty[t], dzi));
           const Cand cw = window_cands(s_bins, i, pseudo_angle(xl, yl), win);
-          for (uint32_t k = la; k < cw.n(); k += GA) {
-            const uint32_t p = cw.at(k);
-            const float2 v = pos[p];
-            if (!phi_ok(xl, yl, v.x, v.y, tol)) continue;
-            const float dx = fsub(v.x, xp), dy = fsub(v.y, yp);
-            const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-            if (!(s2 < par.max_scatter_fwd)) continue;
-            best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)pid[p] << 16) | p);
+          // this lane's candidates (every GA-th), four at a time
+          const uint32_t nw = cw.n();
+          for (uint32_t k0 = la; k0 < nw; k0 += 4 * GA) {
+            uint32_t ps[4];
+            float2 vs[4];
+            bool ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t k = k0 + (uint32_t)u * GA;
+              ok[u] = k < nw;
+              ps[u] = ok[u] ? cw.at(k) : 0u;
+              vs[u] = pos[ps[u]];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (!ok[u] || !phi_ok(xl, yl, vs[u].x, vs[u].y, tol)) continue;
+              const float dx = fsub(vs[u].x, xp), dy = fsub(vs[u].y, yp);
+              const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
+              if (!(s2 < par.max_scatter_fwd)) continue;
+              best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)pid[ps[u]] << 16) | ps[u]);
+            }
           }
         }
 #pragma unroll
