@@ -131,6 +131,30 @@ def test_big_events_class(V, geom):
     assert_parity(res, orc)
 
 
+def test_dense_modules(V, geom, cfg0_events):
+    """Three consecutive modules with about 700 extra isolated hits each: the
+    rounds over them take many passes of the seeding groups, and their phi
+    bins hold many hits each."""
+    ns = geom.n_sensors
+    lists = []
+    for e in (0, 1):
+        base = cfg0_events.subset(e, e + 1)
+        ev = [[(int(base.col[k]), int(base.row[k])) for k in range(int(base.sensor_off[s]), int(base.sensor_off[s + 1]))]
+              for s in range(ns)]
+        if e == 1:
+            grid = [(4 * a + 1, 4 * b + 1) for a in range(15) for b in range(12)]   # 180 isolated pixels
+            for m in (10, 11, 12):
+                for s in range(4 * m, 4 * m + 4):
+                    ev[s] = ev[s] + grid
+        lists.append(ev)
+    ev = velo_synth.make_events(lists, ns)
+    orc = oracle.reconstruct(geom, ev)
+    assert int(orc.cluster_off[2] - orc.cluster_off[1]) > int(orc.cluster_off[1]) + 2000
+    res = _run(V, geom, ev)
+    assert int(res.totals[3]) == 0
+    assert_parity(res, orc)
+
+
 def test_config1_full_size_sampled(V, geom):
     """The 10,000-event nominal batch in the benchmark's launch configuration;
     the oracle recomputes a sample of events one by one."""
