@@ -41,8 +41,10 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["nominal"][1]
 REF_SAMPLE = 2000           # events per oracle step of the reference arm
 CPU_SAMPLE = 10000          # events of the CPU-baseline sample (the whole batch)
+CPU_SECONDS = 10.0          # the CPU baseline repeats the sample for about this long
+CPU_MAX_PASSES = 30
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "reco_kernel_nominal_10k.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "track_kernel_nominal_10k.md")
 KERNELS_BASE = 4            # clustering, retry pass of the largest class, scan, emit (+ one per class)
 
 
@@ -156,11 +158,13 @@ def _profile_traffic(kernel_src: str) -> float | None:
 def _tracking_bytes(stats: dict, n_sensors: int) -> float:
     """Bytes the tracking kernel must move for one call: per event its hit
     positions (8 B per hit), canonical sensor bases (2 B x (n_sensors + 1))
-    and sensor offsets (4 B x (n_sensors + 1)) in; per track 13 state floats,
-    hit count (2 B) and hit offset (4 B), and 4 B per track hit out."""
+    and sensor offsets (4 B x (n_sensors + 1)) in; per kept track its hit
+    count (2 B), hit offset (4 B) and classifier logit (4 B), and 4 B per
+    track hit (canonical id) out.  The per-hit positions and modules it also
+    writes for the emit kernel's fit are not counted."""
     ev = sum(stats["events"])
     return (8.0 * sum(stats["clusters"]) + 6.0 * (n_sensors + 1) * ev
-            + 58.0 * sum(stats["tracks"]) + 4.0 * sum(stats["hits"]))
+            + 10.0 * sum(stats["tracks"]) + 4.0 * sum(stats["hits"]))
 
 
 def _step_bytes(n_pixels: int, n_events: int, n_sensors: int, n_tracks: int, n_track_hits: int) -> float:
@@ -209,9 +213,13 @@ def cpu_baseline(geom, ev, gpu_result=None) -> dict:
     sub = ev.subset(0, min(CPU_SAMPLE, ev.n_events))
     t0 = time.perf_counter()
     r = oracle.reconstruct(geom, sub, n_threads=cores)
+    passes = 1
+    while time.perf_counter() - t0 < CPU_SECONDS and passes < CPU_MAX_PASSES:
+        oracle.reconstruct(geom, sub, n_threads=cores)
+        passes += 1
     dt = time.perf_counter() - t0
-    out = {"value": sub.n_events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"first {sub.n_events} of the 10,000 events, all host cores ({dt:.1f} s)"}
+    out = {"value": passes * sub.n_events / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{passes} passes over the {sub.n_events} events of the workload, all host cores ({dt:.1f} s)"}
     if gpu_result is not None and sub.n_events == gpu_result.n_events:
         q = MET.summarize(sub, r.cluster_off, r.pix_cluster, gpu_result.track_off, gpu_result.hit_off,
                           gpu_result.hit_ids)

@@ -31,6 +31,15 @@
 
 using namespace velo;
 
+namespace velo {
+// Offsets of a request cut from a larger pixel array start at that array's
+// index p0; the device copy of the pixels starts at 0.
+__global__ void rebase_offsets_kernel(uint32_t* off, uint64_t n, uint32_t p0) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) off[i] -= p0;
+}
+}  // namespace velo
+
 namespace {
 
 int report(int code, const char* fmt, ...) {
@@ -83,12 +92,6 @@ ReqLayout layout(uint32_t n_sensors, uint32_t E, uint64_t P) {
   return L;
 }
 
-// Offsets of a request cut from a larger pixel array start at that array's
-// index p0; the device copy of the pixels starts at 0.
-__global__ void rebase_offsets_kernel(uint32_t* off, uint64_t n, uint32_t p0) {
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) off[i] -= p0;
-}
 
 struct Request {
   uint64_t id;
