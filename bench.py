@@ -73,6 +73,20 @@ def _max_over_ranks(x: float, dist) -> float:
     return float(t.item())
 
 
+def shard_config(cfg_index: int, rank: int):
+    """Workload of one rank: the configuration's batch with its own seed
+    (seed + 100 rank), so ranks reconstruct independent events and per-GPU
+    work stays fixed as ranks are added (weak scaling, no collective)."""
+    import velo_synth
+    cfg = velo_synth.config(cfg_index)
+    return velo_synth.config(cfg_index, seed=cfg.seed + 100 * rank)
+
+
+def aggregate_rate(world_size: int, events_per_rank: int, steps: int, slowest_s: float) -> float:
+    """Whole-job events/s: every rank's events over the slowest rank's time."""
+    return world_size * events_per_rank * steps / slowest_s
+
+
 def _barrier(dist):
     if dist is not None:
         dist.barrier()
@@ -283,8 +297,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     geom = velo_synth.geometry()
     cfg_index, workload = WORKLOADS[args.workload]
-    cfg = velo_synth.config(cfg_index)
-    ev = velo_synth.generate(velo_synth.config(cfg_index, seed=cfg.seed + 100 * rank))
+    ev = velo_synth.generate(shard_config(cfg_index, rank))
     V.load_library()
     rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
     d = V.upload_events(ev, dev)
@@ -326,7 +339,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     rc = rec.sync_status(sptr)
     total_s = _max_over_ranks(sum(step_ms) / 1e3, dist)
-    value = ws * ev.n_events * args.steps / total_s
+    value = aggregate_rate(ws, ev.n_events, args.steps, total_s)
 
     gpu_res = out.to_host(ev.n_events) if rank == 0 and ws == 1 else None
 
