@@ -2,10 +2,12 @@
 // the connected components of the fired pixels of a sensor; the raw input is
 // segmented by readout unit, so sensors are decoded in parallel, section 2.3).
 //
-// One CTA per event; warps take sensors from a per-event counter.  A sensor
-// of at most 64 pixels is clustered in registers (one or two pixels per
-// lane); a larger one is staged in the warp's shared-memory slice and joined
-// by union-find.  Every cluster becomes a hit at a provisional position (the
+// One CTA per event.  Sensors are sorted into size classes; warps take work
+// items from a per-event counter, largest sensors first.  A sensor of at most
+// 64 pixels is clustered in registers: up to 8, 16 or 32 pixels in a segment
+// of that many lanes (four, two or one sensor per warp), up to 64 with two
+// pixels per lane.  A larger one is staged in the warp's shared-memory slice
+// and joined by union-find.  Every cluster becomes a hit at a provisional position (the
 // sensor's pixel offset + the cluster's rank by smallest pixel key), which
 // orders hits exactly like their canonical ids; the per-sensor canonical
 // bases and the event's hit count go to global memory, and the event is
@@ -21,8 +23,12 @@ constexpr uint32_t kWarpStage = 1000;           // raw pixels a warp can stage f
 constexpr uint32_t kAccBytes = 8 * 64;          // per-warp packed accumulators
 constexpr uint32_t kWarpSlice = kAccBytes + 6 * kWarpStage;
 
+// Sensor size classes (raw pixels): <= 8, <= 16, <= 32, <= 64, <= kWarpStage,
+// beyond.  The first three are clustered 4, 2 and 1 at a time per warp.
+constexpr int kSizeClasses = 6;
+
 struct ClusterLayout {
-  uint32_t soff, ccnt, misc, scan, warps, total;
+  uint32_t soff, ccnt, misc, scan, lists, warps, total;
 };
 
 __host__ __device__ inline uint32_t c_align16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -34,6 +40,7 @@ __host__ __device__ inline ClusterLayout cluster_layout(int n_threads) {
   L.ccnt = o; o = c_align16(o + 4 * (kMaxSensors + 1));
   L.misc = o; o = c_align16(o + 4 * 32);
   L.scan = o; o = c_align16(o + 4 * 32);
+  L.lists = o; o = c_align16(o + kSizeClasses * kMaxSensors);  // u8 sensor ids per size class
   L.warps = o; o = c_align16(o + kWarpSlice * (uint32_t)(n_threads / 32));
   L.total = o;
   return L;
@@ -221,6 +228,95 @@ __device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const u
   return nroot;
 }
 
+// Sensors of at most W pixels (W = 8, 16 or 32), 32 / W at a time: lane l
+// works on sensor sens[l / W], pixel l % W (sens >= n_sensors: no sensor).
+// The steps of the one-sensor register path below, each confined to its
+// segment of W lanes (sort, repeated pixels, neighbour masks over segment
+// positions, smallest-position labels, member sums, ranks of the roots).
+// Writes every listed sensor's cluster count to s_cnt.
+template <int W>
+__device__ void cluster_segments(const DevGeometry* __restrict__ geo, const uint16_t* __restrict__ col,
+                                 const uint16_t* __restrict__ row, const uint32_t* s_soff, uint32_t sensor,
+                                 int ns, const HitOut& out, unsigned long long* acc, uint32_t* s_cnt, bool& bad) {
+  static_assert(W == 8 || W == 16 || W == 32, "segment width");
+  const int lane = threadIdx.x & 31, seg = lane / W, sl = lane % W;
+  const uint32_t segmask = (W == 32) ? kFull : (((1u << W) - 1u) << (seg * W));
+  const bool have = sensor < (uint32_t)ns;
+  const uint32_t a = have ? s_soff[sensor] : 0u, n = have ? s_soff[sensor + 1] - a : 0u;
+  uint32_t k = kInv;
+  if ((uint32_t)sl < n) {
+    const uint32_t c = col[a + sl], w = row[a + sl];
+    if (c < (uint32_t)geo->n_cols && w < (uint32_t)geo->n_rows) k = (c << 9) | w;
+    else bad = true;
+  }
+  // bitonic sort within the segment (invalid pixels sort last)
+#pragma unroll
+  for (int kk = 2; kk <= W; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const uint32_t o = __shfl_xor_sync(kFull, k, j);
+      const bool up = (sl & kk) == 0, lower = (sl & j) == 0;
+      k = (lower == up) ? min(k, o) : max(k, o);
+    }
+  }
+  const uint32_t prev = __shfl_up_sync(kFull, k, 1, W);
+  const bool valid = k != kInv && !(sl > 0 && prev == k);
+  const uint32_t vseg = (__ballot_sync(kFull, valid) & segmask) >> (seg * W);  // valid segment positions
+  // neighbour masks over segment positions, scanning outward until out of reach
+  uint32_t nb = 0;
+  for (int d = 1; d < W; ++d) {
+    const uint32_t kf = __shfl_down_sync(kFull, k, d, W), kb = __shfl_up_sync(kFull, k, d, W);
+    bool reach = false;
+    if (valid) {
+      if (sl + d < W && kf != kInv && kf - k <= 513u) {
+        reach = true;
+        const uint32_t dl = kf - k;
+        if (dl == 1u || dl - 511u <= 2u) nb |= 1u << (sl + d);
+      }
+      if (sl >= d && k - kb <= 513u) {
+        reach = true;
+        const uint32_t dl = k - kb;
+        if (dl == 1u || dl - 511u <= 2u) nb |= 1u << (sl - d);
+      }
+    }
+    if (!__any_sync(kFull, reach)) break;
+  }
+  nb &= vseg;
+  // propagate the smallest position over the neighbour masks
+  uint32_t lab = (uint32_t)sl;
+  while (true) {
+    bool ch = false;
+    uint32_t bits = nb;
+    const uint32_t cnt = __reduce_max_sync(kFull, (uint32_t)__popc(bits));
+    for (uint32_t it = 0; it < cnt; ++it) {
+      const int q = bits ? __ffs(bits) - 1 : sl;
+      bits &= bits - 1;
+      const uint32_t lq = __shfl_sync(kFull, lab, q, W);
+      if (lq < lab) {
+        lab = lq;
+        ch = true;
+      }
+    }
+    if (!__any_sync(kFull, ch)) break;
+  }
+  // member sums at the root: count << 56 | sum(col) << 28 | sum(row)
+  acc[lane] = 0ull;
+  __syncwarp();
+  if (valid) atomicAdd(&acc[seg * W + lab], (1ull << 56) | ((unsigned long long)(k >> 9) << 28) | (k & 511u));
+  __syncwarp();
+  const bool root = valid && lab == (uint32_t)sl;
+  const uint32_t rseg = (__ballot_sync(kFull, root) & segmask) >> (seg * W);
+  if (root) {
+    const unsigned long long v = acc[lane];
+    const uint32_t key16 = ((k >> 9) << 8) | (k & 255u);
+    const uint32_t rank = __popc(rseg & ((1u << sl) - 1u));
+    store_cluster(out, sensor_geo(geo, (int)sensor), a + rank, key16, (uint32_t)(v >> 56),
+                  (uint32_t)((v >> 28) & 0xFFFFFFFull), (uint32_t)(v & 0xFFFFFFFull));
+  }
+  if (have && sl == 0) s_cnt[sensor] = __popc(rseg);
+  __syncwarp();
+}
+
 // lock-free union-find on local indices; the root with the larger pixel key
 // is hooked under the root with the smaller key, so roots end at the
 // component's smallest key (parent pointers always lead to smaller keys)
@@ -300,7 +396,7 @@ __device__ uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const 
   return nroot;
 }
 
-enum { CM_NEXT = 0, CM_STATUS = 1 };
+enum { CM_NEXT = 0, CM_STATUS = 1, CM_CLASS = 8 };  // CM_CLASS..: sensors per size class
 
 template <int NT>
 __global__ void __launch_bounds__(NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
@@ -311,6 +407,7 @@ __global__ void __launch_bounds__(NT) cluster_kernel(const DevGeometry* __restri
   uint32_t* s_cnt = (uint32_t*)(smem + L.ccnt);
   uint32_t* s_misc = (uint32_t*)(smem + L.misc);
   uint32_t* s_scan = (uint32_t*)(smem + L.scan);
+  uint8_t* s_list = (uint8_t*)(smem + L.lists);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   unsigned char* slice = smem + L.warps + warp * kWarpSlice;
   unsigned long long* acc = (unsigned long long*)slice;
@@ -340,19 +437,43 @@ __global__ void __launch_bounds__(NT) cluster_kernel(const DevGeometry* __restri
     const uint16_t* row = ev.row + gbase;
     const HitOut out{wk.prov + gbase, wk.prov_key ? wk.prov_key + gbase : nullptr};
     bool bad = false, big = false;
-    while (true) {
-      uint32_t s = 0;
-      if (lane == 0) s = atomicAdd(&s_misc[CM_NEXT], 1u);
-      s = __shfl_sync(kFull, s, 0);
-      if (s >= (uint32_t)ns) break;
-      const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
-      const SensorGeo g = sensor_geo(geo, (int)s);
-      uint32_t nroot;
-      if (n <= 32) nroot = cluster_sensor_reg<1>(col, row, a, n, ncols, nrows, g, out, acc, bad);
-      else if (n <= 64) nroot = cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, out, acc, bad);
-      else if (n <= kWarpStage) nroot = cluster_sensor_smem(col, row, a, n, ncols, nrows, g, out, w_pk, w_par, bad);
-      else { nroot = 0; big = true; }
-      if (lane == 0) s_cnt[s] = nroot;
+    // sensors by size class
+    for (int s = tid; s < ns; s += NT) {
+      const uint32_t n = s_soff[s + 1] - s_soff[s];
+      const int c = n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : n <= 64 ? 3 : n <= kWarpStage ? 4 : 5;
+      const uint32_t p = atomicAdd(&s_misc[CM_CLASS + c], 1u);
+      s_list[c * kMaxSensors + p] = (uint8_t)s;
+    }
+    __syncthreads();
+    // work items, largest sensors first: one sensor each of classes 4, 3, 2,
+    // two of class 1, four of class 0 (class 5 is beyond the staging capacity)
+    const uint32_t n0 = s_misc[CM_CLASS + 0], n1 = s_misc[CM_CLASS + 1], n2 = s_misc[CM_CLASS + 2];
+    const uint32_t n3 = s_misc[CM_CLASS + 3], n4 = s_misc[CM_CLASS + 4];
+    big = s_misc[CM_CLASS + 5] != 0;
+    const uint32_t e4 = n4, e3 = e4 + n3, e2 = e3 + n2, e1 = e2 + (n1 + 1) / 2, e0 = e1 + (n0 + 3) / 4;
+    while (!big) {
+      uint32_t it = 0;
+      if (lane == 0) it = atomicAdd(&s_misc[CM_NEXT], 1u);
+      it = __shfl_sync(kFull, it, 0);
+      if (it >= e0) break;
+      if (it < e3) {
+        const uint32_t s = s_list[(it < e4 ? 4 : 3) * kMaxSensors + (it < e4 ? it : it - e4)];
+        const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
+        const SensorGeo g = sensor_geo(geo, (int)s);
+        const uint32_t nroot =
+            n <= 64 ? cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, out, acc, bad)
+                    : cluster_sensor_smem(col, row, a, n, ncols, nrows, g, out, w_pk, w_par, bad);
+        if (lane == 0) s_cnt[s] = nroot;
+      } else if (it < e2) {
+        cluster_segments<32>(geo, col, row, s_soff, s_list[2 * kMaxSensors + (it - e3)], ns, out, acc, s_cnt, bad);
+      } else if (it < e1) {
+        const uint32_t j = 2 * (it - e2) + (uint32_t)(lane / 16);
+        cluster_segments<16>(geo, col, row, s_soff, j < n1 ? s_list[1 * kMaxSensors + j] : 0xFFFFu, ns, out, acc,
+                             s_cnt, bad);
+      } else {
+        const uint32_t j = 4 * (it - e1) + (uint32_t)(lane / 8);
+        cluster_segments<8>(geo, col, row, s_soff, j < n0 ? s_list[j] : 0xFFFFu, ns, out, acc, s_cnt, bad);
+      }
     }
     if (__any_sync(kFull, bad) && lane == 0) atomicOr(&s_misc[CM_STATUS], VELO_EV_BAD_PIXEL);
     if (__syncthreads_or(big)) {  // a sensor beyond the warp's staging capacity
