@@ -231,13 +231,21 @@ typedef struct velo_stats {
 } velo_stats;
 
 /*
- * Launch schedule of the tracking kernel (paper section 2.3 maps one event to
- * one block; the schedule only decides how blocks share the GPU).  Events run
- * in the smallest shared-memory class that holds their hits; class_mask
- * selects the classes by CTAs per SM: bit 0 = 8, 1 = 6, 2 = 4, 3 = 3, 4 = 2,
- * 5 = 1 (always present); at most four classes.  concurrent = 1 runs the
- * classes on their own streams at once, 0 one after another.  Results are
- * identical under every schedule.  Default: {256, 0x1C, 1} (4, 3, 2, 1 CTAs per SM).
+ * Launch schedule of the tracking kernels (paper section 2.3 maps one event
+ * to one block; the schedule only decides how blocks share the GPU).  Events
+ * run in the first class that holds their hits.  class_mask selects the
+ * classes:
+ *   bit 6: the module-window class (128 threads, eight CTAs per SM, up to
+ *          8192 hits; it keeps only the three modules of a round and the
+ *          next one in shared memory);
+ *   bits 0-5: whole-event classes by CTAs per SM: bit 0 = 8, 1 = 6, 2 = 4,
+ *          3 = 3, 4 = 2, 5 = 1 (always present), track_threads each; a class
+ *          that holds no more hits than the classes before it is skipped.
+ * At most four classes.  Events that outgrow their class go to a retry pass
+ * of the last (one-CTA-per-SM) class.  concurrent = 1 runs the classes on
+ * their own streams at once, 0 one after another.  Results are identical
+ * under every schedule.  Default: {256, 0x60, 1} (module-window class, then
+ * one CTA per SM).
  */
 typedef struct velo_schedule {
   uint32_t track_threads;  /* 128 or 256 threads per tracking CTA */

@@ -56,12 +56,16 @@ struct velo_handle {
   // clustering kernel
   int cl_threads = 256;
   // tracking-kernel classes (increasing shared-memory plans), each on its stream
-  velo_schedule sched{256, 0x1Cu, 1};  // 4, 3, 2, 1 CTAs per SM (bits over kPerSm), concurrent
+  velo_schedule sched{256, 0x60u, 1};  // module-window class, then 1 CTA per SM (bits over kPerSm), concurrent
   int n_classes = 0;
   Caps caps[kMaxClasses]{};
   int per_sm[kMaxClasses]{};
   int threads = 256;
   int ctas[kMaxClasses]{};
+  bool ring_cls[kMaxClasses]{};  // class k runs the module-window kernel
+  // module-window kernel: CTAs per SM and its per-CTA global regions
+  int ring_per_sm = 0;
+  void* ring_buf = nullptr;
   int smem_sm = 0, smem_optin = 0;
   // captured launch sequences, replayed while the call descriptors match
   bool use_graphs = false;
@@ -230,6 +234,8 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
 // CTAs per SM of the candidate classes; a schedule's class_mask selects
 // from this list (at most kMaxClasses; one CTA per SM is always included).
 constexpr int kPerSm[6] = {8, 6, 4, 3, 2, 1};
+// class_mask bit of the module-window class (128 threads, eight CTAs per SM).
+constexpr uint32_t kRingClassBit = 1u << 6;
 
 // Hit-slot bytes of a class plan: kMaxModules u16 per candidate, max_tracks
 // candidates per CTA.
@@ -255,14 +261,54 @@ size_t trk_bytes_bound(const velo_handle* h) {
   return best;
 }
 
+// The module-window kernel's CTAs per SM and the global regions of all its
+// CTAs (array by array, each 256-byte aligned).  Without room for one CTA
+// per SM the class is left out of every schedule.
+int setup_ring(velo_handle* h) {
+  cudaError_t e = ring_set_smem_limit();
+  if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(ring): %s", cudaGetErrorString(e));
+  int occ = 0;
+  e = ring_occupancy(&occ);
+  if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "occupancy query (ring): %s", cudaGetErrorString(e));
+  if (occ < 1) return VELO_OK;
+  h->ring_per_sm = occ > 8 ? 8 : occ;
+  const size_t n = (size_t)h->ring_per_sm * h->n_sm;
+  size_t o = 0;
+  const size_t o_pos = o; o = align256(o + n * kRingPosCap * sizeof(float2));
+  const size_t o_pid = o; o = align256(o + n * kRingPosCap * sizeof(uint16_t));
+  const size_t o_bins = o; o = align256(o + n * kMaxModules * kNB * sizeof(uint16_t));
+  const size_t o_trk = o; o = align256(o + n * kRingMaxT * kRingTrackHits * sizeof(uint16_t));
+  const size_t o_sp = o; o = align256(o + n * 3 * kRingMaxT * sizeof(uint16_t));
+  const size_t o_n = o; o = align256(o + n * kRingMaxT);
+  const size_t o_seed = o; o = align256(o + n * kRingMaxT * sizeof(float));
+  e = cudaMalloc(&h->ring_buf, o);
+  if (e != cudaSuccess) {
+    h->ring_buf = nullptr;
+    return fail(VELO_ERR_NOMEM, "cudaMalloc(%zu) (ring): %s", o, cudaGetErrorString(e));
+  }
+  char* b = (char*)h->ring_buf;
+  h->wk.ring = RingScratch{(float2*)(b + o_pos), (uint16_t*)(b + o_pid), (uint16_t*)(b + o_bins),
+                           (uint16_t*)(b + o_trk), (uint16_t*)(b + o_sp), (uint8_t*)(b + o_n), (float*)(b + o_seed)};
+  return VELO_OK;
+}
+
 int build_classes(velo_handle* h, const velo_schedule& sc) {
   if (sc.track_threads != 128 && sc.track_threads != 256)
     return fail(VELO_ERR_INPUT, "schedule: track_threads must be 128 or 256");
   const int threads = (int)sc.track_threads;
   Caps caps[kMaxClasses]{};
   int per_sm[kMaxClasses]{}, n = 0;
+  bool ring[kMaxClasses]{};
   uint32_t prev_maxh = 0;
   const uint32_t mask = sc.class_mask | (1u << 5);
+  if ((mask & kRingClassBit) && h->ring_per_sm > 0) {
+    // module-window class first: every event of up to kRingMaxH hits
+    caps[0] = Caps{kRingMaxH, kRingMaxT, ring_smem_bytes()};
+    per_sm[0] = h->ring_per_sm;
+    ring[0] = true;
+    n = 1;
+    prev_maxh = kRingMaxH;
+  }
   for (int i = 0; i < 6; ++i) {
     if (!((mask >> i) & 1u)) continue;
     uint32_t budget = (uint32_t)(h->smem_sm / kPerSm[i]) - 1024u;
@@ -281,8 +327,10 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     prev_maxh = c.maxh;
   }
   if (n == 0) return fail(VELO_ERR_INPUT, "schedule: no class");
+  if (ring[n - 1]) return fail(VELO_ERR_INPUT, "schedule: no whole-event class for the retry pass");
   size_t need = 0;
-  for (int k = 0; k < n; ++k) need += class_trk_bytes(caps[k], per_sm[k] * h->n_sm);
+  for (int k = 0; k < n; ++k)
+    if (!ring[k]) need += class_trk_bytes(caps[k], per_sm[k] * h->n_sm);
   if (need > h->trk_bytes) return fail(VELO_ERR_NOMEM, "schedule: hit slots need %zu bytes, have %zu", need, h->trk_bytes);
   cudaError_t e = track_set_smem_limit(threads, (int)caps[n - 1].smem);
   if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e));
@@ -294,15 +342,22 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     h->per_sm[k] = k < n ? per_sm[k] : 0;
     h->ctas[k] = k < n ? per_sm[k] * h->n_sm : 0;
     h->wk.class_maxh[k] = k < n ? caps[k].maxh : 0;
+    h->ring_cls[k] = k < n && ring[k];
   }
   h->wk.n_classes = n;
   size_t off = 0;
   for (int k = 0; k < kMaxClasses; ++k) {
-    h->wk.trk_hits[k] = k < n ? h->trk + off : nullptr;
-    if (k < n) off += (size_t)h->ctas[k] * caps[k].maxt * kMaxModules;
+    h->wk.trk_hits[k] = k < n && !ring[k] ? h->trk + off : nullptr;
+    if (k < n && !ring[k]) off += (size_t)h->ctas[k] * caps[k].maxt * kMaxModules;
   }
   h->version++;
   return VELO_OK;
+}
+
+// Tracking kernel of class k on its own queue.
+cudaError_t launch_class(velo_handle* h, const EventsView& ev, const WorkView& wk, int k, cudaStream_t st) {
+  if (h->ring_cls[k]) return launch_track_ring(h->d_geo, h->par, ev, wk, k, k, h->ctas[k], st);
+  return launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], st);
 }
 
 // The launch sequence of one call: counters, clustering, tracking classes
@@ -325,13 +380,13 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
       CUDA_TRY(cudaEventRecord(h->fork, st));
       for (int k = h->n_classes - 1; k >= 0; --k) {
         CUDA_TRY(cudaStreamWaitEvent(h->cls_stream[k], h->fork, 0));
-        CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], h->cls_stream[k]));
+        CUDA_TRY(launch_class(h, ev, wk, k, h->cls_stream[k]));
         CUDA_TRY(cudaEventRecord(h->join[k], h->cls_stream[k]));
       }
       for (int k = 0; k < h->n_classes; ++k) CUDA_TRY(cudaStreamWaitEvent(st, h->join[k], 0));
     } else {
       for (int k = h->n_classes - 1; k >= 0; --k)
-        CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], st));
+        CUDA_TRY(launch_class(h, ev, wk, k, st));
     }
     // events that ran out of track storage in their class: largest plan
     const int big = h->n_classes - 1;
@@ -484,6 +539,8 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     h->wk.cnt = h->d_cnt;
     h->d_mlp = base + fx.mlp;
     carve_work(h, base + fx.total, h->cfg);
+    rc = setup_ring(h);
+    if (rc) break;
     h->trk_bytes = trk_bytes_bound(h);
     e = cudaMalloc(&h->trk, h->trk_bytes);
     if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", h->trk_bytes, cudaGetErrorString(e)); h->trk = nullptr; break; }
@@ -523,6 +580,7 @@ void velo_destroy(velo_handle* h) {
   if (h->arena) cudaFree(h->arena);
   if (h->stage) cudaFree(h->stage);
   if (h->trk) cudaFree(h->trk);
+  if (h->ring_buf) cudaFree(h->ring_buf);
   if (h->h_totals) cudaFreeHost(h->h_totals);
   delete h;
 }
@@ -536,10 +594,10 @@ int velo_describe(const velo_handle* h, char* buf, size_t n) {
                    h->sched.concurrent, h->cl_threads, cluster_smem_bytes(h->cl_threads));
   for (int k = 0; k < h->n_classes && w > 0 && (size_t)w < n; ++k)
     w += snprintf(buf + w, n - w,
-                  "%s{\"threads\": %d, \"ctas_per_sm\": %d, \"ctas\": %d, \"smem\": %u, \"max_hits\": %u, "
-                  "\"max_tracks\": %u}",
-                  k ? ", " : "", h->threads, h->per_sm[k], h->ctas[k], h->caps[k].smem, h->caps[k].maxh,
-                  h->caps[k].maxt);
+                  "%s{\"kernel\": \"%s\", \"threads\": %d, \"ctas_per_sm\": %d, \"ctas\": %d, \"smem\": %u, "
+                  "\"max_hits\": %u, \"max_tracks\": %u}",
+                  k ? ", " : "", h->ring_cls[k] ? "window" : "event", h->ring_cls[k] ? kRingThreads : h->threads,
+                  h->per_sm[k], h->ctas[k], h->caps[k].smem, h->caps[k].maxh, h->caps[k].maxt);
   if (w > 0 && (size_t)w < n) snprintf(buf + w, n - w, "]}");
   return VELO_OK;
 }
@@ -590,12 +648,14 @@ int velo_get_schedule(const velo_handle* h, velo_schedule* sc) {
 int velo_autotune(velo_handle* h, const velo_events* events, const velo_output* out, void* stream,
                   velo_schedule* best_out, float* best_ms) {
   if (!h || !events || !out) return fail(VELO_ERR_INPUT, "velo_autotune: null argument");
-  // threads per tracking CTA, classes (bits over 8, 6, 4, 3, 2, 1 CTAs per SM), concurrency
-  //   256 threads: {4,3,2,1} concurrent and in sequence, {4,2,1}, {3,2,1}, {2,1}, {4,1}
-  //   128 threads: {8,4,2,1} concurrent and in sequence, {6,4,2,1}, {8,6,4,1}, {6,3,1}, {4,2,1}
+  // threads per whole-event CTA, classes (bit 6: module window; bits over 8,
+  // 6, 4, 3, 2, 1 CTAs per SM), concurrency
+  //   window + 1, concurrent and in sequence; window + {2,1}
+  //   256 threads: {4,3,2,1} concurrent and in sequence, {4,2,1}, {3,2,1}, {2,1}
+  //   128 threads: {8,4,2,1}, {6,4,2,1}
   static const velo_schedule cand[] = {
-      {256, 0x1Cu, 1}, {256, 0x1Cu, 0}, {256, 0x14u, 1}, {256, 0x18u, 1}, {256, 0x10u, 1}, {256, 0x04u, 1},
-      {128, 0x15u, 1}, {128, 0x15u, 0}, {128, 0x16u, 1}, {128, 0x07u, 1}, {128, 0x0Au, 1}, {128, 0x14u, 1},
+      {256, 0x60u, 1}, {256, 0x60u, 0}, {256, 0x70u, 1}, {256, 0x1Cu, 1}, {256, 0x1Cu, 0}, {256, 0x14u, 1},
+      {256, 0x18u, 1}, {256, 0x10u, 1}, {128, 0x15u, 1}, {128, 0x16u, 1},
   };
   cudaStream_t st = (cudaStream_t)stream;
   const bool graphs = h->use_graphs, timing = h->timing;

@@ -20,6 +20,17 @@ constexpr int kMlpIn = 10, kMlpH = 32;
 constexpr int kMlpParams = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1441
 constexpr int kMlpNormOffset = (2 * kMlpParams + 15) & ~15;  // byte offset of the float normalisation
 
+// Module-window tracking kernel (velo_track_ring.cu): CTA size and the
+// capacities of its shared-memory window and global region; an event beyond
+// any of them goes to the retry queue.
+constexpr int kRingThreads = 128;
+constexpr uint32_t kRingModHits = 256;    // hits of one module
+constexpr uint32_t kRingMaxH = 8192;      // hits of one event
+constexpr uint32_t kRingMaxAct = 192;     // active tracks in one round
+constexpr uint32_t kRingMaxT = 512;       // track candidates of one event
+constexpr uint32_t kRingTrackHits = 32;   // hits of one candidate
+constexpr uint32_t kRingPosCap = kRingMaxH + 8 * kMaxModules;  // module blocks padded to 8 hits
+
 // Device copy of the geometry (in the handle's arena).
 struct DevGeometry {
   int n_modules, n_sensors, n_cols, n_rows;
@@ -75,6 +86,23 @@ struct Counters {
   unsigned long long cls_pixels[kMaxClasses];  // raw pixels of the completed events
 };
 
+// Global region of the module-window kernel, one per CTA (arrays of
+// n_ctas regions): hits by (module, phi bin), each module's block at a
+// multiple of 8 hits; per-module phi-bin ends; candidate hit lists; seeds.
+struct RingScratch {
+  float2* pos;        // [kRingPosCap] per CTA
+  uint16_t* pid;      // [kRingPosCap] canonical ids
+  uint16_t* bins;     // [kMaxModules * kNB] module-local bin ends
+  uint16_t* trk;      // [kRingMaxT * kRingTrackHits] hit positions per candidate
+  uint16_t* seed_pos; // [3 * kRingMaxT] seed hit positions a, b, c
+  uint8_t* n_hits;    // [kRingMaxT]
+  float* seed;        // [kRingMaxT] seed scatter, then the classifier logit
+};
+
+// Bytes of one CTA's region.
+constexpr size_t kRingCtaBytes = (size_t)kRingPosCap * (8 + 2) + (size_t)kMaxModules * kNB * 2 +
+                                 (size_t)kRingMaxT * kRingTrackHits * 2 + (size_t)kRingMaxT * (3 * 2 + 1 + 4);
+
 // Device views.
 struct EventsView {
   uint32_t n_events;
@@ -105,6 +133,7 @@ struct WorkView {
   // tracking-kernel hit slots per class: kMaxModules positions per candidate,
   // max_tracks candidates per CTA, one region per CTA of the class
   uint16_t* trk_hits[kMaxClasses];
+  RingScratch ring;
   uint32_t cap_tracks, cap_hits;
   // scratch clusters (canonical, at the event's pixel base), may be null
   float* cl_x;
@@ -128,6 +157,13 @@ cudaError_t track_set_smem_limit(int n_threads, int bytes);
 cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm);
 cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                          const Caps& caps, int cls, int queue, int n_threads, int n_ctas, cudaStream_t st);
+
+// Module-window tracking kernel (velo_track_ring.cu).
+uint32_t ring_smem_bytes();
+cudaError_t ring_set_smem_limit();
+cudaError_t ring_occupancy(int* blocks_per_sm);
+cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
+                              int cls, int queue, int n_ctas, cudaStream_t st);
 
 // Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);

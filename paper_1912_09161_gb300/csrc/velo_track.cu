@@ -19,16 +19,17 @@
 // used flags and the windows refer to positions, every decision that prefers
 // one hit to another compares canonical ids.  Each candidate's hit positions
 // are appended to a fixed slot in global memory (the CTA's own region, reused
-// event after event), which only the cuts and the output read back.  All tracking decisions use explicit round-to-nearest IEEE
-// single-precision operations in a fixed order, so results do not depend on
-// the order of hits within a bin, the schedule, the thread count or the class
-// an event runs in.
+// event after event), which only the cuts and the output read back.  All
+// tracking decisions use explicit round-to-nearest IEEE single-precision
+// operations in a fixed order, so results do not depend on the order of hits
+// within a bin, the schedule, the thread count or the class an event runs in.
 #include <math.h>
 #include <stdint.h>
 
 #include "velo_device.cuh"
 #include "velo_fit.cuh"
 #include "velo_mlp.cuh"
+#include "velo_track_common.cuh"
 
 namespace velo {
 
@@ -95,90 +96,6 @@ Caps make_caps(uint32_t smem_budget, uint32_t n_modules, int n_threads) {
   c.maxt = caps_maxt(c.maxh);
   c.smem = make_layout(c.maxh, c.maxt, n_modules, nw).total;
   return c;
-}
-
-// Visits the phi bins of a module covering [pa - w, pa + w] (wrapping).
-struct BinWindow {
-  int first, count;
-};
-__device__ __forceinline__ BinWindow bin_window(float pa, float w) {
-  const int lo = (int)floorf((pa - w) * (kNB * 0.25f));
-  const int hi = (int)floorf((pa + w) * (kNB * 0.25f));
-  int cnt = hi - lo + 1;
-  if (cnt > kNB) cnt = kNB;
-  return BinWindow{lo & (kNB - 1), cnt};  // kNB is a power of two
-}
-
-// Candidate positions of module m in the phi window around pa: one or two
-// contiguous ranges (bins[k] = end position of bin k of the event).
-struct Cand {
-  uint32_t s0, n0, s1, n1;
-  __device__ __forceinline__ uint32_t n() const { return n0 + n1; }
-  __device__ __forceinline__ uint32_t at(uint32_t k) const { return k < n0 ? s0 + k : s1 + (k - n0); }
-};
-__device__ __forceinline__ Cand window_cands(const uint16_t* bins, int m, float pa, float w) {
-  const BinWindow bw = bin_window(pa, w);
-  const int base = m * kNB;
-  const int last = bw.first + bw.count - 1;
-  Cand c;
-  c.s0 = (base + bw.first) ? bins[base + bw.first - 1] : 0u;
-  if (last < kNB) {
-    c.n0 = bins[base + last] - c.s0;
-    c.s1 = 0;
-    c.n1 = 0;
-  } else {
-    c.n0 = bins[base + kNB - 1] - c.s0;
-    c.s1 = base ? bins[base - 1] : 0u;
-    c.n1 = bins[base + last - kNB] - c.s1;
-  }
-  return c;
-}
-
-// phi compatibility of two hits: |x_p y_q - y_p x_q| <= tol * (x_p x_q + y_p y_q), dot > 0
-__device__ __forceinline__ bool phi_ok(float xp, float yp, float xq, float yq, float tol) {
-  const float dot = fadd(fmul(xp, xq), fmul(yp, yq));
-  const float cross = fsub(fmul(xp, yq), fmul(yp, xq));
-  return dot > 0.0f && fabsf(cross) <= fmul(tol, dot);
-}
-
-__device__ __forceinline__ bool bit(const uint32_t* bm, uint32_t p) { return (bm[p >> 5] >> (p & 31)) & 1u; }
-__device__ __forceinline__ void set_bit(uint32_t* bm, uint32_t p) { atomicOr(&bm[p >> 5], 1u << (p & 31)); }
-
-// Appends val for every lane with pred to list (counter in shared memory);
-// called by all lanes of the warp.
-__device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* list, uint32_t* counter) {
-  const uint32_t m = __ballot_sync(kFull, pred);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(m) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(counter, (uint32_t)__popc(m));
-  base = __shfl_sync(kFull, base, leader);
-  if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = val;
-}
-
-// An event that runs out of storage in its class goes to the retry queue,
-// which the largest class drains after all classes finish; running out there
-// marks the event.
-__device__ void defer_or_fail(const WorkView& wk, int queue, uint32_t e, uint32_t gbase, uint32_t H, uint32_t status) {
-  if (queue != kRetryQueue) {
-    const uint32_t pos = atomicAdd(&wk.cnt->queue_len[kRetryQueue], 1u);
-    wk.queue[kRetryQueue][pos] = e;
-  } else {
-    wk.rec[e] = EventRec{0, 0, H, status | VELO_EV_OVERFLOW, 0, 0, gbase, 0};
-    atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
-  }
-}
-
-// Module of hit position p: positions of module m are [cb[4m], cb[4m + 4]).
-__device__ __forceinline__ int module_of(const uint16_t* cb, int nm, uint32_t p) {
-  int lo = 0, hi = nm - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cb[kSPM * mid] <= p) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
 }
 
 enum Misc { M_EVENT = 0, M_NTR = 1, M_KEPT = 5, M_TBASE = 7, M_HBASE = 8, M_SKIP = 10, M_NACT = 12 };

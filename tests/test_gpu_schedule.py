@@ -12,7 +12,9 @@ from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(256, 0x1C, 1), (256, 0x1C, 0), (256, 0x10, 1), (128, 0x15, 1), (128, 0x07, 0), (128, 0x0A, 1)]
+# module-window class (bit 6) with whole-event classes, and whole-event classes alone
+SCHEDULES = [(256, 0x60, 1), (256, 0x60, 0), (128, 0x70, 1), (256, 0x1C, 1), (256, 0x1C, 0), (256, 0x10, 1),
+             (128, 0x15, 1), (128, 0x07, 0), (128, 0x0A, 1)]
 
 
 @pytest.fixture(scope="module")
