@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kRingThreads, 8) track_ring_kernel(const DevGe
 
 // Lanes per active track in phase A and per middle hit in phase B.
 constexpr int kRingGroupA = 2;
-constexpr int kRingGroupB = 4;
+constexpr int kRingGroupB = 2;
 
 }  // namespace
 
