@@ -235,7 +235,7 @@ typedef struct velo_stats {
  * to one block; the schedule only decides how blocks share the GPU).  Events
  * run in the first class that holds their hits.  class_mask selects the
  * classes:
- *   bit 6: the module-window class (128 threads, eight CTAs per SM, up to
+ *   bit 6: the module-window class (128 threads, nine CTAs per SM, up to
  *          8192 hits; it keeps only the three modules of a round and the
  *          next one in shared memory);
  *   bits 0-5: whole-event classes by CTAs per SM: bit 0 = 8, 1 = 6, 2 = 4,

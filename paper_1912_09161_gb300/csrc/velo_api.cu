@@ -234,7 +234,7 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
 // CTAs per SM of the candidate classes; a schedule's class_mask selects
 // from this list (at most kMaxClasses; one CTA per SM is always included).
 constexpr int kPerSm[6] = {8, 6, 4, 3, 2, 1};
-// class_mask bit of the module-window class (128 threads, eight CTAs per SM).
+// class_mask bit of the module-window class (128 threads, kRingCtasPerSm CTAs per SM).
 constexpr uint32_t kRingClassBit = 1u << 6;
 
 // Hit-slot bytes of a class plan: kMaxModules u16 per candidate, max_tracks
@@ -271,7 +271,7 @@ int setup_ring(velo_handle* h) {
   e = ring_occupancy(&occ);
   if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "occupancy query (ring): %s", cudaGetErrorString(e));
   if (occ < 1) return VELO_OK;
-  h->ring_per_sm = occ > 8 ? 8 : occ;
+  h->ring_per_sm = occ > kRingCtasPerSm ? kRingCtasPerSm : occ;
   const size_t n = (size_t)h->ring_per_sm * h->n_sm;
   size_t o = 0;
   const size_t o_pos = o; o = align256(o + n * kRingPosCap * sizeof(float2));

@@ -24,9 +24,10 @@ constexpr int kMlpNormOffset = (2 * kMlpParams + 15) & ~15;  // byte offset of t
 // capacities of its shared-memory window and global region; an event beyond
 // any of them goes to the retry queue.
 constexpr int kRingThreads = 128;
+constexpr int kRingCtasPerSm = 9;         // register budget: 65536 / (128 * 9) -> 56 per thread
 constexpr uint32_t kRingModHits = 256;    // hits of one module
 constexpr uint32_t kRingMaxH = 8192;      // hits of one event
-constexpr uint32_t kRingMaxAct = 192;     // active tracks in one round
+constexpr uint32_t kRingMaxAct = 160;     // active tracks in one round
 constexpr uint32_t kRingMaxT = 512;       // track candidates of one event
 constexpr uint32_t kRingTrackHits = 32;   // hits of one candidate
 constexpr uint32_t kRingPosCap = kRingMaxH + 8 * kMaxModules;  // module blocks padded to 8 hits

@@ -1,5 +1,5 @@
 // Tracking kernel with a rolling module window: hits -> track candidates, one
-// event per CTA of 128 threads, eight CTAs per SM.
+// event per CTA of 128 threads, nine CTAs per SM.
 //
 // The search by triplet (paper section 2.3.1) only ever looks at three
 // consecutive modules: round i extends the active tracks into module i
@@ -7,8 +7,8 @@
 // (phase B).  So this kernel keeps in shared memory only a ring of four module
 // slots (the three of the round, and the next module, copied in with cp.async
 // while the round runs), the active tracks (double-buffered records), and two
-// bitmaps over the event's hits -- about 25 KB per event instead of the whole
-// event, so eight events share an SM.  Per event:
+// bitmaps over the event's hits -- about 22 KB per event instead of the whole
+// event, so nine events share an SM.  Per event:
 //   1. order each module's hits by phi bin (one warp per module) into the
 //      CTA's region of global memory, each module at a 16-byte-aligned offset;
 //   2. copy the last three modules into the ring; run the rounds from the last
@@ -40,13 +40,15 @@ constexpr int kRingSlots = 4;
 
 // shared-memory plan
 struct RingLayout {
-  uint32_t z, cb, moff, misc, scan, wscr, slots, used, act, total;
+  uint32_t z, cb, moff, misc, scan, slots, used, act, total;  // act also holds the binning scratch
 };
 
 constexpr uint32_t kSlotPos = 0, kSlotPid = 8 * kRingModHits, kSlotBins = kSlotPid + 2 * kRingModHits;
 constexpr uint32_t kSlotBytes = kSlotBins + 2 * kNB;
 // active-track records, per list: x, y, z, tx, ty (f32), track id (u16), hits, skips (u8)
 constexpr uint32_t kActBytes = kRingMaxAct * (5 * 4 + 2 + 1 + 1);
+static_assert(2 * kActBytes >= 4u * kNB * (kRingThreads / 32), "binning scratch fits the track lists");
+static_assert(2 * kActBytes >= 3u * 4u * kRingMaxT, "ranking arrays fit the track lists");
 
 __host__ __device__ constexpr uint32_t ralign16(uint32_t x) { return (x + 15u) & ~15u; }
 
@@ -58,7 +60,6 @@ __host__ __device__ inline RingLayout ring_layout() {
   L.moff = o; o = ralign16(o + 4 * (kMaxModules + 1));
   L.misc = o; o = ralign16(o + 4 * 32);
   L.scan = o; o = ralign16(o + 4 * 32);
-  L.wscr = o; o = ralign16(o + 4 * kNB * (kRingThreads / 32));
   L.slots = o; o = ralign16(o + kRingSlots * kSlotBytes);
   L.used = o; o = ralign16(o + 2 * (kRingMaxH / 8));  // two bitmaps
   L.act = o; o = ralign16(o + 2 * kActBytes);
@@ -148,7 +149,7 @@ __device__ __forceinline__ uint32_t ring_index(const uint16_t* cb, const uint32_
 }
 
 template <int GA, int GB>
-__global__ void __launch_bounds__(kRingThreads, 8) track_ring_kernel(const DevGeometry* __restrict__ geo,
+__global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kernel(const DevGeometry* __restrict__ geo,
                                                                      DevParams par, EventsView ev, WorkView wk,
                                                                      int cls, int qi) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kRingThreads, 8) track_ring_kernel(const DevGe
     {
       const uint32_t* so = ev.sensor_off + (size_t)e * ns;
       constexpr int BPL = kNB / 32;
-      uint32_t* wc = (uint32_t*)(smem + L.wscr) + kNB * warp;
+      uint32_t* wc = (uint32_t*)(smem + L.act) + kNB * warp;  // the rounds have not started
       for (int m = warp; m < nm; m += NW) {
         const uint32_t s0 = kSPM * m;
         const uint32_t c0 = s_cb[s0], c1 = s_cb[s0 + 4];
