@@ -153,13 +153,16 @@ def _measured_peak_hbm() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def _profile_traffic(kernel_src: str) -> float | None:
-    """DRAM bytes per call of the tracking kernel from the committed ncu
-    summary, if it was taken on the current kernel source (its sha256 prefix
-    is recorded in the summary)."""
+def _profile_traffic(kernel_srcs: list[str]) -> float | None:
+    """DRAM bytes per call of the tracking kernels from the committed ncu
+    summary, if it was taken on the current kernel sources (the sha256 prefix
+    of their concatenation is recorded in the summary)."""
     try:
         text = open(PROFILE_SUMMARY).read()
-        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for src in kernel_srcs:
+            h.update(open(src, "rb").read())
+        sha = h.hexdigest()[:16]
     except OSError:
         return None
     m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
@@ -352,7 +355,8 @@ def run_ours(args):
     desc = rec.describe()
     peak, peak_kind = _measured_peak_hbm()
     achieved = sum(reco_bytes) / (sum(reco_ms) / 1e3) / 1e9
-    traffic = _profile_traffic(os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", "velo_track.cu"))
+    traffic = _profile_traffic([os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", f)
+                                for f in ("velo_track_ring.cu", "velo_track.cu")])
     tot = out.totals.cpu().numpy().view(np.uint32)
     step_bytes = _step_bytes(ev.n_pixels, ev.n_events, geom.n_sensors, int(tot[0]), int(tot[1]))
     stage = [statistics.mean(x[k] for x in stage_ms) for k in range(4)]
@@ -368,7 +372,8 @@ def run_ours(args):
                    "parallelism": f"events sharded over {ws} GPU(s), no collective",
                    "launch": desc, "status": rc},
         "roofline": {"bound": "hbm",
-                     "kernel": "track_kernel (all shared-memory classes of one call, concurrent on their streams)",
+                     "kernel": "tracking: track_ring_kernel (module-window class) and track_kernel (whole-event "
+                               "class and retry pass) of one call, concurrent on their streams",
                      "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel_ms_per_step": statistics.mean(reco_ms),
