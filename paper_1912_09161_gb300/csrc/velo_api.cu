@@ -274,11 +274,8 @@ int setup_ring(velo_handle* h) {
   h->ring_per_sm = occ > kRingCtasPerSm ? kRingCtasPerSm : occ;
   const size_t n = (size_t)h->ring_per_sm * h->n_sm;
   size_t o = 0;
-  const size_t o_pos = o; o = align256(o + n * kRingPosCap * sizeof(float2));
-  const size_t o_pid = o; o = align256(o + n * kRingPosCap * sizeof(uint16_t));
-  const size_t o_bins = o; o = align256(o + n * kMaxModules * kNB * sizeof(uint16_t));
   const size_t o_trk = o; o = align256(o + n * kRingMaxT * kRingTrackHits * sizeof(uint16_t));
-  const size_t o_sp = o; o = align256(o + n * 3 * kRingMaxT * sizeof(uint16_t));
+  const size_t o_sh = o; o = align256(o + n * 3 * kRingMaxT * sizeof(uint16_t));
   const size_t o_n = o; o = align256(o + n * kRingMaxT);
   const size_t o_seed = o; o = align256(o + n * kRingMaxT * sizeof(float));
   e = cudaMalloc(&h->ring_buf, o);
@@ -287,8 +284,7 @@ int setup_ring(velo_handle* h) {
     return fail(VELO_ERR_NOMEM, "cudaMalloc(%zu) (ring): %s", o, cudaGetErrorString(e));
   }
   char* b = (char*)h->ring_buf;
-  h->wk.ring = RingScratch{(float2*)(b + o_pos), (uint16_t*)(b + o_pid), (uint16_t*)(b + o_bins),
-                           (uint16_t*)(b + o_trk), (uint16_t*)(b + o_sp), (uint8_t*)(b + o_n), (float*)(b + o_seed)};
+  h->wk.ring = RingScratch{(uint16_t*)(b + o_trk), (uint16_t*)(b + o_sh), (uint8_t*)(b + o_n), (float*)(b + o_seed)};
   return VELO_OK;
 }
 

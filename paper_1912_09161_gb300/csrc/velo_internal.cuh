@@ -30,7 +30,6 @@ constexpr uint32_t kRingMaxH = 8192;      // hits of one event
 constexpr uint32_t kRingMaxAct = 160;     // active tracks in one round
 constexpr uint32_t kRingMaxT = 512;       // track candidates of one event
 constexpr uint32_t kRingTrackHits = 32;   // hits of one candidate
-constexpr uint32_t kRingPosCap = kRingMaxH + 8 * kMaxModules;  // module blocks padded to 8 hits
 
 // Device copy of the geometry (in the handle's arena).
 struct DevGeometry {
@@ -87,22 +86,14 @@ struct Counters {
   unsigned long long cls_pixels[kMaxClasses];  // raw pixels of the completed events
 };
 
-// Global region of the module-window kernel, one per CTA (arrays of
-// n_ctas regions): hits by (module, phi bin), each module's block at a
-// multiple of 8 hits; per-module phi-bin ends; candidate hit lists; seeds.
+// Global region of the module-window kernel, one per CTA (arrays of n_ctas
+// regions): each candidate's hit list and its seed (canonical ids).
 struct RingScratch {
-  float2* pos;        // [kRingPosCap] per CTA
-  uint16_t* pid;      // [kRingPosCap] canonical ids
-  uint16_t* bins;     // [kMaxModules * kNB] module-local bin ends
-  uint16_t* trk;      // [kRingMaxT * kRingTrackHits] hit positions per candidate
-  uint16_t* seed_pos; // [3 * kRingMaxT] seed hit positions a, b, c
+  uint16_t* trk;      // [kRingMaxT * kRingTrackHits] canonical hit ids per candidate
+  uint16_t* seed_hit; // [3 * kRingMaxT] seed hits a, b, c
   uint8_t* n_hits;    // [kRingMaxT]
   float* seed;        // [kRingMaxT] seed scatter, then the classifier logit
 };
-
-// Bytes of one CTA's region.
-constexpr size_t kRingCtaBytes = (size_t)kRingPosCap * (8 + 2) + (size_t)kMaxModules * kNB * 2 +
-                                 (size_t)kRingMaxT * kRingTrackHits * 2 + (size_t)kRingMaxT * (3 * 2 + 1 + 4);
 
 // Device views.
 struct EventsView {

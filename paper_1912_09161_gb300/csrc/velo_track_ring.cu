@@ -5,25 +5,25 @@
 // consecutive modules: round i extends the active tracks into module i
 // (phase A) and seeds triplets with a in module i + 2, b in i + 1 and c in i
 // (phase B).  So this kernel keeps in shared memory only a ring of four module
-// slots (the three of the round, and the next module, copied in with cp.async
-// while the round runs), the active tracks (double-buffered records), and two
-// bitmaps over the event's hits -- about 22 KB per event instead of the whole
-// event, so nine events share an SM.  Per event:
-//   1. order each module's hits by phi bin (one warp per module) into the
-//      CTA's region of global memory, each module at a 16-byte-aligned offset;
-//   2. copy the last three modules into the ring; run the rounds from the last
-//      module pair toward the interaction region, prefetching module i - 1
-//      during round i;
-//   3. apply the plain cuts (or the classifier), rank the kept candidates
-//      canonically and write their hits (ids, positions, modules) to scratch
-//      for the emit kernel, which fits them.
-// Candidate hit lists (up to kRingTrackHits positions) and seed records live
-// in the CTA's global region too.  Events beyond the window's capacities (a
-// module of more than kRingModHits hits, more than kRingMaxAct active tracks,
-// kRingMaxT candidates, kRingMaxH hits, or a track of kRingTrackHits hits) go
-// to the retry queue, which a whole-event class drains.  Decisions are the
-// same IEEE single-precision operations, in the same order, as in the
-// whole-event kernel: results are identical whichever kernel runs an event.
+// slots (each: the module's hits ordered by phi bin, their canonical ids, the
+// bin ends and a used bitmap), the active tracks (double-buffered records)
+// and the next module's raw hits -- about 24 KB per event, so nine events
+// share an SM.  The hits come straight from the clustering output:
+//   - round i copies module i - 2's hits into a staging buffer with cp.async
+//     during its phase B;
+//   - round i - 1 bins them by phi into the free slot during its phase A, on
+//     a warp that phase A leaves idle;
+// so every hit is read from global memory once.  After the rounds the kernel
+// applies the plain cuts (or the classifier), ranks the kept candidates
+// canonically and writes their hits (ids, positions, modules) to scratch for
+// the emit kernel, which fits them.  Candidate hit lists (canonical ids, up
+// to kRingTrackHits) and seed records live in the CTA's global region.
+// Events beyond the window's capacities (a module of more than kRingModHits
+// hits, more than kRingMaxAct active tracks, kRingMaxT candidates, kRingMaxH
+// hits, or a candidate of kRingTrackHits hits) go to the retry queue, which a
+// whole-event class drains.  Decisions are the same IEEE single-precision
+// operations, in the same order, as in the whole-event kernel: results are
+// identical whichever kernel runs an event.
 #include <math.h>
 #include <stdint.h>
 
@@ -38,17 +38,20 @@ namespace {
 
 constexpr int kRingSlots = 4;
 
-// shared-memory plan
-struct RingLayout {
-  uint32_t z, cb, moff, misc, scan, slots, used, act, total;  // act also holds the binning scratch
-};
-
+// ring slot: hits by phi bin, their canonical ids, bin ends (module-local),
+// used bitmap over the slot's positions
 constexpr uint32_t kSlotPos = 0, kSlotPid = 8 * kRingModHits, kSlotBins = kSlotPid + 2 * kRingModHits;
-constexpr uint32_t kSlotBytes = kSlotBins + 2 * kNB;
+constexpr uint32_t kSlotUsed = kSlotBins + 2 * kNB;
+constexpr uint32_t kSlotBytes = kSlotUsed + kRingModHits / 8;
 // active-track records, per list: x, y, z, tx, ty (f32), track id (u16), hits, skips (u8)
 constexpr uint32_t kActBytes = kRingMaxAct * (5 * 4 + 2 + 1 + 1);
-static_assert(2 * kActBytes >= 4u * kNB * (kRingThreads / 32), "binning scratch fits the track lists");
 static_assert(2 * kActBytes >= 3u * 4u * kRingMaxT, "ranking arrays fit the track lists");
+static_assert(kRingSlots * kSlotBytes >= 2u * (kRingMaxH / 8), "seen bitmaps fit the ring");
+
+// shared-memory plan
+struct RingLayout {
+  uint32_t z, cb, misc, scan, wbin, pend, stage, slots, act, total;
+};
 
 __host__ __device__ constexpr uint32_t ralign16(uint32_t x) { return (x + 15u) & ~15u; }
 
@@ -57,18 +60,19 @@ __host__ __device__ inline RingLayout ring_layout() {
   uint32_t o = 0;
   L.z = o; o = ralign16(o + 4 * kMaxModules);
   L.cb = o; o = ralign16(o + 2 * (kMaxSensors + 1));
-  L.moff = o; o = ralign16(o + 4 * (kMaxModules + 1));
   L.misc = o; o = ralign16(o + 4 * 32);
   L.scan = o; o = ralign16(o + 4 * 32);
+  L.wbin = o; o = ralign16(o + 3 * 4 * kNB);             // bin counters of up to three warps
+  L.pend = o; o = ralign16(o + 2 * kRingModHits);         // last round's seeds: b and c slot positions
+  L.stage = o; o = ralign16(o + 8 * kRingModHits);        // raw hits of the next module
   L.slots = o; o = ralign16(o + kRingSlots * kSlotBytes);
-  L.used = o; o = ralign16(o + 2 * (kRingMaxH / 8));  // two bitmaps
   L.act = o; o = ralign16(o + 2 * kActBytes);
   L.total = o;
   return L;
 }
 
 enum RMisc {
-  R_EVENT = 0, R_NTR = 1, R_MAXMOD = 2, R_KEPT = 5, R_TBASE = 7, R_HBASE = 8, R_SKIP = 10, R_NACT = 12, R_OVF = 14
+  R_EVENT = 0, R_NTR = 1, R_MAXMOD = 2, R_NPEND = 3, R_KEPT = 5, R_TBASE = 7, R_HBASE = 8, R_SKIP = 10, R_NACT = 12
 };
 
 struct ActList {
@@ -104,48 +108,99 @@ __device__ __forceinline__ int list_slot(bool pred, uint32_t* counter, uint32_t 
   return (pred && idx < cap) ? (int)idx : -1;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Copies module m (positions, ids and phi-bin ends, module-local) from the
-// CTA's global region into its ring slot; every thread of the CTA issues its
-// share of 16-byte copies.  The arrays are padded to 8 hits, so whole chunks
-// stay inside them.
-__device__ __forceinline__ void ring_load(int m, unsigned char* slots, const uint32_t* moff, const uint16_t* cb,
-                                          const float2* gpos, const uint16_t* gpid, const uint16_t* gbins) {
-  unsigned char* slot = slots + (m & (kRingSlots - 1)) * kSlotBytes;
-  const uint32_t n = (uint32_t)cb[kSPM * (m + 1)] - cb[kSPM * m];
-  const uint32_t o = moff[m];
-  const uint32_t n_pos = (n + 1) / 2, n_pid = (n + 7) / 8, n_bins = kNB / 8;
-  for (uint32_t c = threadIdx.x; c < n_pos + n_pid + n_bins; c += blockDim.x) {
-    if (c < n_pos) cp_async16(slot + kSlotPos + 16 * c, gpos + o + 2 * c);
-    else if (c < n_pos + n_pid) cp_async16(slot + kSlotPid + 16 * (c - n_pos), gpid + o + 8 * (c - n_pos));
-    else cp_async16(slot + kSlotBins + 16 * (c - n_pos - n_pid), gbins + kNB * m + 8 * (c - n_pos - n_pid));
-  }
+// Hits of module m in canonical order, from the clustering output: canonical
+// id k of sensor s sits at so[s] + (k - cb[s]) (so: the event's absolute
+// sensor offsets).
+__device__ __forceinline__ uint32_t module_src(const uint16_t* cb, const uint32_t* so, int m, uint32_t k) {
+  const uint32_t s0 = kSPM * m;
+  const uint32_t s = s0 + (k >= cb[s0 + 1]) + (k >= cb[s0 + 2]) + (k >= cb[s0 + 3]);
+  return __ldg(&so[s]) + (k - cb[s]);
+}
+
+// Copies module m's hits (canonical order) into the staging buffer, every
+// thread its share of 8-byte cp.async copies; committed as one group.
+__device__ __forceinline__ void stage_module(int m, const uint16_t* cb, const uint32_t* so, const float2* prov,
+                                             float2* stage) {
+  const uint32_t c0 = cb[kSPM * m], n = (uint32_t)cb[kSPM * (m + 1)] - c0;
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) cp_async8(stage + j, prov + module_src(cb, so, m, c0 + j));
   cp_async_commit();
+}
+
+// Bins module m into its ring slot (one warp, counters wc[kNB]): hits by phi
+// bin, their canonical ids, the module-local bin ends, a clear used bitmap.
+// src(j) gives hit j of the module in canonical order.
+template <class Src>
+__device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned char* slots, uint32_t* wc, Src src) {
+  const int lane = threadIdx.x & 31;
+  constexpr int BPL = kNB / 32;
+  unsigned char* slot = slots + (m & (kRingSlots - 1)) * kSlotBytes;
+  float2* pos = (float2*)(slot + kSlotPos);
+  uint16_t* pid = (uint16_t*)(slot + kSlotPid);
+  uint16_t* bins = (uint16_t*)(slot + kSlotBins);
+  uint32_t* ub = (uint32_t*)(slot + kSlotUsed);
+  const uint32_t c0 = cb[kSPM * m], n = (uint32_t)cb[kSPM * (m + 1)] - c0;
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) wc[BPL * lane + u] = 0;
+  if (lane < (int)(kRingModHits / 32)) ub[lane] = 0;
+  __syncwarp();
+  for (uint32_t j = lane; j < n; j += 32) {
+    const float2 v = src(j);
+    atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
+  }
+  __syncwarp();
+  uint32_t cnt[BPL], sum = 0;
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) {
+    cnt[u] = wc[BPL * lane + u];
+    sum += cnt[u];
+  }
+  uint32_t cur = warp_incl_scan(sum) - sum;
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < BPL; ++u) {
+    wc[BPL * lane + u] = cur;
+    cur += cnt[u];
+    bins[BPL * lane + u] = (uint16_t)cur;
+  }
+  __syncwarp();
+  for (uint32_t j = lane; j < n; j += 32) {
+    const float2 v = src(j);
+    const uint32_t p = atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
+    pos[p] = v;
+    pid[p] = (uint16_t)(c0 + j);
+  }
+  __syncwarp();
 }
 
 struct Slot {
   const float2* pos;
   const uint16_t* pid;
   const uint16_t* bins;
-  uint32_t base;  // event position of the module's first hit
+  uint32_t* used;
 };
 
-__device__ __forceinline__ Slot slot_of(const unsigned char* slots, int m, const uint16_t* cb) {
-  const unsigned char* s = slots + (m & (kRingSlots - 1)) * kSlotBytes;
+__device__ __forceinline__ Slot slot_of(unsigned char* slots, int m) {
+  unsigned char* s = slots + (m & (kRingSlots - 1)) * kSlotBytes;
   return Slot{(const float2*)(s + kSlotPos), (const uint16_t*)(s + kSlotPid), (const uint16_t*)(s + kSlotBins),
-              (uint32_t)cb[kSPM * m]};
+              (uint32_t*)(s + kSlotUsed)};
 }
 
-// Canonical id and position of event position p (from the global region).
-__device__ __forceinline__ uint32_t ring_index(const uint16_t* cb, const uint32_t* moff, int nm, uint32_t p) {
-  const int m = module_of(cb, nm, p);
-  return moff[m] + (p - cb[kSPM * m]);
+// Sensor of canonical id k: the last s with cb[s] <= k.
+__device__ __forceinline__ int sensor_of(const uint16_t* cb, int ns, uint32_t k) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cb[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
 
 template <int GA, int GB>
@@ -157,15 +212,19 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
   const RingLayout L = ring_layout();
   float* s_z = (float*)(smem + L.z);
   uint16_t* s_cb = (uint16_t*)(smem + L.cb);
-  uint32_t* s_moff = (uint32_t*)(smem + L.moff);
   uint32_t* s_misc = (uint32_t*)(smem + L.misc);
   uint32_t* s_scan = (uint32_t*)(smem + L.scan);
+  uint32_t* s_wbin = (uint32_t*)(smem + L.wbin);
+  uint8_t* pend_b = (uint8_t*)(smem + L.pend);
+  uint8_t* pend_c = pend_b + kRingModHits;
+  float2* stage = (float2*)(smem + L.stage);
   unsigned char* slots = smem + L.slots;
-  uint32_t* used = (uint32_t*)(smem + L.used);
   const ActList act[2] = {act_list(smem + L.act), act_list(smem + L.act + kActBytes)};
   uint32_t* t_key = (uint32_t*)(smem + L.act);  // after the rounds
   uint32_t* t_rank = t_key + kRingMaxT;
   uint32_t* t_hoff = t_rank + kRingMaxT;         // indexed by rank
+  uint32_t* seen1 = (uint32_t*)slots;            // after the rounds, over canonical ids
+  uint32_t* seen2 = seen1 + kRingMaxH / 32;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = geo->n_sensors;
@@ -175,11 +234,8 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
 
   // this CTA's global region
   const RingScratch& R = wk.ring;
-  float2* gpos = R.pos + (size_t)blockIdx.x * kRingPosCap;
-  uint16_t* gpid = R.pid + (size_t)blockIdx.x * kRingPosCap;
-  uint16_t* gbins = R.bins + (size_t)blockIdx.x * kMaxModules * kNB;
   uint16_t* trk = R.trk + (size_t)blockIdx.x * kRingMaxT * kRingTrackHits;
-  uint16_t* mpa = R.seed_pos + (size_t)blockIdx.x * 3 * kRingMaxT;
+  uint16_t* mpa = R.seed_hit + (size_t)blockIdx.x * 3 * kRingMaxT;
   uint16_t* mpb = mpa + kRingMaxT;
   uint16_t* mpc = mpb + kRingMaxT;
   uint8_t* mn = R.n_hits + (size_t)blockIdx.x * kRingMaxT;
@@ -201,108 +257,58 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
       if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
       continue;
     }
+    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
 
-    // ---- 1. hits by (module, phi bin), into the global region ---------------
+    // ---- 1. the last three modules into the ring, the next one staged -------
     const uint16_t* cbg = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
     for (int s = tid; s <= ns; s += NT) s_cb[s] = cbg[s];
-    const uint32_t nwords = (H + 31) / 32;
-    uint32_t* pend = used + kRingMaxH / 32;  // unused during the rounds; seen twice after them
-    for (uint32_t k = tid; k < nwords; k += NT) {
-      used[k] = 0;
-      pend[k] = 0;
-    }
     __syncthreads();
     if (warp == 0) {
-      // module offsets in the global region: sizes rounded up to 8 hits
-      uint32_t sz[2], mx = 0;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int m = 2 * lane + u;
-        const uint32_t n = m < nm ? (uint32_t)s_cb[kSPM * (m + 1)] - s_cb[kSPM * m] : 0u;
-        mx = max(mx, n);
-        sz[u] = (n + 7) & ~7u;
-      }
-      const uint32_t incl = warp_incl_scan(sz[0] + sz[1]);
-      s_moff[2 * lane] = incl - sz[0] - sz[1];
-      s_moff[2 * lane + 1] = incl - sz[1];
+      uint32_t mx = 0;
+      for (int m = lane; m < nm; m += 32) mx = max(mx, (uint32_t)s_cb[kSPM * (m + 1)] - s_cb[kSPM * m]);
       mx = __reduce_max_sync(kFull, mx);
       if (lane == 0) s_misc[R_MAXMOD] = mx;
+    }
+    if (wk.cl_x) {  // canonical cluster list (verification output)
+      for (int s = warp; s < ns; s += NW) {
+        const uint32_t c0 = s_cb[s], nc = (uint32_t)s_cb[s + 1] - c0, a = __ldg(&so[s]);
+        for (uint32_t j = lane; j < nc; j += 32) {
+          const float2 v = wk.prov[a + j];
+          wk.cl_x[gbase + c0 + j] = v.x;
+          wk.cl_y[gbase + c0 + j] = v.y;
+          wk.cl_key[gbase + c0 + j] = ((uint32_t)s << 16) | wk.prov_key[a + j];
+        }
+      }
     }
     __syncthreads();
     if (s_misc[R_MAXMOD] > kRingModHits) {
       if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
       continue;
     }
-    {
-      const uint32_t* so = ev.sensor_off + (size_t)e * ns;
-      constexpr int BPL = kNB / 32;
-      uint32_t* wc = (uint32_t*)(smem + L.act) + kNB * warp;  // the rounds have not started
-      for (int m = warp; m < nm; m += NW) {
-        const uint32_t s0 = kSPM * m;
-        const uint32_t c0 = s_cb[s0], c1 = s_cb[s0 + 4];
-        const uint32_t b1 = s_cb[s0 + 1], b2 = s_cb[s0 + 2], b3 = s_cb[s0 + 3];
-        const uint32_t o = s_moff[m];
-#pragma unroll
-        for (int u = 0; u < BPL; ++u) wc[BPL * lane + u] = 0;
-        __syncwarp();
-        for (uint32_t k = c0 + lane; k < c1; k += 32) {
-          const uint32_t s = s0 + (k >= b1) + (k >= b2) + (k >= b3);
-          const uint32_t src = __ldg(&so[s]) + (k - s_cb[s]);
-          const float2 v = wk.prov[src];
-          atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
-          if (wk.cl_x) {
-            wk.cl_x[gbase + k] = v.x;
-            wk.cl_y[gbase + k] = v.y;
-            wk.cl_key[gbase + k] = (s << 16) | wk.prov_key[src];
-          }
-        }
-        __syncwarp();
-        uint32_t cnt[BPL], sum = 0;
-#pragma unroll
-        for (int u = 0; u < BPL; ++u) {
-          cnt[u] = wc[BPL * lane + u];
-          sum += cnt[u];
-        }
-        uint32_t cur = warp_incl_scan(sum) - sum;  // module-local start of this lane's first bin
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < BPL; ++u) {
-          wc[BPL * lane + u] = cur;
-          cur += cnt[u];
-          gbins[kNB * m + BPL * lane + u] = (uint16_t)cur;  // module-local end of the bin
-        }
-        __syncwarp();
-        for (uint32_t k = c0 + lane; k < c1; k += 32) {
-          const uint32_t s = s0 + (k >= b1) + (k >= b2) + (k >= b3);
-          const float2 v = wk.prov[__ldg(&so[s]) + (k - s_cb[s])];
-          const uint32_t p = o + atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
-          gpos[p] = v;
-          gpid[p] = (uint16_t)k;
-        }
-        __syncwarp();
-      }
+    if (nm >= 4) stage_module(nm - 4, s_cb, so, wk.prov, stage);
+    if (warp < 3 && nm - 1 - warp >= 0) {
+      const int m = nm - 1 - warp;
+      const uint32_t c0 = s_cb[kSPM * m];
+      bin_module(m, s_cb, slots, s_wbin + kNB * warp,
+                 [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
     }
-    __syncthreads();  // the region is written; copies of it may start
-    for (int m = nm - 1; m >= nm - 3 && m >= 0; --m) ring_load(m, slots, s_moff, s_cb, gpos, gpid, gbins);
     cp_async_wait_all();
     __syncthreads();
 
     // ---- 2. search by triplet over the module window ------------------------
-    uint32_t seed_lo = 0;
     int cur = 0;
     bool overflow = false;
     for (int i = nm - 3; i >= 0; --i) {
-      if (i >= 1) ring_load(i - 1, slots, s_moff, s_cb, gpos, gpid, gbins);  // next round's module
       const float zi = s_z[i];
-      const Slot Si = slot_of(slots, i, s_cb);
+      const Slot Si = slot_of(slots, i), Sb = slot_of(slots, i + 1), Sa = slot_of(slots, i + 2);
       bool ovf = false;
-      // phase A: hits of the newest seeds become used; every active track is
-      // extended into module i by its best hit (GA lanes per track)
-      const uint32_t seed_hi = s_misc[R_NTR];
-      for (uint32_t t = seed_lo + tid; t < seed_hi; t += NT) {
-        set_bit(used, mpa[t]);
-        set_bit(used, mpb[t]);
-        set_bit(used, mpc[t]);
+      // phase A: the b and c hits of the last round's seeds become used;
+      // every active track is extended into module i by its best hit (GA
+      // lanes per track); the last warp bins module i - 1 into the free slot
+      const uint32_t npend = s_misc[R_NPEND];
+      for (uint32_t j = tid; j < npend; j += NT) {
+        set_bit(Sa.used, pend_b[j]);  // b of a seed of round i + 1 lies in module i + 2
+        set_bit(Sb.used, pend_c[j]);  // its c in module i + 1
       }
       const uint32_t nact = s_misc[R_NACT + cur];
       const ActList& A = act[cur];
@@ -348,9 +354,9 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
             if (n >= kRingTrackHits) {
               ovf = true;
             } else {
-              trk[(size_t)t * kRingTrackHits + n] = (uint16_t)(Si.base + p);
+              trk[(size_t)t * kRingTrackHits + n] = (uint16_t)(best >> 16);  // canonical id
               mn[t] = (uint8_t)(n + 1);
-              set_bit(used, Si.base + p);
+              set_bit(Si.used, p);
               tx = fdiv(fsub(xl, v.x), dzq);
               ty = fdiv(fsub(yl, v.y), dzq);
               xl = v.x;
@@ -378,20 +384,23 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
           N.skip[o] = (uint8_t)sk;
         }
       }
+      if (warp == NW - 1 && i >= 1) bin_module(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
       if (__syncthreads_or(ovf)) { overflow = true; break; }
-      seed_lo = seed_hi;
-      if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
+      if (tid == 0) {
+        s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
+        s_misc[R_NPEND] = 0;
+      }
+      if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage);  // binned in the next round
       // phase B: seeds with the middle hit b in module i + 1
       {
-        const Slot Sb = slot_of(slots, i + 1, s_cb), Sa = slot_of(slots, i + 2, s_cb);
         const float za = s_z[i + 2], zb = s_z[i + 1];
         const float dzab = fsub(za, zb), dzc = fsub(zi, zb), dzbc = fsub(zb, zi);
         constexpr int NG = NT / GB;
         const int g = tid / GB, gl = tid % GB;
-        const uint32_t nb = (uint32_t)s_cb[kSPM * (i + 2)] - Sb.base;
-        for (uint32_t base = 0; base < nb; base += NG) {
-          const uint32_t qb = base + g;
-          const bool has = qb < nb && !bit(used, Sb.base + qb);
+        const uint32_t nb = (uint32_t)s_cb[kSPM * (i + 2)] - s_cb[kSPM * (i + 1)];
+        for (uint32_t b0 = 0; b0 < nb; b0 += NG) {
+          const uint32_t qb = b0 + g;
+          const bool has = qb < nb && !bit(Sb.used, qb);
           unsigned long long best = ~0ull;
           uint32_t bpos = 0;
           float2 vb = make_float2(0.0f, 0.0f);
@@ -402,7 +411,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
             const Cand cc = window_cands(Si.bins, 0, pab, win);
             for (uint32_t k = gl; k < ca.n(); k += GB) {
               const uint32_t qa = ca.at(k);
-              if (bit(used, Sa.base + qa)) continue;
+              if (bit(Sa.used, qa)) continue;
               const float2 va = Sa.pos[qa];
               if (!phi_ok(va.x, va.y, vb.x, vb.y, tol)) continue;
               const float txs = fdiv(fsub(va.x, vb.x), dzab);
@@ -413,7 +422,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
               const unsigned long long ida = (unsigned long long)Sa.pid[qa] << 16;
               for (uint32_t kc = 0; kc < cc.n(); ++kc) {
                 const uint32_t qc = cc.at(kc);
-                if (bit(used, Si.base + qc)) continue;
+                if (bit(Si.used, qc)) continue;
                 const float2 vc = Si.pos[qc];
                 if (!phi_ok(vb.x, vb.y, vc.x, vc.y, tol)) continue;
                 const float dx = fsub(vc.x, xp), dy = fsub(vc.y, yp);
@@ -422,7 +431,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
                 const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | Si.pid[qc];
                 if (key < best) {
                   best = key;
-                  bpos = (qa << 16) | qc;
+                  bpos = qc;
                 }
               }
             }
@@ -444,17 +453,21 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
             if (t >= kRingMaxT) {
               ovf = true;
             } else {
-              const uint32_t pa = Sa.base + (bpos >> 16), pb = Sb.base + qb, pc = Si.base + (bpos & 0xFFFFu);
+              const uint32_t ia = (uint32_t)(best >> 16) & 0xFFFFu, ic = (uint32_t)best & 0xFFFFu;
+              const uint32_t ib = Sb.pid[qb];
               uint16_t* th = trk + (size_t)t * kRingTrackHits;
-              th[0] = (uint16_t)pa;
-              th[1] = (uint16_t)pb;
-              th[2] = (uint16_t)pc;
-              mpa[t] = (uint16_t)pa;
-              mpb[t] = (uint16_t)pb;
-              mpc[t] = (uint16_t)pc;
+              th[0] = (uint16_t)ia;
+              th[1] = (uint16_t)ib;
+              th[2] = (uint16_t)ic;
+              mpa[t] = (uint16_t)ia;
+              mpb[t] = (uint16_t)ib;
+              mpc[t] = (uint16_t)ic;
               mn[t] = 3;
               mseed[t] = __uint_as_float((uint32_t)(best >> 32));
-              vc = Si.pos[bpos & 0xFFFFu];
+              const uint32_t pe = atomicAdd(&s_misc[R_NPEND], 1u);  // one per b: < nb <= kRingModHits
+              pend_b[pe] = (uint8_t)qb;
+              pend_c[pe] = (uint8_t)bpos;
+              vc = Si.pos[bpos];
               seeded = true;
             }
           }
@@ -472,7 +485,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
           }
         }
       }
-      cp_async_wait_all();  // module i - 1 is in its slot for the next round
+      cp_async_wait_all();  // module i - 2 is staged for the next round
       if (__syncthreads_or(ovf)) { overflow = true; break; }
       cur ^= 1;
     }
@@ -486,12 +499,16 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
 
     // ---- 3. plain cuts or classifier, canonical order -----------------------
     const uint32_t ntr = s_misc[R_NTR];
-    auto id_of = [&](uint32_t p) -> uint32_t { return gpid[ring_index(s_cb, s_moff, nm, p)]; };
+    const uint32_t nwords = (H + 31) / 32;
+    // position of canonical id k in the clustering output, and its module
+    auto hit_xy = [&](uint32_t k, int& m) -> float2 {
+      const int s = sensor_of(s_cb, ns, k);
+      m = s / kSPM;
+      return wk.prov[__ldg(&so[s]) + (k - s_cb[s])];
+    };
     if (!use_mlp) {
       // plain cuts: >= 4 hits, or 3 hits with a small seed scatter and no hit
       // shared with another candidate
-      uint32_t* seen1 = used;
-      uint32_t* seen2 = pend;
       for (uint32_t k = tid; k < nwords; k += NT) {
         seen1[k] = 0;
         seen2[k] = 0;
@@ -501,17 +518,17 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
         const uint16_t* th = trk + (size_t)t * kRingTrackHits;
         const uint32_t n = mn[t];
         for (uint32_t k = 0; k < n; ++k) {
-          const uint32_t p = th[k], b = 1u << (p & 31);
-          if (atomicOr(&seen1[p >> 5], b) & b) atomicOr(&seen2[p >> 5], b);
+          const uint32_t h = th[k], b = 1u << (h & 31);
+          if (atomicOr(&seen1[h >> 5], b) & b) atomicOr(&seen2[h >> 5], b);
         }
       }
       __syncthreads();
       for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint32_t pa = mpa[t], pb = mpb[t], pc = mpc[t], n = mn[t];
+        const uint32_t ha = mpa[t], hb = mpb[t], hc = mpc[t], n = mn[t];
         bool keep = n >= 4;
         if (n == 3 && mseed[t] < par.max_scatter_3hit)
-          keep = !bit(seen2, pa) && !bit(seen2, pb) && !bit(seen2, pc);
-        t_key[t] = keep ? ((id_of(pa) << 16) | id_of(pb)) : 0xFFFFFFFFu;
+          keep = !bit(seen2, ha) && !bit(seen2, hb) && !bit(seen2, hc);
+        t_key[t] = keep ? ((ha << 16) | hb) : 0xFFFFFFFFu;
       }
     } else {
       const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
@@ -523,19 +540,17 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
         fit_track(
             n,
             [&](uint32_t k, float& x, float& y, int& m) {
-              const uint32_t p = th[k];
-              m = module_of(s_cb, nm, p);
-              const float2 v = gpos[s_moff[m] + (p - s_cb[kSPM * m])];
+              const float2 v = hit_xy(th[k], m);
               x = v.x;
               y = v.y;
             },
             s_z, sig2, kms, st);
         float f[kMlpIn];
-        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, module_of(s_cb, nm, th[0]),
-                     module_of(s_cb, nm, th[n - 1]), f);
+        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, sensor_of(s_cb, ns, th[0]) / kSPM,
+                     sensor_of(s_cb, ns, th[n - 1]) / kSPM, f);
         const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
         mseed[t] = logit;
-        t_key[t] = logit >= par.mlp_logit_threshold ? ((id_of(mpa[t]) << 16) | id_of(mpb[t])) : 0xFFFFFFFFu;
+        t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)mpa[t] << 16) | mpb[t]) : 0xFFFFFFFFu;
       }
     }
     __syncthreads();
@@ -587,13 +602,12 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
       const uint32_t r = t_rank[t], n = mn[t];
       const uint16_t* th = trk + (size_t)t * kRingTrackHits;
       const uint32_t h0 = hb + t_hoff[r];
-      int m = nm - 1;  // hits are stored by decreasing module
       for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t p = th[k];
-        while (s_cb[kSPM * m] > p) --m;
-        const uint32_t gi = s_moff[m] + (p - s_cb[kSPM * m]);
-        wk.tr_hits[h0 + k] = gpid[gi];
-        wk.tr_xy[h0 + k] = gpos[gi];
+        int m;
+        const uint32_t id = th[k];
+        const float2 v = hit_xy(id, m);
+        wk.tr_hits[h0 + k] = id;
+        wk.tr_xy[h0 + k] = v;
         wk.tr_mod[h0 + k] = (uint8_t)m;
       }
       const size_t o = (size_t)tb + r;
