@@ -19,6 +19,9 @@
 namespace velo {
 
 constexpr int kClusterThreads = 256;
+// Sensors of 33 to 64 pixels: neighbour masks in registers (false) or the
+// sorted union-find of the larger sensors (true).
+constexpr bool kSortedUnionFor64 = false;
 constexpr uint32_t kWarpStage = 1000;           // raw pixels a warp can stage for one large sensor
 constexpr uint32_t kAccBytes = 8 * 64;          // per-warp packed accumulators
 constexpr uint32_t kWarpSlice = kAccBytes + 6 * kWarpStage;
@@ -73,6 +76,42 @@ __device__ __forceinline__ void store_cluster(const HitOut& out, const SensorGeo
   if (out.key) out.key[p] = (uint16_t)key16;
 }
 
+// Ascending bitonic sort of 32 R keys held R per lane (element e = lane + 32 r
+// in register r): exchanges between registers for distances of 32 and more,
+// shuffles below.
+template <int R>
+__device__ __forceinline__ void warp_bitonic(uint32_t (&k)[R]) {
+  constexpr uint32_t NE = 32 * R;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
+#pragma unroll
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int rp = r ^ (int)(j >> 5);
+          if (rp > r) {
+            const uint32_t e = lane + 32u * r;
+            const bool up = (e & kk) == 0;
+            const uint32_t lo = min(k[r], k[rp]), hi = max(k[r], k[rp]);
+            k[r] = up ? lo : hi;
+            k[rp] = up ? hi : lo;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t o = __shfl_xor_sync(kFull, k[r], j);
+          const uint32_t e = lane + 32u * r;
+          const bool up = (e & kk) == 0, lower = (e & j) == 0;
+          k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
+        }
+      }
+    }
+  }
+}
+
 // Value held at sorted position q (element q lives in lane q % 32, register q / 32).
 template <int R>
 __device__ __forceinline__ uint32_t warp_fetch(const uint32_t (&v)[R], uint32_t q) {
@@ -113,34 +152,7 @@ __device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const u
       else bad = true;
     }
   }
-  // bitonic sort over element index e = lane + 32 r
-#pragma unroll
-  for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
-#pragma unroll
-    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int rp = r ^ (int)(j >> 5);
-          if (rp > r) {
-            const uint32_t e = lane + 32u * r;
-            const bool up = (e & kk) == 0;
-            const uint32_t lo = min(k[r], k[rp]), hi = max(k[r], k[rp]);
-            k[r] = up ? lo : hi;
-            k[rp] = up ? hi : lo;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const uint32_t o = __shfl_xor_sync(kFull, k[r], j);
-          const uint32_t e = lane + 32u * r;
-          const bool up = (e & kk) == 0, lower = (e & j) == 0;
-          k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
-        }
-      }
-    }
-  }
+  warp_bitonic<R>(k);
   // repeated pixels; valid-position mask
   uint64_t vm = 0;
 #pragma unroll
@@ -396,10 +408,108 @@ __device__ uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const 
   return nroot;
 }
 
+// Union of the components of sorted positions x and y (lock-free on parent
+// indices): the root with the larger position goes under the one with the
+// smaller, so every root ends at its component's smallest position.
+__device__ void uf_unite_pos(uint16_t* par, int x, int y) {
+  const volatile uint16_t* vp = par;
+  while (true) {
+    x = uf_find(vp, x);
+    y = uf_find(vp, y);
+    if (x == y) return;
+    if (x > y) {
+      const int t = x;
+      x = y;
+      y = t;
+    }
+    const unsigned short old = atomicCAS((unsigned short*)&par[y], (unsigned short)y, (unsigned short)x);
+    if (old == (unsigned short)y) return;
+  }
+}
+
+// Sensors of up to 32 R pixels (R = 2, 4 or 8): keys c * 512 + r sorted in
+// registers, then in the warp's staging area (keys, parents, member sums):
+// repeated pixels are equal neighbours in sorted order; each pixel scans
+// forward while keys stay within 513 and joins its 8-neighbours by
+// union-find; sums go to the component roots (smallest positions, so
+// smallest keys), which are ranked in sorted order.
+template <int R>
+__device__ uint32_t cluster_sensor_mid(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row, uint32_t a,
+                                       uint32_t n, int ncols, int nrows, const SensorGeo& g, const HitOut& out,
+                                       unsigned char* stage, bool& bad) {
+  constexpr uint32_t NE = 32 * R;
+  const int lane = threadIdx.x & 31;
+  uint32_t* ks = (uint32_t*)stage;                                 // [NE] sorted keys
+  uint16_t* par = (uint16_t*)(stage + 4 * NE);                     // [NE] parents
+  unsigned long long* acc = (unsigned long long*)(stage + 6 * NE);  // [NE] member sums
+  uint32_t k[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t idx = lane + 32 * r;
+    k[r] = kInv;
+    if (idx < n) {
+      const uint32_t c = col[a + idx], w = row[a + idx];
+      if (c < (uint32_t)ncols && w < (uint32_t)nrows) k[r] = (c << 9) | w;
+      else bad = true;
+    }
+  }
+  warp_bitonic<R>(k);
+#pragma unroll
+  for (int r = 0; r < R; ++r) ks[lane + 32 * r] = k[r];
+  __syncwarp();
+  bool valid[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t e = lane + 32u * r;
+    valid[r] = k[r] != kInv && !(e > 0 && ks[e - 1] == k[r]);
+    par[e] = (uint16_t)e;
+    acc[e] = 0ull;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (!valid[r]) continue;
+    const uint32_t e = lane + 32u * r;
+    for (uint32_t j = e + 1; j < NE; ++j) {
+      const uint32_t kj = ks[j];
+      if (kj == kInv || kj - k[r] > 513u) break;
+      const uint32_t dl = kj - k[r];
+      if (kj != ks[j - 1] && (dl == 1u || dl - 511u <= 2u)) uf_unite_pos(par, (int)e, (int)j);
+    }
+  }
+  __syncwarp();
+  uint32_t root_of[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) root_of[r] = valid[r] ? (uint32_t)uf_find(par, lane + 32 * r) : 0u;
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (valid[r])
+      atomicAdd(&acc[root_of[r]], (1ull << 56) | ((unsigned long long)(k[r] >> 9) << 28) | (k[r] & 511u));
+  __syncwarp();
+  uint32_t nroot = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t e = lane + 32u * r;
+    const bool root = valid[r] && root_of[r] == e;
+    const uint32_t rm = __ballot_sync(kFull, root);
+    const uint32_t rank = nroot + __popc(rm & ((1u << lane) - 1u));
+    nroot += __popc(rm);
+    if (root) {
+      const unsigned long long v = acc[e];
+      const uint32_t key16 = ((k[r] >> 9) << 8) | (k[r] & 255u);
+      store_cluster(out, g, a + rank, key16, (uint32_t)(v >> 56), (uint32_t)((v >> 28) & 0xFFFFFFFull),
+                    (uint32_t)(v & 0xFFFFFFFull));
+    }
+  }
+  __syncwarp();
+  return nroot;
+}
+
 enum { CM_NEXT = 0, CM_STATUS = 1, CM_CLASS = 8 };  // CM_CLASS..: sensors per size class
 
 template <int NT>
-__global__ void __launch_bounds__(NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
+__global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
                                                      WorkView wk) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ClusterLayout L = cluster_layout(NT);
@@ -460,9 +570,13 @@ __global__ void __launch_bounds__(NT) cluster_kernel(const DevGeometry* __restri
         const uint32_t s = s_list[(it < e4 ? 4 : 3) * kMaxSensors + (it < e4 ? it : it - e4)];
         const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
         const SensorGeo g = sensor_geo(geo, (int)s);
-        const uint32_t nroot =
-            n <= 64 ? cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, out, acc, bad)
-                    : cluster_sensor_smem(col, row, a, n, ncols, nrows, g, out, w_pk, w_par, bad);
+        uint32_t nroot;
+        if (n <= 64 && !kSortedUnionFor64)
+          nroot = cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, out, acc, bad);
+        else if (n <= 64) nroot = cluster_sensor_mid<2>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
+        else if (n <= 128) nroot = cluster_sensor_mid<4>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
+        else if (n <= 256) nroot = cluster_sensor_mid<8>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
+        else nroot = cluster_sensor_smem(col, row, a, n, ncols, nrows, g, out, w_pk, w_par, bad);
         if (lane == 0) s_cnt[s] = nroot;
       } else if (it < e2) {
         cluster_segments<32>(geo, col, row, s_soff, s_list[2 * kMaxSensors + (it - e3)], ns, out, acc, s_cnt, bad);
