@@ -6,9 +6,10 @@
 // (phase A) and seeds triplets with a in module i + 2, b in i + 1 and c in i
 // (phase B).  So this kernel keeps in shared memory only a ring of four module
 // slots (each: the module's hits ordered by phi bin, their canonical ids, the
-// bin ends and a used bitmap), the active tracks (double-buffered records)
-// and the next module's raw hits -- about 24 KB per event, so nine events
-// share an SM.  The hits come straight from the clustering output:
+// bin ends, a used bitmap and a bitmap of the running round's seed hits), the
+// active tracks (double-buffered records), the list of the round's unused
+// middle hits and the next module's raw hits -- about 24 KB per event, so
+// nine events share an SM.  The hits come straight from the clustering output:
 //   - round i copies module i - 2's hits into a staging buffer with cp.async
 //     during its phase B;
 //   - round i - 1 bins them by phi into the free slot during its phase A, on
@@ -39,10 +40,11 @@ namespace {
 constexpr int kRingSlots = 4;
 
 // ring slot: hits by phi bin, their canonical ids, bin ends (module-local),
-// used bitmap over the slot's positions
+// bitmaps over the slot's positions: used, and hits of seeds of the running
+// round (merged into used at the next round's start)
 constexpr uint32_t kSlotPos = 0, kSlotPid = 8 * kRingModHits, kSlotBins = kSlotPid + 2 * kRingModHits;
-constexpr uint32_t kSlotUsed = kSlotBins + 2 * kNB;
-constexpr uint32_t kSlotBytes = kSlotUsed + kRingModHits / 8;
+constexpr uint32_t kSlotUsed = kSlotBins + 2 * kNB, kSlotPend = kSlotUsed + kRingModHits / 8;
+constexpr uint32_t kSlotBytes = kSlotPend + kRingModHits / 8;
 // active-track records, per list: x, y, z, tx, ty (f32), track id (u16), hits, skips (u8)
 constexpr uint32_t kActBytes = kRingMaxAct * (5 * 4 + 2 + 1 + 1);
 static_assert(2 * kActBytes >= 3u * 4u * kRingMaxT, "ranking arrays fit the track lists");
@@ -50,7 +52,7 @@ static_assert(kRingSlots * kSlotBytes >= 2u * (kRingMaxH / 8), "seen bitmaps fit
 
 // shared-memory plan
 struct RingLayout {
-  uint32_t z, cb, misc, scan, wbin, pend, stage, slots, act, total;
+  uint32_t z, cb, misc, scan, wbin, blist, stage, slots, act, total;
 };
 
 __host__ __device__ constexpr uint32_t ralign16(uint32_t x) { return (x + 15u) & ~15u; }
@@ -63,7 +65,7 @@ __host__ __device__ inline RingLayout ring_layout() {
   L.misc = o; o = ralign16(o + 4 * 32);
   L.scan = o; o = ralign16(o + 4 * 32);
   L.wbin = o; o = ralign16(o + 3 * 4 * kNB);             // bin counters of up to three warps
-  L.pend = o; o = ralign16(o + 2 * kRingModHits);         // last round's seeds: b and c slot positions
+  L.blist = o; o = ralign16(o + kRingModHits);            // unused middle hits of the round
   L.stage = o; o = ralign16(o + 8 * kRingModHits);        // raw hits of the next module
   L.slots = o; o = ralign16(o + kRingSlots * kSlotBytes);
   L.act = o; o = ralign16(o + 2 * kActBytes);
@@ -72,7 +74,7 @@ __host__ __device__ inline RingLayout ring_layout() {
 }
 
 enum RMisc {
-  R_EVENT = 0, R_NTR = 1, R_MAXMOD = 2, R_NPEND = 3, R_KEPT = 5, R_TBASE = 7, R_HBASE = 8, R_SKIP = 10, R_NACT = 12
+  R_EVENT = 0, R_NTR = 1, R_MAXMOD = 2, R_NB = 3, R_KEPT = 5, R_TBASE = 7, R_HBASE = 8, R_SKIP = 10, R_NACT = 12
 };
 
 struct ActList {
@@ -144,11 +146,11 @@ __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned c
   float2* pos = (float2*)(slot + kSlotPos);
   uint16_t* pid = (uint16_t*)(slot + kSlotPid);
   uint16_t* bins = (uint16_t*)(slot + kSlotBins);
-  uint32_t* ub = (uint32_t*)(slot + kSlotUsed);
+  uint32_t* ub = (uint32_t*)(slot + kSlotUsed);  // then the pending bitmap
   const uint32_t c0 = cb[kSPM * m], n = (uint32_t)cb[kSPM * (m + 1)] - c0;
 #pragma unroll
   for (int u = 0; u < BPL; ++u) wc[BPL * lane + u] = 0;
-  if (lane < (int)(kRingModHits / 32)) ub[lane] = 0;
+  if (lane < (int)(2 * kRingModHits / 32)) ub[lane] = 0;
   __syncwarp();
   for (uint32_t j = lane; j < n; j += 32) {
     const float2 v = src(j);
@@ -184,12 +186,13 @@ struct Slot {
   const uint16_t* pid;
   const uint16_t* bins;
   uint32_t* used;
+  uint32_t* pend;
 };
 
 __device__ __forceinline__ Slot slot_of(unsigned char* slots, int m) {
   unsigned char* s = slots + (m & (kRingSlots - 1)) * kSlotBytes;
   return Slot{(const float2*)(s + kSlotPos), (const uint16_t*)(s + kSlotPid), (const uint16_t*)(s + kSlotBins),
-              (uint32_t*)(s + kSlotUsed)};
+              (uint32_t*)(s + kSlotUsed), (uint32_t*)(s + kSlotPend)};
 }
 
 // Sensor of canonical id k: the last s with cb[s] <= k.
@@ -215,8 +218,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
   uint32_t* s_misc = (uint32_t*)(smem + L.misc);
   uint32_t* s_scan = (uint32_t*)(smem + L.scan);
   uint32_t* s_wbin = (uint32_t*)(smem + L.wbin);
-  uint8_t* pend_b = (uint8_t*)(smem + L.pend);
-  uint8_t* pend_c = pend_b + kRingModHits;
+  uint8_t* blist = (uint8_t*)(smem + L.blist);
   float2* stage = (float2*)(smem + L.stage);
   unsigned char* slots = smem + L.slots;
   const ActList act[2] = {act_list(smem + L.act), act_list(smem + L.act + kActBytes)};
@@ -302,14 +304,11 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
       const float zi = s_z[i];
       const Slot Si = slot_of(slots, i), Sb = slot_of(slots, i + 1), Sa = slot_of(slots, i + 2);
       bool ovf = false;
-      // phase A: the b and c hits of the last round's seeds become used;
-      // every active track is extended into module i by its best hit (GA
-      // lanes per track); the last warp bins module i - 1 into the free slot
-      const uint32_t npend = s_misc[R_NPEND];
-      for (uint32_t j = tid; j < npend; j += NT) {
-        set_bit(Sa.used, pend_b[j]);  // b of a seed of round i + 1 lies in module i + 2
-        set_bit(Sb.used, pend_c[j]);  // its c in module i + 1
-      }
+      // phase A: every active track is extended into module i by its best
+      // hit (GA lanes per track).  Meanwhile warp NW - 2 makes the b and c
+      // hits of the last round's seeds used (modules i + 2 and i + 1) and
+      // lists the unused middle hits of module i + 1, and warp NW - 1 bins
+      // module i - 1 into the free slot.
       const uint32_t nact = s_misc[R_NACT + cur];
       const ActList& A = act[cur];
       const ActList& N = act[cur ^ 1];
@@ -384,12 +383,28 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
           N.skip[o] = (uint8_t)sk;
         }
       }
+      if (warp == NW - 2) {
+        if (lane < (int)(2 * kRingModHits / 32)) {
+          const Slot& S = lane < (int)(kRingModHits / 32) ? Sa : Sb;
+          const int w = lane % (kRingModHits / 32);
+          S.used[w] |= S.pend[w];
+          S.pend[w] = 0;
+        }
+        __syncwarp();
+        const uint32_t nb = (uint32_t)s_cb[kSPM * (i + 2)] - s_cb[kSPM * (i + 1)];
+        uint32_t cnt = 0;
+        for (uint32_t q0 = 0; q0 < nb; q0 += 32) {
+          const uint32_t qb = q0 + lane;
+          const bool un = qb < nb && !bit(Sb.used, qb);
+          const uint32_t m = __ballot_sync(kFull, un);
+          if (un) blist[cnt + __popc(m & ((1u << lane) - 1u))] = (uint8_t)qb;
+          cnt += __popc(m);
+        }
+        if (lane == 0) s_misc[R_NB] = cnt;
+      }
       if (warp == NW - 1 && i >= 1) bin_module(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
       if (__syncthreads_or(ovf)) { overflow = true; break; }
-      if (tid == 0) {
-        s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
-        s_misc[R_NPEND] = 0;
-      }
+      if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
       if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage);  // binned in the next round
       // phase B: seeds with the middle hit b in module i + 1
       {
@@ -397,10 +412,10 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
         const float dzab = fsub(za, zb), dzc = fsub(zi, zb), dzbc = fsub(zb, zi);
         constexpr int NG = NT / GB;
         const int g = tid / GB, gl = tid % GB;
-        const uint32_t nb = (uint32_t)s_cb[kSPM * (i + 2)] - s_cb[kSPM * (i + 1)];
-        for (uint32_t b0 = 0; b0 < nb; b0 += NG) {
-          const uint32_t qb = b0 + g;
-          const bool has = qb < nb && !bit(Sb.used, qb);
+        const uint32_t nbl = s_misc[R_NB];
+        for (uint32_t b0 = 0; b0 < nbl; b0 += NG) {
+          const bool has = b0 + g < nbl;
+          const uint32_t qb = has ? blist[b0 + g] : 0u;
           unsigned long long best = ~0ull;
           uint32_t bpos = 0;
           float2 vb = make_float2(0.0f, 0.0f);
@@ -464,9 +479,8 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
               mpc[t] = (uint16_t)ic;
               mn[t] = 3;
               mseed[t] = __uint_as_float((uint32_t)(best >> 32));
-              const uint32_t pe = atomicAdd(&s_misc[R_NPEND], 1u);  // one per b: < nb <= kRingModHits
-              pend_b[pe] = (uint8_t)qb;
-              pend_c[pe] = (uint8_t)bpos;
+              set_bit(Sb.pend, qb);
+              set_bit(Si.pend, bpos);
               vc = Si.pos[bpos];
               seeded = true;
             }
@@ -619,8 +633,8 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
 }
 
 // Lanes per active track in phase A and per middle hit in phase B.
-constexpr int kRingGroupA = 2;
-constexpr int kRingGroupB = 2;
+constexpr int kRingGroupA = 1;
+constexpr int kRingGroupB = 4;
 
 }  // namespace
 
