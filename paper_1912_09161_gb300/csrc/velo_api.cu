@@ -175,7 +175,7 @@ FixedPlan plan_fixed() {
 }
 
 struct WorkPlan {
-  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, hits, xy, mod, clx, cly, clk, total;
+  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, hits, clx, cly, clk, total;
 };
 
 WorkPlan plan_work(const velo_config& c) {
@@ -190,8 +190,6 @@ WorkPlan plan_work(const velo_config& c) {
   a.nh = o; o = align256(o + 2ull * c.max_tracks);
   a.ho = o; o = align256(o + 4ull * c.max_tracks);
   a.hits = o; o = align256(o + 4ull * c.max_track_hits);
-  a.xy = o; o = align256(o + 8ull * c.max_track_hits);
-  a.mod = o; o = align256(o + 1ull * c.max_track_hits);
   if (c.flags & VELO_CFG_CLUSTERS) {
     a.clx = o; o = align256(o + 4ull * c.max_pixels);
     a.cly = o; o = align256(o + 4ull * c.max_pixels);
@@ -215,8 +213,6 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
   w.tr_nhits = (uint16_t*)(base + a.nh);
   w.tr_hitoff = (uint32_t*)(base + a.ho);
   w.tr_hits = (uint32_t*)(base + a.hits);
-  w.tr_xy = (float2*)(base + a.xy);
-  w.tr_mod = (uint8_t*)(base + a.mod);
   w.cap_tracks = (uint32_t)c.max_tracks;
   w.cap_hits = (uint32_t)c.max_track_hits;
   w.cl_x = (c.flags & VELO_CFG_CLUSTERS) ? (float*)(base + a.clx) : nullptr;
@@ -274,7 +270,7 @@ int setup_ring(velo_handle* h) {
   h->ring_per_sm = occ > kRingCtasPerSm ? kRingCtasPerSm : occ;
   const size_t n = (size_t)h->ring_per_sm * h->n_sm;
   size_t o = 0;
-  const size_t o_trk = o; o = align256(o + n * kRingMaxT * kRingTrackHits * sizeof(uint16_t));
+  const size_t o_trk = o; o = align256(o + n * kRingMaxT * kRingTrackHits * sizeof(uint32_t));
   const size_t o_sh = o; o = align256(o + n * 3 * kRingMaxT * sizeof(uint16_t));
   const size_t o_n = o; o = align256(o + n * kRingMaxT);
   const size_t o_seed = o; o = align256(o + n * kRingMaxT * sizeof(float));
@@ -284,7 +280,7 @@ int setup_ring(velo_handle* h) {
     return fail(VELO_ERR_NOMEM, "cudaMalloc(%zu) (ring): %s", o, cudaGetErrorString(e));
   }
   char* b = (char*)h->ring_buf;
-  h->wk.ring = RingScratch{(uint16_t*)(b + o_trk), (uint16_t*)(b + o_sh), (uint8_t*)(b + o_n), (float*)(b + o_seed)};
+  h->wk.ring = RingScratch{(uint32_t*)(b + o_trk), (uint16_t*)(b + o_sh), (uint8_t*)(b + o_n), (float*)(b + o_seed)};
   return VELO_OK;
 }
 
@@ -391,7 +387,7 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[2], st, mark));
   CUDA_TRY(launch_scan(E, wk, out, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[3], st, mark));
-  CUDA_TRY(launch_emit(E, h->d_geo, h->par, wk, out, st));
+  CUDA_TRY(launch_emit(E, h->d_geo, h->par, ev, wk, out, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[4], st, mark));
   CUDA_TRY(cudaMemcpyAsync(h->h_totals, &h->d_cnt->error, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   if (tm) CUDA_TRY(cudaMemcpyAsync(h->h_cnt, h->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));

@@ -34,6 +34,18 @@ __device__ __forceinline__ int phi_bin(float pa) {
   return b < 0 ? 0 : (b >= kNB ? kNB - 1 : b);
 }
 
+// Sensor of an event's canonical hit id k, given the canonical id of every
+// sensor's first hit cb[0, ns]: the last s with cb[s] <= k.
+__device__ __forceinline__ int sensor_of(const uint16_t* cb, int ns, uint32_t k) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cb[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll

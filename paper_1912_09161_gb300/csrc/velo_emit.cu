@@ -87,14 +87,23 @@ cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output
 constexpr int kEmitThreads = 128;
 
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
-                                                            DevParams par, WorkView wk, velo_output out) {
+                                                            DevParams par, EventsView ev, WorkView wk,
+                                                            velo_output out) {
   __shared__ float s_z[kMaxModules];
+  __shared__ uint16_t s_cb[kMaxSensors + 1];  // canonical id of each sensor's first hit
+  __shared__ uint32_t s_so[kMaxSensors + 1];  // each sensor's first hit in the clustering output
+  const int ns = geo->n_sensors;
   for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
-  __syncthreads();
   const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
   const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
   const float kms = fit_kms(par);
   for (uint32_t e = blockIdx.x; e < n_events; e += gridDim.x) {
+    __syncthreads();
+    for (int s = threadIdx.x; s <= ns; s += blockDim.x) {
+      s_cb[s] = wk.ev_cbase[(size_t)e * (kMaxSensors + 1) + s];
+      s_so[s] = ev.sensor_off[(size_t)e * ns + s];
+    }
+    __syncthreads();
     const EventRec r = wk.rec[e];
     const uint32_t o0 = out.track_off[e], h0 = r.out_hit_base;
     uint32_t status = r.status;
@@ -105,15 +114,22 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, c
         const uint32_t t = r.track_base + k;
         const uint32_t nh = wk.tr_nhits[t];
         const uint32_t hoff = wk.tr_hitoff[t];
-        const float2* xy = wk.tr_xy + r.hit_base + hoff;
-        const uint8_t* md = wk.tr_mod + r.hit_base + hoff;
+        // the track's hits from the clustering output, by canonical id
+        float2 xy[kMaxModules];
+        uint8_t md[kMaxModules];
+        for (uint32_t j = 0; j < nh; ++j) {
+          const uint32_t h = wk.tr_hits[r.hit_base + hoff + j];
+          const uint32_t id = h & 0xFFFFu, m = h >> 16, s0 = kSPM * m;
+          const uint32_t s = s0 + (id >= s_cb[s0 + 1]) + (id >= s_cb[s0 + 2]) + (id >= s_cb[s0 + 3]);
+          xy[j] = wk.prov[s_so[s] + (id - s_cb[s])];
+          md[j] = (uint8_t)m;
+        }
         float st[12];
         fit_track(
             nh,
             [&](uint32_t j, float& x, float& y, int& m) {
-              const float2 v = xy[j];
-              x = v.x;
-              y = v.y;
+              x = xy[j].x;
+              y = xy[j].y;
               m = md[j];
             },
             s_z, sig2, kms, st);
@@ -124,7 +140,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, c
         out.hit_off[o0 + k] = h0 + hoff;
       }
       for (uint32_t k = threadIdx.x; k < r.n_hits; k += blockDim.x)
-        out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k];
+        out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k] & 0xFFFFu;
     } else if (r.n_tracks) {
       status |= VELO_EV_TRUNCATED;
     }
@@ -144,11 +160,11 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, c
   }
 }
 
-cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const WorkView& wk,
-                        const velo_output& out, cudaStream_t st) {
+cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
+                        const WorkView& wk, const velo_output& out, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;
   int blocks = (int)(n_events < 152u * 16u ? n_events : 152u * 16u);
-  emit_kernel<<<blocks, kEmitThreads, 0, st>>>(n_events, geo, par, wk, out);
+  emit_kernel<<<blocks, kEmitThreads, 0, st>>>(n_events, geo, par, ev, wk, out);
   return cudaGetLastError();
 }
 

@@ -89,7 +89,7 @@ struct Counters {
 // Global region of the module-window kernel, one per CTA (arrays of n_ctas
 // regions): each candidate's hit list and its seed (canonical ids).
 struct RingScratch {
-  uint16_t* trk;      // [kRingMaxT * kRingTrackHits] canonical hit ids per candidate
+  uint32_t* trk;      // [kRingMaxT * kRingTrackHits] hits per candidate: module << 16 | canonical id
   uint16_t* seed_hit; // [3 * kRingMaxT] seed hits a, b, c
   uint8_t* n_hits;    // [kRingMaxT]
   float* seed;        // [kRingMaxT] seed scatter, then the classifier logit
@@ -115,13 +115,11 @@ struct WorkView {
   uint16_t* prov_key;            // [cap_pixels] smallest pixel key (cluster output only)
   uint16_t* ev_cbase;            // [max_events][kMaxSensors + 1] canonical id of each sensor's first hit
   // scratch tracks (SoA), bump-allocated per event, canonical order within
-  // the event; the emit kernel fits them from their hits' positions
+  // the event; the emit kernel fits them from their hits' ids
   float* tr_logit;               // [cap_tracks] classifier logit (0 without the classifier)
   uint16_t* tr_nhits;            // [cap_tracks]
   uint32_t* tr_hitoff;           // [cap_tracks] first hit, relative to the event's hit base
-  uint32_t* tr_hits;             // [cap_hits] event-local canonical ids
-  float2* tr_xy;                 // [cap_hits] hit positions (global x, y)
-  uint8_t* tr_mod;               // [cap_hits] hit modules
+  uint32_t* tr_hits;             // [cap_hits] module << 16 | event-local canonical id
   // tracking-kernel hit slots per class: kMaxModules positions per candidate,
   // max_tracks candidates per CTA, one region per CTA of the class
   uint16_t* trk_hits[kMaxClasses];
@@ -159,8 +157,8 @@ cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, cons
 
 // Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
-cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const WorkView& wk,
-                        const velo_output& out, cudaStream_t st);
+cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
+                        const WorkView& wk, const velo_output& out, cudaStream_t st);
 
 // Working storage of a handle outside its own arena (serving): the capacities
 // a call of n_events / n_pixels gets, the bytes they take, and the rebinding

@@ -516,8 +516,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
     if (s_misc[M_SKIP]) continue;
     const uint32_t tb = s_misc[M_TBASE], hb = s_misc[M_HBASE];
 
-    // kept tracks to scratch in canonical order: hit ids, and the hit
-    // positions and modules the emit kernel fits
+    // kept tracks to scratch in canonical order: their hits as module << 16 |
+    // canonical id (the emit kernel fits them from the clustering output)
     for (uint32_t t = tid; t < ntr; t += NT) {
       if (t_key[t] == 0xFFFFFFFFu) continue;
       const uint32_t r = t_rank[t], n = t_n[t];
@@ -527,9 +527,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
       for (uint32_t k = 0; k < n; ++k) {
         const uint32_t p = th[k];
         while (s_cb[kSPM * m] > p) --m;
-        wk.tr_hits[h0 + k] = pid[p];
-        wk.tr_xy[h0 + k] = pos[p];
-        wk.tr_mod[h0 + k] = (uint8_t)m;
+        wk.tr_hits[h0 + k] = ((uint32_t)m << 16) | pid[p];
       }
       const size_t o = (size_t)tb + r;
       wk.tr_logit[o] = use_mlp ? t_seed[t] : 0.0f;

@@ -16,8 +16,8 @@
 //     a warp that phase A leaves idle;
 // so every hit is read from global memory once.  After the rounds the kernel
 // applies the plain cuts (or the classifier), ranks the kept candidates
-// canonically and writes their hits (ids, positions, modules) to scratch for
-// the emit kernel, which fits them.  Candidate hit lists (canonical ids, up
+// canonically and writes their hits (module, canonical id) to scratch for the
+// emit kernel, which fits them.  Candidate hit lists (canonical ids, up
 // to kRingTrackHits) and seed records live in the CTA's global region.
 // Events beyond the window's capacities (a module of more than kRingModHits
 // hits, more than kRingMaxAct active tracks, kRingMaxT candidates, kRingMaxH
@@ -195,17 +195,6 @@ __device__ __forceinline__ Slot slot_of(unsigned char* slots, int m) {
               (uint32_t*)(s + kSlotUsed), (uint32_t*)(s + kSlotPend)};
 }
 
-// Sensor of canonical id k: the last s with cb[s] <= k.
-__device__ __forceinline__ int sensor_of(const uint16_t* cb, int ns, uint32_t k) {
-  int lo = 0, hi = ns - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cb[mid] <= k) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 template <int GA, int GB>
 __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kernel(const DevGeometry* __restrict__ geo,
                                                                      DevParams par, EventsView ev, WorkView wk,
@@ -236,7 +225,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
 
   // this CTA's global region
   const RingScratch& R = wk.ring;
-  uint16_t* trk = R.trk + (size_t)blockIdx.x * kRingMaxT * kRingTrackHits;
+  uint32_t* trk = R.trk + (size_t)blockIdx.x * kRingMaxT * kRingTrackHits;  // module << 16 | canonical id
   uint16_t* mpa = R.seed_hit + (size_t)blockIdx.x * 3 * kRingMaxT;
   uint16_t* mpb = mpa + kRingMaxT;
   uint16_t* mpc = mpb + kRingMaxT;
@@ -353,7 +342,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
             if (n >= kRingTrackHits) {
               ovf = true;
             } else {
-              trk[(size_t)t * kRingTrackHits + n] = (uint16_t)(best >> 16);  // canonical id
+              trk[(size_t)t * kRingTrackHits + n] = ((uint32_t)i << 16) | (uint32_t)((best >> 16) & 0xFFFFu);
               mn[t] = (uint8_t)(n + 1);
               set_bit(Si.used, p);
               tx = fdiv(fsub(xl, v.x), dzq);
@@ -470,10 +459,10 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
             } else {
               const uint32_t ia = (uint32_t)(best >> 16) & 0xFFFFu, ic = (uint32_t)best & 0xFFFFu;
               const uint32_t ib = Sb.pid[qb];
-              uint16_t* th = trk + (size_t)t * kRingTrackHits;
-              th[0] = (uint16_t)ia;
-              th[1] = (uint16_t)ib;
-              th[2] = (uint16_t)ic;
+              uint32_t* th = trk + (size_t)t * kRingTrackHits;
+              th[0] = ((uint32_t)(i + 2) << 16) | ia;
+              th[1] = ((uint32_t)(i + 1) << 16) | ib;
+              th[2] = ((uint32_t)i << 16) | ic;
               mpa[t] = (uint16_t)ia;
               mpb[t] = (uint16_t)ib;
               mpc[t] = (uint16_t)ic;
@@ -529,10 +518,10 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
       }
       __syncthreads();
       for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint16_t* th = trk + (size_t)t * kRingTrackHits;
+        const uint32_t* th = trk + (size_t)t * kRingTrackHits;
         const uint32_t n = mn[t];
         for (uint32_t k = 0; k < n; ++k) {
-          const uint32_t h = th[k], b = 1u << (h & 31);
+          const uint32_t h = th[k] & 0xFFFFu, b = 1u << (h & 31);
           if (atomicOr(&seen1[h >> 5], b) & b) atomicOr(&seen2[h >> 5], b);
         }
       }
@@ -548,20 +537,19 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
       const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
       const float kms = fit_kms(par);
       for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint16_t* th = trk + (size_t)t * kRingTrackHits;
+        const uint32_t* th = trk + (size_t)t * kRingTrackHits;
         const uint32_t n = mn[t];
         float st[12];
         fit_track(
             n,
             [&](uint32_t k, float& x, float& y, int& m) {
-              const float2 v = hit_xy(th[k], m);
+              const float2 v = hit_xy(th[k] & 0xFFFFu, m);
               x = v.x;
               y = v.y;
             },
             s_z, sig2, kms, st);
         float f[kMlpIn];
-        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, sensor_of(s_cb, ns, th[0]) / kSPM,
-                     sensor_of(s_cb, ns, th[n - 1]) / kSPM, f);
+        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, (int)(th[0] >> 16), (int)(th[n - 1] >> 16), f);
         const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
         mseed[t] = logit;
         t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)mpa[t] << 16) | mpb[t]) : 0xFFFFFFFFu;
@@ -609,21 +597,14 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
     if (s_misc[R_SKIP]) continue;
     const uint32_t tb = s_misc[R_TBASE], hb = s_misc[R_HBASE];
 
-    // kept tracks to scratch in canonical order: hit ids, and the hit
-    // positions and modules the emit kernel fits
+    // kept tracks to scratch in canonical order: their hits' canonical ids
+    // (the emit kernel fits them from the clustering output)
     for (uint32_t t = tid; t < ntr; t += NT) {
       if (t_key[t] == 0xFFFFFFFFu) continue;
       const uint32_t r = t_rank[t], n = mn[t];
-      const uint16_t* th = trk + (size_t)t * kRingTrackHits;
+      const uint32_t* th = trk + (size_t)t * kRingTrackHits;
       const uint32_t h0 = hb + t_hoff[r];
-      for (uint32_t k = 0; k < n; ++k) {
-        int m;
-        const uint32_t id = th[k];
-        const float2 v = hit_xy(id, m);
-        wk.tr_hits[h0 + k] = id;
-        wk.tr_xy[h0 + k] = v;
-        wk.tr_mod[h0 + k] = (uint8_t)m;
-      }
+      for (uint32_t k = 0; k < n; ++k) wk.tr_hits[h0 + k] = th[k];  // module << 16 | canonical id
       const size_t o = (size_t)tb + r;
       wk.tr_logit[o] = use_mlp ? mseed[t] : 0.0f;
       wk.tr_nhits[o] = (uint16_t)n;
