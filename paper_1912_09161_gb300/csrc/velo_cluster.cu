@@ -2,54 +2,44 @@
 // the connected components of the fired pixels of a sensor; the raw input is
 // segmented by readout unit, so sensors are decoded in parallel, section 2.3).
 //
-// One CTA per event.  Sensors are sorted into size classes; warps take work
-// items from a per-event counter, largest sensors first.  A sensor of at most
-// 64 pixels is clustered in registers: up to 8, 16 or 32 pixels in a segment
-// of that many lanes (four, two or one sensor per warp), up to 64 with two
-// pixels per lane.  A larger one is staged in the warp's shared-memory slice
-// and joined by union-find.  Every cluster becomes a hit at a provisional position (the
-// sensor's pixel offset + the cluster's rank by smallest pixel key), which
-// orders hits exactly like their canonical ids; the per-sensor canonical
-// bases and the event's hit count go to global memory, and the event is
-// queued for the tracking-kernel class whose shared-memory plan holds it.
+// One CTA per event (cluster_event).  Sensors are sorted into size classes;
+// warps take work items from a per-event counter, largest sensors first.  A
+// sensor of at most 64 pixels is clustered in registers: up to 8, 16 or 32
+// pixels in a segment of that many lanes (four, two or one sensor per warp),
+// up to 64 with two pixels per lane.  Up to 256 pixels: keys sorted in
+// registers, union-find in the warp's shared-memory slice; up to 1000 (warp 0
+// only): union-find over unsorted staged pixels.  Every cluster becomes a hit
+// at a provisional position (the sensor's pixel offset + the cluster's rank
+// by smallest pixel key), which orders hits exactly like their canonical ids;
+// the per-sensor canonical bases and the event's hit count go to global
+// memory, and the event is queued for the tracking-kernel class whose
+// shared-memory plan holds it.
 #include <stdint.h>
 
 #include "velo_device.cuh"
 
 namespace velo {
 
-constexpr int kClusterThreads = 256;
 // Sensors of 33 to 64 pixels: neighbour masks in registers (false) or the
 // sorted union-find of the larger sensors (true).
 constexpr bool kSortedUnionFor64 = false;
-constexpr uint32_t kWarpStage = 1000;           // raw pixels a warp can stage for one large sensor
-constexpr uint32_t kAccBytes = 8 * 64;          // per-warp packed accumulators
-constexpr uint32_t kWarpSlice = kAccBytes + 6 * kWarpStage;
-
-// Sensor size classes (raw pixels): <= 8, <= 16, <= 32, <= 64, <= kWarpStage,
-// beyond.  The first three are clustered 4, 2 and 1 at a time per warp.
-constexpr int kSizeClasses = 6;
-
-struct ClusterLayout {
-  uint32_t soff, ccnt, misc, scan, lists, warps, total;
-};
-
-__host__ __device__ inline uint32_t c_align16(uint32_t x) { return (x + 15u) & ~15u; }
-
-__host__ __device__ inline ClusterLayout cluster_layout(int n_threads) {
-  ClusterLayout L;
-  uint32_t o = 0;
-  L.soff = o; o = c_align16(o + 4 * (kMaxSensors + 1));
-  L.ccnt = o; o = c_align16(o + 4 * (kMaxSensors + 1));
-  L.misc = o; o = c_align16(o + 4 * 32);
-  L.scan = o; o = c_align16(o + 4 * 32);
-  L.lists = o; o = c_align16(o + kSizeClasses * kMaxSensors);  // u8 sensor ids per size class
-  L.warps = o; o = c_align16(o + kWarpSlice * (uint32_t)(n_threads / 32));
-  L.total = o;
-  return L;
+constexpr uint32_t kWarpStage = 1000;  // raw pixels warp 0 can stage for one large sensor
+constexpr uint32_t kMidStage = 256;    // raw pixels of the sorted union-find path
+constexpr uint32_t kAccBytes = 8 * 64; // per-warp packed accumulators
+// Per-warp shared-memory slices: warp 0 stages sensors of up to kWarpStage
+// pixels (keys and parents), the other warps up to kMidStage (keys, parents,
+// member sums).
+constexpr uint32_t kBigSlice = kAccBytes + 6 * kWarpStage;
+constexpr uint32_t kSmallSlice = kAccBytes + 14 * kMidStage;
+static_assert(kBigSlice >= kSmallSlice, "warp 0 can run every path");
+__host__ __device__ constexpr uint32_t cluster_warps_bytes(int n_warps) {
+  return kBigSlice + (uint32_t)(n_warps - 1) * kSmallSlice;
 }
 
-uint32_t cluster_smem_bytes(int n_threads) { return cluster_layout(n_threads).total; }
+// Sensor size classes (raw pixels): <= 8, <= 16, <= 32, <= 64, <= kMidStage,
+// <= kWarpStage, beyond.  The first three are clustered 4, 2 and 1 at a time
+// per warp; the sixth only by warp 0; the last is beyond capacity.
+constexpr int kSizeClasses = 7;
 
 struct SensorGeo {
   float ox, oy, cdx, cdy, rdx, rdy, pitch;
@@ -76,37 +66,64 @@ __device__ __forceinline__ void store_cluster(const HitOut& out, const SensorGeo
   if (out.key) out.key[p] = (uint16_t)key16;
 }
 
+// Compare-exchange of registers r and r ^ D (distance 32 D) in the bitonic
+// stage of block size kk.
+template <int R, int D>
+__device__ __forceinline__ void bitonic_regs(uint32_t (&k)[R], uint32_t kk, int lane) {
+  if constexpr (D < R) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int rp = r ^ D;
+      if (rp > r) {
+        const bool up = ((lane + 32u * r) & kk) == 0;
+        const uint32_t lo = min(k[r], k[rp]), hi = max(k[r], k[rp]);
+        k[r] = up ? lo : hi;
+        k[rp] = up ? hi : lo;
+      }
+    }
+  }
+}
+
+// Compare-exchange across lanes at distance j < 32 in the stage of block
+// size kk.
+template <int R>
+__device__ __forceinline__ void bitonic_lanes(uint32_t (&k)[R], uint32_t kk, uint32_t j, int lane) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t o = __shfl_xor_sync(kFull, k[r], j);
+    const uint32_t e = lane + 32u * r;
+    const bool up = (e & kk) == 0, lower = (e & j) == 0;
+    k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
+  }
+}
+
 // Ascending bitonic sort of 32 R keys held R per lane (element e = lane + 32 r
 // in register r): exchanges between registers for distances of 32 and more,
-// shuffles below.
+// shuffles below.  Up to 64 keys the network is unrolled; beyond, the stages
+// are loops (one copy of each step), which keeps the code small enough to
+// stay in the instruction cache next to the other clustering paths.
 template <int R>
 __device__ __forceinline__ void warp_bitonic(uint32_t (&k)[R]) {
   constexpr uint32_t NE = 32 * R;
   const int lane = threadIdx.x & 31;
+  if constexpr (R <= 2) {
 #pragma unroll
-  for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
+    for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
 #pragma unroll
-    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int rp = r ^ (int)(j >> 5);
-          if (rp > r) {
-            const uint32_t e = lane + 32u * r;
-            const bool up = (e & kk) == 0;
-            const uint32_t lo = min(k[r], k[rp]), hi = max(k[r], k[rp]);
-            k[r] = up ? lo : hi;
-            k[rp] = up ? hi : lo;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const uint32_t o = __shfl_xor_sync(kFull, k[r], j);
-          const uint32_t e = lane + 32u * r;
-          const bool up = (e & kk) == 0, lower = (e & j) == 0;
-          k[r] = (lower == up) ? min(k[r], o) : max(k[r], o);
-        }
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+        if (j >= 32) bitonic_regs<R, 1>(k, kk, lane);
+        else bitonic_lanes<R>(k, kk, j, lane);
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (uint32_t kk = 2; kk <= NE; kk <<= 1) {
+#pragma unroll 1
+      for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+        if (j == 128) bitonic_regs<R, 4>(k, kk, lane);
+        else if (j == 64) bitonic_regs<R, 2>(k, kk, lane);
+        else if (j == 32) bitonic_regs<R, 1>(k, kk, lane);
+        else bitonic_lanes<R>(k, kk, j, lane);
       }
     }
   }
@@ -337,7 +354,7 @@ __device__ __forceinline__ int uf_find(const volatile uint16_t* par, int x) {
   while ((p = par[x]) != x) x = p;
   return x;
 }
-__device__ void uf_unite(uint16_t* par, const uint32_t* pk, int x, int y) {
+__device__ inline void uf_unite(uint16_t* par, const uint32_t* pk, int x, int y) {
   const volatile uint16_t* vp = par;
   while (true) {
     x = uf_find(vp, x);
@@ -351,7 +368,7 @@ __device__ void uf_unite(uint16_t* par, const uint32_t* pk, int x, int y) {
 
 // Larger sensors (n <= kWarpStage, 1000 raw pixels): pixels staged in the warp's slice,
 // repeated pixels dropped, 8-neighbours joined by union-find, roots ranked.
-__device__ uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
+__device__ inline uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
                                         uint32_t a, uint32_t n, int ncols, int nrows, const SensorGeo& g,
                                         const HitOut& out, uint32_t* k_, uint16_t* p_, bool& bad) {
   const int lane = threadIdx.x & 31;
@@ -411,7 +428,7 @@ __device__ uint32_t cluster_sensor_smem(const uint16_t* __restrict__ col, const 
 // Union of the components of sorted positions x and y (lock-free on parent
 // indices): the root with the larger position goes under the one with the
 // smaller, so every root ends at its component's smallest position.
-__device__ void uf_unite_pos(uint16_t* par, int x, int y) {
+__device__ inline void uf_unite_pos(uint16_t* par, int x, int y) {
   const volatile uint16_t* vp = par;
   while (true) {
     x = uf_find(vp, x);
@@ -432,72 +449,75 @@ __device__ void uf_unite_pos(uint16_t* par, int x, int y) {
 // repeated pixels are equal neighbours in sorted order; each pixel scans
 // forward while keys stay within 513 and joins its 8-neighbours by
 // union-find; sums go to the component roots (smallest positions, so
-// smallest keys), which are ranked in sorted order.
+// smallest keys), which are ranked in sorted order.  After the sort every
+// step is one loop over the lane's positions e = lane + 32 r (one copy of
+// its code whatever R).
 template <int R>
 __device__ uint32_t cluster_sensor_mid(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row, uint32_t a,
                                        uint32_t n, int ncols, int nrows, const SensorGeo& g, const HitOut& out,
                                        unsigned char* stage, bool& bad) {
   constexpr uint32_t NE = 32 * R;
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31;
   uint32_t* ks = (uint32_t*)stage;                                 // [NE] sorted keys
   uint16_t* par = (uint16_t*)(stage + 4 * NE);                     // [NE] parents
   unsigned long long* acc = (unsigned long long*)(stage + 6 * NE);  // [NE] member sums
-  uint32_t k[R];
+  {
+    uint32_t k[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t idx = lane + 32 * r;
-    k[r] = kInv;
-    if (idx < n) {
-      const uint32_t c = col[a + idx], w = row[a + idx];
-      if (c < (uint32_t)ncols && w < (uint32_t)nrows) k[r] = (c << 9) | w;
-      else bad = true;
+    for (int r = 0; r < R; ++r) {
+      const uint32_t idx = lane + 32 * r;
+      k[r] = kInv;
+      if (idx < n) {
+        const uint32_t c = col[a + idx], w = row[a + idx];
+        if (c < (uint32_t)ncols && w < (uint32_t)nrows) k[r] = (c << 9) | w;
+        else bad = true;
+      }
     }
+    warp_bitonic<R>(k);
+#pragma unroll
+    for (int r = 0; r < R; ++r) ks[lane + 32 * r] = k[r];
   }
-  warp_bitonic<R>(k);
-#pragma unroll
-  for (int r = 0; r < R; ++r) ks[lane + 32 * r] = k[r];
   __syncwarp();
-  bool valid[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t e = lane + 32u * r;
-    valid[r] = k[r] != kInv && !(e > 0 && ks[e - 1] == k[r]);
+  // a valid position holds a pixel that differs from its sorted predecessor
+  auto valid = [&](uint32_t e, uint32_t ke) { return ke != kInv && !(e > 0 && ks[e - 1] == ke); };
+#pragma unroll 1
+  for (uint32_t e = lane; e < NE; e += 32) {
     par[e] = (uint16_t)e;
     acc[e] = 0ull;
   }
   __syncwarp();
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    if (!valid[r]) continue;
-    const uint32_t e = lane + 32u * r;
+#pragma unroll 1
+  for (uint32_t e = lane; e < NE; e += 32) {
+    const uint32_t ke = ks[e];
+    if (!valid(e, ke)) continue;
     for (uint32_t j = e + 1; j < NE; ++j) {
       const uint32_t kj = ks[j];
-      if (kj == kInv || kj - k[r] > 513u) break;
-      const uint32_t dl = kj - k[r];
+      if (kj == kInv || kj - ke > 513u) break;
+      const uint32_t dl = kj - ke;
       if (kj != ks[j - 1] && (dl == 1u || dl - 511u <= 2u)) uf_unite_pos(par, (int)e, (int)j);
     }
   }
   __syncwarp();
-  uint32_t root_of[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) root_of[r] = valid[r] ? (uint32_t)uf_find(par, lane + 32 * r) : 0u;
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-    if (valid[r])
-      atomicAdd(&acc[root_of[r]], (1ull << 56) | ((unsigned long long)(k[r] >> 9) << 28) | (k[r] & 511u));
+  // the forest is final: member sums to the roots
+#pragma unroll 1
+  for (uint32_t e = lane; e < NE; e += 32) {
+    const uint32_t ke = ks[e];
+    if (!valid(e, ke)) continue;
+    const int root = uf_find(par, (int)e);
+    atomicAdd(&acc[root], (1ull << 56) | ((unsigned long long)(ke >> 9) << 28) | (ke & 511u));
+  }
   __syncwarp();
   uint32_t nroot = 0;
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const uint32_t e = lane + 32u * r;
-    const bool root = valid[r] && root_of[r] == e;
+#pragma unroll 1
+  for (uint32_t e = lane; e < NE; e += 32) {
+    const uint32_t ke = ks[e];
+    const bool root = valid(e, ke) && par[e] == e;
     const uint32_t rm = __ballot_sync(kFull, root);
     const uint32_t rank = nroot + __popc(rm & ((1u << lane) - 1u));
     nroot += __popc(rm);
     if (root) {
       const unsigned long long v = acc[e];
-      const uint32_t key16 = ((k[r] >> 9) << 8) | (k[r] & 255u);
+      const uint32_t key16 = ((ke >> 9) << 8) | (ke & 255u);
       store_cluster(out, g, a + rank, key16, (uint32_t)(v >> 56), (uint32_t)((v >> 28) & 0xFFFFFFFull),
                     (uint32_t)(v & 0xFFFFFFFull));
     }
@@ -508,66 +528,88 @@ __device__ uint32_t cluster_sensor_mid(const uint16_t* __restrict__ col, const u
 
 enum { CM_NEXT = 0, CM_STATUS = 1, CM_CLASS = 8 };  // CM_CLASS..: sensors per size class
 
+// Shared memory for clustering one event.
+struct ClusterSmem {
+  uint32_t* soff;        // [kMaxSensors + 1] sensor pixel offsets within the event
+  uint32_t* cnt;         // [kMaxSensors + 1] clusters per sensor, then canonical bases
+  uint32_t* misc;        // [32]
+  uint32_t* scan;        // [32]
+  uint8_t* list;         // [kSizeClasses * kMaxSensors] sensor ids per size class
+  unsigned char* warps;  // cluster_warps_bytes(NT / 32)
+};
+
+// Clusters event e with the whole CTA (NT threads).  On success returns true,
+// with H the event's hit count and status its status bits; cnt[s] is then
+// the canonical id of sensor s's first hit (cnt[ns] = H), also written to
+// the event's canonical bases in global memory.  On failure (bad offsets, a
+// sensor beyond kWarpStage pixels, more than 65535 hits) writes the event's
+// record and returns false.
 template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
-                                                     WorkView wk) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const ClusterLayout L = cluster_layout(NT);
-  uint32_t* s_soff = (uint32_t*)(smem + L.soff);
-  uint32_t* s_cnt = (uint32_t*)(smem + L.ccnt);
-  uint32_t* s_misc = (uint32_t*)(smem + L.misc);
-  uint32_t* s_scan = (uint32_t*)(smem + L.scan);
-  uint8_t* s_list = (uint8_t*)(smem + L.lists);
+__device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsView& ev, const WorkView& wk,
+                              uint32_t e, const ClusterSmem& S, uint32_t& H_out, uint32_t& status_out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  unsigned char* slice = smem + L.warps + warp * kWarpSlice;
+  const int ns = geo->n_sensors, ncols = geo->n_cols, nrows = geo->n_rows;
+  unsigned char* slice = S.warps + (warp == 0 ? 0u : kBigSlice + (uint32_t)(warp - 1) * kSmallSlice);
   unsigned long long* acc = (unsigned long long*)slice;
   uint32_t* w_pk = (uint32_t*)(slice + kAccBytes);
-  uint16_t* w_par = (uint16_t*)(slice + kAccBytes + 4 * kWarpStage);
-  const int ns = geo->n_sensors, ncols = geo->n_cols, nrows = geo->n_rows;
+  uint16_t* w_par = (uint16_t*)(slice + kAccBytes + 4 * kWarpStage);  // warp 0 only
+  uint32_t* s_soff = S.soff;
+  uint32_t* s_cnt = S.cnt;
+  uint32_t* s_misc = S.misc;
 
-  for (uint32_t e = blockIdx.x; e < ev.n_events; e += gridDim.x) {
-    __syncthreads();
-    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
-    const uint32_t gbase = so[0];
-    bool badoff = false;
-    for (int s = tid; s <= ns; s += NT) {
-      const uint32_t v = so[s];
-      s_soff[s] = v - gbase;
-      if (s < ns && so[s + 1] < v) badoff = true;
+  __syncthreads();
+  const uint32_t* so = ev.sensor_off + (size_t)e * ns;
+  const uint32_t gbase = so[0];
+  bool badoff = false;
+  for (int s = tid; s <= ns; s += NT) {
+    const uint32_t v = so[s];
+    s_soff[s] = v - gbase;
+    if (s < ns && so[s + 1] < v) badoff = true;
+  }
+  if (tid < 32) s_misc[tid] = 0;
+  if (__syncthreads_or(badoff || (uint64_t)so[ns] > wk.cap_pixels)) {
+    if (tid == 0) {
+      wk.rec[e] = EventRec{0, 0, 0, VELO_EV_BAD_OFFSETS, 0, 0, gbase, 0};
+      atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
     }
-    if (tid < 32) s_misc[tid] = 0;
-    if (__syncthreads_or(badoff || (uint64_t)so[ns] > wk.cap_pixels)) {
-      if (tid == 0) {
-        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_BAD_OFFSETS, 0, 0, gbase, 0};
-        atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+    return false;
+  }
+  const uint16_t* col = ev.col + gbase;
+  const uint16_t* row = ev.row + gbase;
+  const HitOut out{wk.prov + gbase, wk.prov_key ? wk.prov_key + gbase : nullptr};
+  bool bad = false;
+  // sensors by size class
+  for (int s = tid; s < ns; s += NT) {
+    const uint32_t n = s_soff[s + 1] - s_soff[s];
+    const int c = n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : n <= 64 ? 3 : n <= kMidStage ? 4 : n <= kWarpStage ? 5 : 6;
+    const uint32_t p = atomicAdd(&s_misc[CM_CLASS + c], 1u);
+    S.list[c * kMaxSensors + p] = (uint8_t)s;
+  }
+  __syncthreads();
+  const bool big = s_misc[CM_CLASS + 6] != 0;
+  if (!big) {
+    // the largest sensors, one at a time on warp 0 (its slice stages them)
+    if (warp == 0) {
+      for (uint32_t j = 0; j < s_misc[CM_CLASS + 5]; ++j) {
+        const uint32_t s = S.list[5 * kMaxSensors + j];
+        const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
+        const uint32_t nroot = cluster_sensor_smem(col, row, a, n, ncols, nrows, sensor_geo(geo, (int)s), out, w_pk,
+                                                   w_par, bad);
+        if (lane == 0) s_cnt[s] = nroot;
       }
-      continue;
     }
-    const uint16_t* col = ev.col + gbase;
-    const uint16_t* row = ev.row + gbase;
-    const HitOut out{wk.prov + gbase, wk.prov_key ? wk.prov_key + gbase : nullptr};
-    bool bad = false, big = false;
-    // sensors by size class
-    for (int s = tid; s < ns; s += NT) {
-      const uint32_t n = s_soff[s + 1] - s_soff[s];
-      const int c = n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : n <= 64 ? 3 : n <= kWarpStage ? 4 : 5;
-      const uint32_t p = atomicAdd(&s_misc[CM_CLASS + c], 1u);
-      s_list[c * kMaxSensors + p] = (uint8_t)s;
-    }
-    __syncthreads();
     // work items, largest sensors first: one sensor each of classes 4, 3, 2,
-    // two of class 1, four of class 0 (class 5 is beyond the staging capacity)
+    // two of class 1, four of class 0
     const uint32_t n0 = s_misc[CM_CLASS + 0], n1 = s_misc[CM_CLASS + 1], n2 = s_misc[CM_CLASS + 2];
     const uint32_t n3 = s_misc[CM_CLASS + 3], n4 = s_misc[CM_CLASS + 4];
-    big = s_misc[CM_CLASS + 5] != 0;
     const uint32_t e4 = n4, e3 = e4 + n3, e2 = e3 + n2, e1 = e2 + (n1 + 1) / 2, e0 = e1 + (n0 + 3) / 4;
-    while (!big) {
+    while (true) {
       uint32_t it = 0;
       if (lane == 0) it = atomicAdd(&s_misc[CM_NEXT], 1u);
       it = __shfl_sync(kFull, it, 0);
       if (it >= e0) break;
       if (it < e3) {
-        const uint32_t s = s_list[(it < e4 ? 4 : 3) * kMaxSensors + (it < e4 ? it : it - e4)];
+        const uint32_t s = S.list[(it < e4 ? 4 : 3) * kMaxSensors + (it < e4 ? it : it - e4)];
         const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
         const SensorGeo g = sensor_geo(geo, (int)s);
         uint32_t nroot;
@@ -575,41 +617,87 @@ __global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometr
           nroot = cluster_sensor_reg<2>(col, row, a, n, ncols, nrows, g, out, acc, bad);
         else if (n <= 64) nroot = cluster_sensor_mid<2>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
         else if (n <= 128) nroot = cluster_sensor_mid<4>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
-        else if (n <= 256) nroot = cluster_sensor_mid<8>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
-        else nroot = cluster_sensor_smem(col, row, a, n, ncols, nrows, g, out, w_pk, w_par, bad);
+        else nroot = cluster_sensor_mid<8>(col, row, a, n, ncols, nrows, g, out, (unsigned char*)w_pk, bad);
         if (lane == 0) s_cnt[s] = nroot;
       } else if (it < e2) {
-        cluster_segments<32>(geo, col, row, s_soff, s_list[2 * kMaxSensors + (it - e3)], ns, out, acc, s_cnt, bad);
+        cluster_segments<32>(geo, col, row, s_soff, S.list[2 * kMaxSensors + (it - e3)], ns, out, acc, s_cnt, bad);
       } else if (it < e1) {
         const uint32_t j = 2 * (it - e2) + (uint32_t)(lane / 16);
-        cluster_segments<16>(geo, col, row, s_soff, j < n1 ? s_list[1 * kMaxSensors + j] : 0xFFFFu, ns, out, acc,
+        cluster_segments<16>(geo, col, row, s_soff, j < n1 ? S.list[1 * kMaxSensors + j] : 0xFFFFu, ns, out, acc,
                              s_cnt, bad);
       } else {
         const uint32_t j = 4 * (it - e1) + (uint32_t)(lane / 8);
-        cluster_segments<8>(geo, col, row, s_soff, j < n0 ? s_list[j] : 0xFFFFu, ns, out, acc, s_cnt, bad);
+        cluster_segments<8>(geo, col, row, s_soff, j < n0 ? S.list[j] : 0xFFFFu, ns, out, acc, s_cnt, bad);
       }
     }
-    if (__any_sync(kFull, bad) && lane == 0) atomicOr(&s_misc[CM_STATUS], VELO_EV_BAD_PIXEL);
-    if (__syncthreads_or(big)) {  // a sensor beyond the warp's staging capacity
-      if (tid == 0) {
-        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_OVERFLOW | s_misc[CM_STATUS], 0, 0, gbase, 0};
-        atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
-      }
-      continue;
-    }
-    const uint32_t H = block_exscan(s_cnt, (uint32_t)ns, s_scan);
-    uint16_t* cb = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
-    if (H <= 0xFFFFu)
-      for (int s = tid; s <= ns; s += NT) cb[s] = (uint16_t)(s < ns ? s_cnt[s] : H);
+  }
+  if (__any_sync(kFull, bad) && lane == 0) atomicOr(&s_misc[CM_STATUS], VELO_EV_BAD_PIXEL);
+  if (__syncthreads_or(big)) {  // a sensor beyond the staging capacity
     if (tid == 0) {
-      uint32_t st = s_misc[CM_STATUS];
-      if (st & VELO_EV_BAD_PIXEL) atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+      wk.rec[e] = EventRec{0, 0, 0, VELO_EV_OVERFLOW | s_misc[CM_STATUS], 0, 0, gbase, 0};
+      atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+    }
+    return false;
+  }
+  const uint32_t H = block_exscan(s_cnt, (uint32_t)ns, S.scan);
+  s_cnt[ns] = H;
+  uint32_t st = s_misc[CM_STATUS];
+  __syncthreads();  // status read by everyone before the next event clears it
+  if (tid == 0 && (st & VELO_EV_BAD_PIXEL)) atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+  if (H > 0xFFFFu) {
+    if (tid == 0) {
+      wk.rec[e] = EventRec{0, 0, 0, st | VELO_EV_OVERFLOW, 0, 0, gbase, 0};
+      atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+    }
+    return false;
+  }
+  uint16_t* cb = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
+  for (int s = tid; s <= ns; s += NT) cb[s] = (uint16_t)s_cnt[s];
+  H_out = H;
+  status_out = st;
+  return true;
+}
+
+constexpr int kClusterThreads = 256;
+
+struct ClusterLayout {
+  uint32_t soff, ccnt, misc, scan, lists, warps, total;
+};
+
+__host__ __device__ inline uint32_t c_align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+__host__ __device__ inline ClusterLayout cluster_layout(int n_threads) {
+  ClusterLayout L;
+  uint32_t o = 0;
+  L.soff = o; o = c_align16(o + 4 * (kMaxSensors + 1));
+  L.ccnt = o; o = c_align16(o + 4 * (kMaxSensors + 1));
+  L.misc = o; o = c_align16(o + 4 * 32);
+  L.scan = o; o = c_align16(o + 4 * 32);
+  L.lists = o; o = c_align16(o + kSizeClasses * kMaxSensors);  // u8 sensor ids per size class
+  L.warps = o; o = c_align16(o + cluster_warps_bytes(n_threads / 32));
+  L.total = o;
+  return L;
+}
+
+uint32_t cluster_smem_bytes(int n_threads) { return cluster_layout(n_threads).total; }
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
+                                                     WorkView wk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ClusterLayout L = cluster_layout(NT);
+  const ClusterSmem S{(uint32_t*)(smem + L.soff), (uint32_t*)(smem + L.ccnt), (uint32_t*)(smem + L.misc),
+                      (uint32_t*)(smem + L.scan), (uint8_t*)(smem + L.lists), smem + L.warps};
+  for (uint32_t e = blockIdx.x; e < ev.n_events; e += gridDim.x) {
+    uint32_t H = 0, st = 0;
+    if (!cluster_event<NT>(geo, ev, wk, e, S, H, st)) continue;
+    if (threadIdx.x == 0) {
+      const uint32_t gbase = ev.sensor_off[(size_t)e * geo->n_sensors];
       int cls = 0;
       while (cls < wk.n_classes && H > wk.class_maxh[cls]) ++cls;
-      if (H > 0xFFFFu || cls >= wk.n_classes) {
-        st |= VELO_EV_OVERFLOW;
+      if (cls >= wk.n_classes) {
         atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
-        wk.rec[e] = EventRec{0, 0, 0, st, 0, 0, gbase, 0};
+        wk.rec[e] = EventRec{0, 0, 0, st | VELO_EV_OVERFLOW, 0, 0, gbase, 0};
       } else {
         wk.rec[e] = EventRec{0, 0, H, st, 0, 0, gbase, 0};
         const uint32_t pos = atomicAdd(&wk.cnt->queue_len[cls], 1u);

@@ -196,10 +196,9 @@ __device__ __forceinline__ Slot slot_of(unsigned char* slots, int m) {
 }
 
 template <int GA, int GB>
-__global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kernel(const DevGeometry* __restrict__ geo,
-                                                                     DevParams par, EventsView ev, WorkView wk,
-                                                                     int cls, int qi) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo, const DevParams& par,
+                                             const EventsView& ev, const WorkView& wk, int cls, int qi, uint32_t e,
+                                             uint32_t H, uint32_t gbase, uint32_t status, unsigned char* smem) {
   constexpr int NT = kRingThreads, NW = NT / 32;
   const RingLayout L = ring_layout();
   float* s_z = (float*)(smem + L.z);
@@ -231,7 +230,382 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
   uint16_t* mpc = mpb + kRingMaxT;
   uint8_t* mn = R.n_hits + (size_t)blockIdx.x * kRingMaxT;
   float* mseed = R.seed + (size_t)blockIdx.x * kRingMaxT;
+  const uint32_t* so = ev.sensor_off + (size_t)e * ns;
 
+  // ---- 1. the last three modules into the ring, the next one staged -------
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t mx = 0;
+    for (int m = lane; m < nm; m += 32) mx = max(mx, (uint32_t)s_cb[kSPM * (m + 1)] - s_cb[kSPM * m]);
+    mx = __reduce_max_sync(kFull, mx);
+    if (lane == 0) s_misc[R_MAXMOD] = mx;
+  }
+  if (wk.cl_x) {  // canonical cluster list (verification output)
+    for (int s = warp; s < ns; s += NW) {
+      const uint32_t c0 = s_cb[s], nc = (uint32_t)s_cb[s + 1] - c0, a = __ldg(&so[s]);
+      for (uint32_t j = lane; j < nc; j += 32) {
+        const float2 v = wk.prov[a + j];
+        wk.cl_x[gbase + c0 + j] = v.x;
+        wk.cl_y[gbase + c0 + j] = v.y;
+        wk.cl_key[gbase + c0 + j] = ((uint32_t)s << 16) | wk.prov_key[a + j];
+      }
+    }
+  }
+  __syncthreads();
+  if (s_misc[R_MAXMOD] > kRingModHits) {
+    if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
+    return;
+  }
+  if (nm >= 4) stage_module(nm - 4, s_cb, so, wk.prov, stage);
+  if (warp < 3 && nm - 1 - warp >= 0) {
+    const int m = nm - 1 - warp;
+    const uint32_t c0 = s_cb[kSPM * m];
+    bin_module(m, s_cb, slots, s_wbin + kNB * warp,
+               [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
+  }
+  cp_async_wait_all();
+  __syncthreads();
+
+  // ---- 2. search by triplet over the module window ------------------------
+  int cur = 0;
+  bool overflow = false;
+  for (int i = nm - 3; i >= 0; --i) {
+    const float zi = s_z[i];
+    const Slot Si = slot_of(slots, i), Sb = slot_of(slots, i + 1), Sa = slot_of(slots, i + 2);
+    bool ovf = false;
+    // phase A: every active track is extended into module i by its best
+    // hit (GA lanes per track).  Meanwhile warp NW - 2 makes the b and c
+    // hits of the last round's seeds used (modules i + 2 and i + 1) and
+    // lists the unused middle hits of module i + 1, and warp NW - 1 bins
+    // module i - 1 into the free slot.
+    const uint32_t nact = s_misc[R_NACT + cur];
+    const ActList& A = act[cur];
+    const ActList& N = act[cur ^ 1];
+    for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
+      const uint32_t j = j0 + lane / GA;
+      const int la = lane % GA;
+      const bool valid = j < nact;
+      float xl = 0.0f, yl = 0.0f, zl = 0.0f, tx = 0.0f, ty = 0.0f;
+      uint32_t t = 0, n = 0, sk = 0;
+      unsigned long long best = ~0ull;
+      if (valid) {
+        xl = A.x[j];
+        yl = A.y[j];
+        zl = A.z[j];
+        tx = A.tx[j];
+        ty = A.ty[j];
+        t = A.t[j];
+        n = A.n[j];
+        sk = A.skip[j];
+        const float dzi = fsub(zi, zl);
+        const float xp = fadd(xl, fmul(tx, dzi));
+        const float yp = fadd(yl, fmul(ty, dzi));
+        const Cand cw = window_cands(Si.bins, 0, pseudo_angle(xl, yl), win);
+        for (uint32_t k = la; k < cw.n(); k += GA) {
+          const uint32_t p = cw.at(k);
+          const float2 v = Si.pos[p];
+          if (!phi_ok(xl, yl, v.x, v.y, tol)) continue;
+          const float dx = fsub(v.x, xp), dy = fsub(v.y, yp);
+          const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
+          if (!(s2 < par.max_scatter_fwd)) continue;
+          best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)Si.pid[p] << 16) | p);
+        }
+      }
+#pragma unroll
+      for (int off = 1; off < GA; off <<= 1) best = min(best, __shfl_xor_sync(kFull, best, off));
+      bool keep = false;
+      if (valid && la == 0) {
+        if (best != ~0ull) {
+          const uint32_t p = (uint32_t)(best & 0xFFFFu);
+          const float2 v = Si.pos[p];
+          const float dzq = fsub(zl, zi);
+          if (n >= kRingTrackHits) {
+            ovf = true;
+          } else {
+            trk[(size_t)t * kRingTrackHits + n] = ((uint32_t)i << 16) | (uint32_t)((best >> 16) & 0xFFFFu);
+            mn[t] = (uint8_t)(n + 1);
+            set_bit(Si.used, p);
+            tx = fdiv(fsub(xl, v.x), dzq);
+            ty = fdiv(fsub(yl, v.y), dzq);
+            xl = v.x;
+            yl = v.y;
+            zl = zi;
+            n = n + 1;
+            sk = 0;
+            keep = true;
+          }
+        } else {
+          sk = min(sk + 1u, 255u);
+          keep = sk <= par.max_skipped;
+        }
+      }
+      const int o = list_slot(keep, &s_misc[R_NACT + (cur ^ 1)], kRingMaxAct);
+      if (keep && o < 0) ovf = true;
+      if (o >= 0) {
+        N.x[o] = xl;
+        N.y[o] = yl;
+        N.z[o] = zl;
+        N.tx[o] = tx;
+        N.ty[o] = ty;
+        N.t[o] = (uint16_t)t;
+        N.n[o] = (uint8_t)n;
+        N.skip[o] = (uint8_t)sk;
+      }
+    }
+    if (warp == NW - 2) {
+      if (lane < (int)(2 * kRingModHits / 32)) {
+        const Slot& S = lane < (int)(kRingModHits / 32) ? Sa : Sb;
+        const int w = lane % (kRingModHits / 32);
+        S.used[w] |= S.pend[w];
+        S.pend[w] = 0;
+      }
+      __syncwarp();
+      const uint32_t nb = (uint32_t)s_cb[kSPM * (i + 2)] - s_cb[kSPM * (i + 1)];
+      uint32_t cnt = 0;
+      for (uint32_t q0 = 0; q0 < nb; q0 += 32) {
+        const uint32_t qb = q0 + lane;
+        const bool un = qb < nb && !bit(Sb.used, qb);
+        const uint32_t m = __ballot_sync(kFull, un);
+        if (un) blist[cnt + __popc(m & ((1u << lane) - 1u))] = (uint8_t)qb;
+        cnt += __popc(m);
+      }
+      if (lane == 0) s_misc[R_NB] = cnt;
+    }
+    if (warp == NW - 1 && i >= 1) bin_module(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
+    if (__syncthreads_or(ovf)) { overflow = true; break; }
+    if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
+    if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage);  // binned in the next round
+    // phase B: seeds with the middle hit b in module i + 1
+    {
+      const float za = s_z[i + 2], zb = s_z[i + 1];
+      const float dzab = fsub(za, zb), dzc = fsub(zi, zb), dzbc = fsub(zb, zi);
+      constexpr int NG = NT / GB;
+      const int g = tid / GB, gl = tid % GB;
+      const uint32_t nbl = s_misc[R_NB];
+      for (uint32_t b0 = 0; b0 < nbl; b0 += NG) {
+        const bool has = b0 + g < nbl;
+        const uint32_t qb = has ? blist[b0 + g] : 0u;
+        unsigned long long best = ~0ull;
+        uint32_t bpos = 0;
+        float2 vb = make_float2(0.0f, 0.0f);
+        if (has) {
+          vb = Sb.pos[qb];
+          const float pab = pseudo_angle(vb.x, vb.y);
+          const Cand ca = window_cands(Sa.bins, 0, pab, win);
+          const Cand cc = window_cands(Si.bins, 0, pab, win);
+          for (uint32_t k = gl; k < ca.n(); k += GB) {
+            const uint32_t qa = ca.at(k);
+            if (bit(Sa.used, qa)) continue;
+            const float2 va = Sa.pos[qa];
+            if (!phi_ok(va.x, va.y, vb.x, vb.y, tol)) continue;
+            const float txs = fdiv(fsub(va.x, vb.x), dzab);
+            const float tys = fdiv(fsub(va.y, vb.y), dzab);
+            if (fabsf(txs) > par.max_slope || fabsf(tys) > par.max_slope) continue;
+            const float xp = fadd(vb.x, fmul(txs, dzc));
+            const float yp = fadd(vb.y, fmul(tys, dzc));
+            const unsigned long long ida = (unsigned long long)Sa.pid[qa] << 16;
+            for (uint32_t kc = 0; kc < cc.n(); ++kc) {
+              const uint32_t qc = cc.at(kc);
+              if (bit(Si.used, qc)) continue;
+              const float2 vc = Si.pos[qc];
+              if (!phi_ok(vb.x, vb.y, vc.x, vc.y, tol)) continue;
+              const float dx = fsub(vc.x, xp), dy = fsub(vc.y, yp);
+              const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
+              if (!(s2 < par.max_scatter_seed)) continue;
+              const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | Si.pid[qc];
+              if (key < best) {
+                best = key;
+                bpos = qc;
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int off = 1; off < GB; off <<= 1) {
+          const unsigned long long ob = __shfl_xor_sync(kFull, best, off);
+          const uint32_t op = __shfl_xor_sync(kFull, bpos, off);
+          if (ob < best) {
+            best = ob;
+            bpos = op;
+          }
+        }
+        bool seeded = false;
+        uint32_t t = 0;
+        float2 vc = make_float2(0.0f, 0.0f);
+        if (has && gl == 0 && best != ~0ull) {
+          t = atomicAdd(&s_misc[R_NTR], 1u);
+          if (t >= kRingMaxT) {
+            ovf = true;
+          } else {
+            const uint32_t ia = (uint32_t)(best >> 16) & 0xFFFFu, ic = (uint32_t)best & 0xFFFFu;
+            const uint32_t ib = Sb.pid[qb];
+            uint32_t* th = trk + (size_t)t * kRingTrackHits;
+            th[0] = ((uint32_t)(i + 2) << 16) | ia;
+            th[1] = ((uint32_t)(i + 1) << 16) | ib;
+            th[2] = ((uint32_t)i << 16) | ic;
+            mpa[t] = (uint16_t)ia;
+            mpb[t] = (uint16_t)ib;
+            mpc[t] = (uint16_t)ic;
+            mn[t] = 3;
+            mseed[t] = __uint_as_float((uint32_t)(best >> 32));
+            set_bit(Sb.pend, qb);
+            set_bit(Si.pend, bpos);
+            vc = Si.pos[bpos];
+            seeded = true;
+          }
+        }
+        const int o = list_slot(seeded, &s_misc[R_NACT + (cur ^ 1)], kRingMaxAct);
+        if (seeded && o < 0) ovf = true;
+        if (o >= 0) {
+          N.x[o] = vc.x;
+          N.y[o] = vc.y;
+          N.z[o] = zi;
+          N.tx[o] = fdiv(fsub(vb.x, vc.x), dzbc);
+          N.ty[o] = fdiv(fsub(vb.y, vc.y), dzbc);
+          N.t[o] = (uint16_t)t;
+          N.n[o] = 3;
+          N.skip[o] = 0;
+        }
+      }
+    }
+    cp_async_wait_all();  // module i - 2 is staged for the next round
+    if (__syncthreads_or(ovf)) { overflow = true; break; }
+    cur ^= 1;
+  }
+
+  if (overflow) {
+    cp_async_wait_all();
+    __syncthreads();
+    if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
+    return;
+  }
+
+  // ---- 3. plain cuts or classifier, canonical order -----------------------
+  const uint32_t ntr = s_misc[R_NTR];
+  const uint32_t nwords = (H + 31) / 32;
+  // position of canonical id k in the clustering output, and its module
+  auto hit_xy = [&](uint32_t k, int& m) -> float2 {
+    const int s = sensor_of(s_cb, ns, k);
+    m = s / kSPM;
+    return wk.prov[__ldg(&so[s]) + (k - s_cb[s])];
+  };
+  if (!use_mlp) {
+    // plain cuts: >= 4 hits, or 3 hits with a small seed scatter and no hit
+    // shared with another candidate
+    for (uint32_t k = tid; k < nwords; k += NT) {
+      seen1[k] = 0;
+      seen2[k] = 0;
+    }
+    __syncthreads();
+    for (uint32_t t = tid; t < ntr; t += NT) {
+      const uint32_t* th = trk + (size_t)t * kRingTrackHits;
+      const uint32_t n = mn[t];
+      for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t h = th[k] & 0xFFFFu, b = 1u << (h & 31);
+        if (atomicOr(&seen1[h >> 5], b) & b) atomicOr(&seen2[h >> 5], b);
+      }
+    }
+    __syncthreads();
+    for (uint32_t t = tid; t < ntr; t += NT) {
+      const uint32_t ha = mpa[t], hb = mpb[t], hc = mpc[t], n = mn[t];
+      bool keep = n >= 4;
+      if (n == 3 && mseed[t] < par.max_scatter_3hit)
+        keep = !bit(seen2, ha) && !bit(seen2, hb) && !bit(seen2, hc);
+      t_key[t] = keep ? ((ha << 16) | hb) : 0xFFFFFFFFu;
+    }
+  } else {
+    const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
+    const float kms = fit_kms(par);
+    for (uint32_t t = tid; t < ntr; t += NT) {
+      const uint32_t* th = trk + (size_t)t * kRingTrackHits;
+      const uint32_t n = mn[t];
+      float st[12];
+      fit_track(
+          n,
+          [&](uint32_t k, float& x, float& y, int& m) {
+            const float2 v = hit_xy(th[k] & 0xFFFFu, m);
+            x = v.x;
+            y = v.y;
+          },
+          s_z, sig2, kms, st);
+      float f[kMlpIn];
+      mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, (int)(th[0] >> 16), (int)(th[n - 1] >> 16), f);
+      const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
+      mseed[t] = logit;
+      t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)mpa[t] << 16) | mpb[t]) : 0xFFFFFFFFu;
+    }
+  }
+  __syncthreads();
+  uint32_t kept_local = 0;
+  for (uint32_t t = tid; t < ntr; t += NT) {
+    const uint32_t key = t_key[t];
+    if (key == 0xFFFFFFFFu) continue;
+    uint32_t r = 0;
+    for (uint32_t u = 0; u < ntr; ++u) r += t_key[u] < key;
+    t_rank[t] = r;
+    t_hoff[r] = mn[t];
+    kept_local++;
+  }
+  kept_local = __reduce_add_sync(kFull, kept_local);
+  if (lane == 0 && kept_local) atomicAdd(&s_misc[R_KEPT], kept_local);
+  __syncthreads();
+  const uint32_t K = s_misc[R_KEPT];
+  const uint32_t NH = block_exscan(t_hoff, K, s_scan);
+  if (tid == 0) {
+    uint32_t tb = atomicAdd(&wk.cnt->track_cursor, K);
+    uint32_t hb = atomicAdd(&wk.cnt->hit_cursor, NH);
+    uint32_t st = status;
+    uint32_t nk = K, nh = NH;
+    if ((uint64_t)tb + K > wk.cap_tracks || (uint64_t)hb + NH > wk.cap_hits) {
+      st |= VELO_EV_TRUNCATED;
+      atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+      nk = 0;
+      nh = 0;
+      s_misc[R_SKIP] = 1;
+    }
+    if (st & VELO_EV_BAD_PIXEL) atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
+    s_misc[R_TBASE] = tb;
+    s_misc[R_HBASE] = hb;
+    wk.rec[e] = EventRec{nk, nh, H, st, tb, hb, gbase, 0};
+    atomicAdd(&wk.cnt->cls_events[cls], 1u);
+    atomicAdd(&wk.cnt->cls_tracks[cls], nk);
+    atomicAdd(&wk.cnt->cls_hits[cls], nh);
+    atomicAdd(&wk.cnt->cls_clusters[cls], H);
+    atomicAdd(&wk.cnt->cls_pixels[cls], (unsigned long long)(ev.sensor_off[(size_t)(e + 1) * ns] - gbase));
+  }
+  __syncthreads();
+  if (s_misc[R_SKIP]) return;
+  const uint32_t tb = s_misc[R_TBASE], hb = s_misc[R_HBASE];
+
+  // kept tracks to scratch in canonical order: their hits' canonical ids
+  // (the emit kernel fits them from the clustering output)
+  for (uint32_t t = tid; t < ntr; t += NT) {
+    if (t_key[t] == 0xFFFFFFFFu) continue;
+    const uint32_t r = t_rank[t], n = mn[t];
+    const uint32_t* th = trk + (size_t)t * kRingTrackHits;
+    const uint32_t h0 = hb + t_hoff[r];
+    for (uint32_t k = 0; k < n; ++k) wk.tr_hits[h0 + k] = th[k];  // module << 16 | canonical id
+    const size_t o = (size_t)tb + r;
+    wk.tr_logit[o] = use_mlp ? mseed[t] : 0.0f;
+    wk.tr_nhits[o] = (uint16_t)n;
+    wk.tr_hitoff[o] = t_hoff[r];
+  }
+}
+
+// One event per CTA from queue qi (events of up to kRingMaxH hits, clustered
+// by the clustering kernel).
+template <int GA, int GB>
+__global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kernel(const DevGeometry* __restrict__ geo,
+                                                                     DevParams par, EventsView ev, WorkView wk,
+                                                                     int cls, int qi) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int NT = kRingThreads;
+  const RingLayout L = ring_layout();
+  float* s_z = (float*)(smem + L.z);
+  uint16_t* s_cb = (uint16_t*)(smem + L.cb);
+  uint32_t* s_misc = (uint32_t*)(smem + L.misc);
+  const int tid = threadIdx.x;
+  const int ns = geo->n_sensors, nm = geo->n_modules;
   for (int m = tid; m < kMaxModules; m += NT) s_z[m] = m < nm ? geo->module_z[m] : 0.0f;
 
   while (true) {
@@ -248,368 +622,9 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
       if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
       continue;
     }
-    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
-
-    // ---- 1. the last three modules into the ring, the next one staged -------
     const uint16_t* cbg = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
     for (int s = tid; s <= ns; s += NT) s_cb[s] = cbg[s];
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t mx = 0;
-      for (int m = lane; m < nm; m += 32) mx = max(mx, (uint32_t)s_cb[kSPM * (m + 1)] - s_cb[kSPM * m]);
-      mx = __reduce_max_sync(kFull, mx);
-      if (lane == 0) s_misc[R_MAXMOD] = mx;
-    }
-    if (wk.cl_x) {  // canonical cluster list (verification output)
-      for (int s = warp; s < ns; s += NW) {
-        const uint32_t c0 = s_cb[s], nc = (uint32_t)s_cb[s + 1] - c0, a = __ldg(&so[s]);
-        for (uint32_t j = lane; j < nc; j += 32) {
-          const float2 v = wk.prov[a + j];
-          wk.cl_x[gbase + c0 + j] = v.x;
-          wk.cl_y[gbase + c0 + j] = v.y;
-          wk.cl_key[gbase + c0 + j] = ((uint32_t)s << 16) | wk.prov_key[a + j];
-        }
-      }
-    }
-    __syncthreads();
-    if (s_misc[R_MAXMOD] > kRingModHits) {
-      if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
-      continue;
-    }
-    if (nm >= 4) stage_module(nm - 4, s_cb, so, wk.prov, stage);
-    if (warp < 3 && nm - 1 - warp >= 0) {
-      const int m = nm - 1 - warp;
-      const uint32_t c0 = s_cb[kSPM * m];
-      bin_module(m, s_cb, slots, s_wbin + kNB * warp,
-                 [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
-    }
-    cp_async_wait_all();
-    __syncthreads();
-
-    // ---- 2. search by triplet over the module window ------------------------
-    int cur = 0;
-    bool overflow = false;
-    for (int i = nm - 3; i >= 0; --i) {
-      const float zi = s_z[i];
-      const Slot Si = slot_of(slots, i), Sb = slot_of(slots, i + 1), Sa = slot_of(slots, i + 2);
-      bool ovf = false;
-      // phase A: every active track is extended into module i by its best
-      // hit (GA lanes per track).  Meanwhile warp NW - 2 makes the b and c
-      // hits of the last round's seeds used (modules i + 2 and i + 1) and
-      // lists the unused middle hits of module i + 1, and warp NW - 1 bins
-      // module i - 1 into the free slot.
-      const uint32_t nact = s_misc[R_NACT + cur];
-      const ActList& A = act[cur];
-      const ActList& N = act[cur ^ 1];
-      for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
-        const uint32_t j = j0 + lane / GA;
-        const int la = lane % GA;
-        const bool valid = j < nact;
-        float xl = 0.0f, yl = 0.0f, zl = 0.0f, tx = 0.0f, ty = 0.0f;
-        uint32_t t = 0, n = 0, sk = 0;
-        unsigned long long best = ~0ull;
-        if (valid) {
-          xl = A.x[j];
-          yl = A.y[j];
-          zl = A.z[j];
-          tx = A.tx[j];
-          ty = A.ty[j];
-          t = A.t[j];
-          n = A.n[j];
-          sk = A.skip[j];
-          const float dzi = fsub(zi, zl);
-          const float xp = fadd(xl, fmul(tx, dzi));
-          const float yp = fadd(yl, fmul(ty, dzi));
-          const Cand cw = window_cands(Si.bins, 0, pseudo_angle(xl, yl), win);
-          for (uint32_t k = la; k < cw.n(); k += GA) {
-            const uint32_t p = cw.at(k);
-            const float2 v = Si.pos[p];
-            if (!phi_ok(xl, yl, v.x, v.y, tol)) continue;
-            const float dx = fsub(v.x, xp), dy = fsub(v.y, yp);
-            const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-            if (!(s2 < par.max_scatter_fwd)) continue;
-            best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)Si.pid[p] << 16) | p);
-          }
-        }
-#pragma unroll
-        for (int off = 1; off < GA; off <<= 1) best = min(best, __shfl_xor_sync(kFull, best, off));
-        bool keep = false;
-        if (valid && la == 0) {
-          if (best != ~0ull) {
-            const uint32_t p = (uint32_t)(best & 0xFFFFu);
-            const float2 v = Si.pos[p];
-            const float dzq = fsub(zl, zi);
-            if (n >= kRingTrackHits) {
-              ovf = true;
-            } else {
-              trk[(size_t)t * kRingTrackHits + n] = ((uint32_t)i << 16) | (uint32_t)((best >> 16) & 0xFFFFu);
-              mn[t] = (uint8_t)(n + 1);
-              set_bit(Si.used, p);
-              tx = fdiv(fsub(xl, v.x), dzq);
-              ty = fdiv(fsub(yl, v.y), dzq);
-              xl = v.x;
-              yl = v.y;
-              zl = zi;
-              n = n + 1;
-              sk = 0;
-              keep = true;
-            }
-          } else {
-            sk = min(sk + 1u, 255u);
-            keep = sk <= par.max_skipped;
-          }
-        }
-        const int o = list_slot(keep, &s_misc[R_NACT + (cur ^ 1)], kRingMaxAct);
-        if (keep && o < 0) ovf = true;
-        if (o >= 0) {
-          N.x[o] = xl;
-          N.y[o] = yl;
-          N.z[o] = zl;
-          N.tx[o] = tx;
-          N.ty[o] = ty;
-          N.t[o] = (uint16_t)t;
-          N.n[o] = (uint8_t)n;
-          N.skip[o] = (uint8_t)sk;
-        }
-      }
-      if (warp == NW - 2) {
-        if (lane < (int)(2 * kRingModHits / 32)) {
-          const Slot& S = lane < (int)(kRingModHits / 32) ? Sa : Sb;
-          const int w = lane % (kRingModHits / 32);
-          S.used[w] |= S.pend[w];
-          S.pend[w] = 0;
-        }
-        __syncwarp();
-        const uint32_t nb = (uint32_t)s_cb[kSPM * (i + 2)] - s_cb[kSPM * (i + 1)];
-        uint32_t cnt = 0;
-        for (uint32_t q0 = 0; q0 < nb; q0 += 32) {
-          const uint32_t qb = q0 + lane;
-          const bool un = qb < nb && !bit(Sb.used, qb);
-          const uint32_t m = __ballot_sync(kFull, un);
-          if (un) blist[cnt + __popc(m & ((1u << lane) - 1u))] = (uint8_t)qb;
-          cnt += __popc(m);
-        }
-        if (lane == 0) s_misc[R_NB] = cnt;
-      }
-      if (warp == NW - 1 && i >= 1) bin_module(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
-      if (__syncthreads_or(ovf)) { overflow = true; break; }
-      if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
-      if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage);  // binned in the next round
-      // phase B: seeds with the middle hit b in module i + 1
-      {
-        const float za = s_z[i + 2], zb = s_z[i + 1];
-        const float dzab = fsub(za, zb), dzc = fsub(zi, zb), dzbc = fsub(zb, zi);
-        constexpr int NG = NT / GB;
-        const int g = tid / GB, gl = tid % GB;
-        const uint32_t nbl = s_misc[R_NB];
-        for (uint32_t b0 = 0; b0 < nbl; b0 += NG) {
-          const bool has = b0 + g < nbl;
-          const uint32_t qb = has ? blist[b0 + g] : 0u;
-          unsigned long long best = ~0ull;
-          uint32_t bpos = 0;
-          float2 vb = make_float2(0.0f, 0.0f);
-          if (has) {
-            vb = Sb.pos[qb];
-            const float pab = pseudo_angle(vb.x, vb.y);
-            const Cand ca = window_cands(Sa.bins, 0, pab, win);
-            const Cand cc = window_cands(Si.bins, 0, pab, win);
-            for (uint32_t k = gl; k < ca.n(); k += GB) {
-              const uint32_t qa = ca.at(k);
-              if (bit(Sa.used, qa)) continue;
-              const float2 va = Sa.pos[qa];
-              if (!phi_ok(va.x, va.y, vb.x, vb.y, tol)) continue;
-              const float txs = fdiv(fsub(va.x, vb.x), dzab);
-              const float tys = fdiv(fsub(va.y, vb.y), dzab);
-              if (fabsf(txs) > par.max_slope || fabsf(tys) > par.max_slope) continue;
-              const float xp = fadd(vb.x, fmul(txs, dzc));
-              const float yp = fadd(vb.y, fmul(tys, dzc));
-              const unsigned long long ida = (unsigned long long)Sa.pid[qa] << 16;
-              for (uint32_t kc = 0; kc < cc.n(); ++kc) {
-                const uint32_t qc = cc.at(kc);
-                if (bit(Si.used, qc)) continue;
-                const float2 vc = Si.pos[qc];
-                if (!phi_ok(vb.x, vb.y, vc.x, vc.y, tol)) continue;
-                const float dx = fsub(vc.x, xp), dy = fsub(vc.y, yp);
-                const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-                if (!(s2 < par.max_scatter_seed)) continue;
-                const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | Si.pid[qc];
-                if (key < best) {
-                  best = key;
-                  bpos = qc;
-                }
-              }
-            }
-          }
-#pragma unroll
-          for (int off = 1; off < GB; off <<= 1) {
-            const unsigned long long ob = __shfl_xor_sync(kFull, best, off);
-            const uint32_t op = __shfl_xor_sync(kFull, bpos, off);
-            if (ob < best) {
-              best = ob;
-              bpos = op;
-            }
-          }
-          bool seeded = false;
-          uint32_t t = 0;
-          float2 vc = make_float2(0.0f, 0.0f);
-          if (has && gl == 0 && best != ~0ull) {
-            t = atomicAdd(&s_misc[R_NTR], 1u);
-            if (t >= kRingMaxT) {
-              ovf = true;
-            } else {
-              const uint32_t ia = (uint32_t)(best >> 16) & 0xFFFFu, ic = (uint32_t)best & 0xFFFFu;
-              const uint32_t ib = Sb.pid[qb];
-              uint32_t* th = trk + (size_t)t * kRingTrackHits;
-              th[0] = ((uint32_t)(i + 2) << 16) | ia;
-              th[1] = ((uint32_t)(i + 1) << 16) | ib;
-              th[2] = ((uint32_t)i << 16) | ic;
-              mpa[t] = (uint16_t)ia;
-              mpb[t] = (uint16_t)ib;
-              mpc[t] = (uint16_t)ic;
-              mn[t] = 3;
-              mseed[t] = __uint_as_float((uint32_t)(best >> 32));
-              set_bit(Sb.pend, qb);
-              set_bit(Si.pend, bpos);
-              vc = Si.pos[bpos];
-              seeded = true;
-            }
-          }
-          const int o = list_slot(seeded, &s_misc[R_NACT + (cur ^ 1)], kRingMaxAct);
-          if (seeded && o < 0) ovf = true;
-          if (o >= 0) {
-            N.x[o] = vc.x;
-            N.y[o] = vc.y;
-            N.z[o] = zi;
-            N.tx[o] = fdiv(fsub(vb.x, vc.x), dzbc);
-            N.ty[o] = fdiv(fsub(vb.y, vc.y), dzbc);
-            N.t[o] = (uint16_t)t;
-            N.n[o] = 3;
-            N.skip[o] = 0;
-          }
-        }
-      }
-      cp_async_wait_all();  // module i - 2 is staged for the next round
-      if (__syncthreads_or(ovf)) { overflow = true; break; }
-      cur ^= 1;
-    }
-
-    if (overflow) {
-      cp_async_wait_all();
-      __syncthreads();
-      if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
-      continue;
-    }
-
-    // ---- 3. plain cuts or classifier, canonical order -----------------------
-    const uint32_t ntr = s_misc[R_NTR];
-    const uint32_t nwords = (H + 31) / 32;
-    // position of canonical id k in the clustering output, and its module
-    auto hit_xy = [&](uint32_t k, int& m) -> float2 {
-      const int s = sensor_of(s_cb, ns, k);
-      m = s / kSPM;
-      return wk.prov[__ldg(&so[s]) + (k - s_cb[s])];
-    };
-    if (!use_mlp) {
-      // plain cuts: >= 4 hits, or 3 hits with a small seed scatter and no hit
-      // shared with another candidate
-      for (uint32_t k = tid; k < nwords; k += NT) {
-        seen1[k] = 0;
-        seen2[k] = 0;
-      }
-      __syncthreads();
-      for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint32_t* th = trk + (size_t)t * kRingTrackHits;
-        const uint32_t n = mn[t];
-        for (uint32_t k = 0; k < n; ++k) {
-          const uint32_t h = th[k] & 0xFFFFu, b = 1u << (h & 31);
-          if (atomicOr(&seen1[h >> 5], b) & b) atomicOr(&seen2[h >> 5], b);
-        }
-      }
-      __syncthreads();
-      for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint32_t ha = mpa[t], hb = mpb[t], hc = mpc[t], n = mn[t];
-        bool keep = n >= 4;
-        if (n == 3 && mseed[t] < par.max_scatter_3hit)
-          keep = !bit(seen2, ha) && !bit(seen2, hb) && !bit(seen2, hc);
-        t_key[t] = keep ? ((ha << 16) | hb) : 0xFFFFFFFFu;
-      }
-    } else {
-      const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
-      const float kms = fit_kms(par);
-      for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint32_t* th = trk + (size_t)t * kRingTrackHits;
-        const uint32_t n = mn[t];
-        float st[12];
-        fit_track(
-            n,
-            [&](uint32_t k, float& x, float& y, int& m) {
-              const float2 v = hit_xy(th[k] & 0xFFFFu, m);
-              x = v.x;
-              y = v.y;
-            },
-            s_z, sig2, kms, st);
-        float f[kMlpIn];
-        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, (int)(th[0] >> 16), (int)(th[n - 1] >> 16), f);
-        const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
-        mseed[t] = logit;
-        t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)mpa[t] << 16) | mpb[t]) : 0xFFFFFFFFu;
-      }
-    }
-    __syncthreads();
-    uint32_t kept_local = 0;
-    for (uint32_t t = tid; t < ntr; t += NT) {
-      const uint32_t key = t_key[t];
-      if (key == 0xFFFFFFFFu) continue;
-      uint32_t r = 0;
-      for (uint32_t u = 0; u < ntr; ++u) r += t_key[u] < key;
-      t_rank[t] = r;
-      t_hoff[r] = mn[t];
-      kept_local++;
-    }
-    kept_local = __reduce_add_sync(kFull, kept_local);
-    if (lane == 0 && kept_local) atomicAdd(&s_misc[R_KEPT], kept_local);
-    __syncthreads();
-    const uint32_t K = s_misc[R_KEPT];
-    const uint32_t NH = block_exscan(t_hoff, K, s_scan);
-    if (tid == 0) {
-      uint32_t tb = atomicAdd(&wk.cnt->track_cursor, K);
-      uint32_t hb = atomicAdd(&wk.cnt->hit_cursor, NH);
-      uint32_t st = status;
-      uint32_t nk = K, nh = NH;
-      if ((uint64_t)tb + K > wk.cap_tracks || (uint64_t)hb + NH > wk.cap_hits) {
-        st |= VELO_EV_TRUNCATED;
-        atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
-        nk = 0;
-        nh = 0;
-        s_misc[R_SKIP] = 1;
-      }
-      if (st & VELO_EV_BAD_PIXEL) atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
-      s_misc[R_TBASE] = tb;
-      s_misc[R_HBASE] = hb;
-      wk.rec[e] = EventRec{nk, nh, H, st, tb, hb, gbase, 0};
-      atomicAdd(&wk.cnt->cls_events[cls], 1u);
-      atomicAdd(&wk.cnt->cls_tracks[cls], nk);
-      atomicAdd(&wk.cnt->cls_hits[cls], nh);
-      atomicAdd(&wk.cnt->cls_clusters[cls], H);
-      atomicAdd(&wk.cnt->cls_pixels[cls], (unsigned long long)(ev.sensor_off[(size_t)(e + 1) * ns] - gbase));
-    }
-    __syncthreads();
-    if (s_misc[R_SKIP]) continue;
-    const uint32_t tb = s_misc[R_TBASE], hb = s_misc[R_HBASE];
-
-    // kept tracks to scratch in canonical order: their hits' canonical ids
-    // (the emit kernel fits them from the clustering output)
-    for (uint32_t t = tid; t < ntr; t += NT) {
-      if (t_key[t] == 0xFFFFFFFFu) continue;
-      const uint32_t r = t_rank[t], n = mn[t];
-      const uint32_t* th = trk + (size_t)t * kRingTrackHits;
-      const uint32_t h0 = hb + t_hoff[r];
-      for (uint32_t k = 0; k < n; ++k) wk.tr_hits[h0 + k] = th[k];  // module << 16 | canonical id
-      const size_t o = (size_t)tb + r;
-      wk.tr_logit[o] = use_mlp ? mseed[t] : 0.0f;
-      wk.tr_nhits[o] = (uint16_t)n;
-      wk.tr_hitoff[o] = t_hoff[r];
-    }
+    window_event<GA, GB>(geo, par, ev, wk, cls, qi, e, H, gbase, status, smem);
   }
 }
 
