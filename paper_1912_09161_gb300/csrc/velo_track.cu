@@ -150,15 +150,17 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
           for (int u = 0; u < 4; ++u) {
             ok[u] = kc + u < nc;
             pcs[u] = ok[u] ? cc.at(kc + u) : pb;
-            ok[u] = ok[u] && !bit(used, pcs[u]);
             vcs[u] = pos[pcs[u]];
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            if (!ok[u] || !phi_ok(vb.x, vb.y, vcs[u].x, vcs[u].y, tol)) continue;
+            if (!ok[u]) continue;
+            // scatter first (the most selective test; one that cannot beat
+            // the lane's best is dropped), then used and the phi window
             const float dx = fsub(vcs[u].x, xp), dy = fsub(vcs[u].y, yp);
             const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-            if (!(s2 < par.max_scatter_seed)) continue;
+            if (!(s2 < par.max_scatter_seed) || __float_as_uint(s2) > (uint32_t)(best >> 32)) continue;
+            if (bit(used, pcs[u]) || !phi_ok(vb.x, vb.y, vcs[u].x, vcs[u].y, tol)) continue;
             const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | pid[pcs[u]];
             if (key < best) {
               best = key;
@@ -371,10 +373,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              if (!ok[u] || !phi_ok(xl, yl, vs[u].x, vs[u].y, tol)) continue;
+              if (!ok[u]) continue;
               const float dx = fsub(vs[u].x, xp), dy = fsub(vs[u].y, yp);
               const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-              if (!(s2 < par.max_scatter_fwd)) continue;
+              if (!(s2 < par.max_scatter_fwd) || __float_as_uint(s2) > (uint32_t)(best >> 32)) continue;
+              if (!phi_ok(xl, yl, vs[u].x, vs[u].y, tol)) continue;
               best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)pid[ps[u]] << 16) | ps[u]);
             }
           }

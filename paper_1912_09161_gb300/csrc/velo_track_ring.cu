@@ -304,10 +304,12 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         for (uint32_t k = la; k < cw.n(); k += GA) {
           const uint32_t p = cw.at(k);
           const float2 v = Si.pos[p];
-          if (!phi_ok(xl, yl, v.x, v.y, tol)) continue;
+          // scatter first (the most selective test; one that cannot beat
+          // the lane's best is dropped), then the phi window
           const float dx = fsub(v.x, xp), dy = fsub(v.y, yp);
           const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-          if (!(s2 < par.max_scatter_fwd)) continue;
+          if (!(s2 < par.max_scatter_fwd) || __float_as_uint(s2) > (uint32_t)(best >> 32)) continue;
+          if (!phi_ok(xl, yl, v.x, v.y, tol)) continue;
           best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)Si.pid[p] << 16) | p);
         }
       }
@@ -406,12 +408,11 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
             const unsigned long long ida = (unsigned long long)Sa.pid[qa] << 16;
             for (uint32_t kc = 0; kc < cc.n(); ++kc) {
               const uint32_t qc = cc.at(kc);
-              if (bit(Si.used, qc)) continue;
               const float2 vc = Si.pos[qc];
-              if (!phi_ok(vb.x, vb.y, vc.x, vc.y, tol)) continue;
               const float dx = fsub(vc.x, xp), dy = fsub(vc.y, yp);
               const float s2 = fadd(fmul(dx, dx), fmul(dy, dy));
-              if (!(s2 < par.max_scatter_seed)) continue;
+              if (!(s2 < par.max_scatter_seed) || __float_as_uint(s2) > (uint32_t)(best >> 32)) continue;
+              if (bit(Si.used, qc) || !phi_ok(vb.x, vb.y, vc.x, vc.y, tol)) continue;
               const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | Si.pid[qc];
               if (key < best) {
                 best = key;
