@@ -126,9 +126,9 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
     float2 vb = make_float2(0.0f, 0.0f);
     if (has) {
       vb = pos[pb];
-      const float pab = pseudo_angle(vb.x, vb.y);
-      const Cand ca = window_cands(bins, ma, pab, win);
-      const Cand cc = window_cands(bins, i, pab, win);
+      const float pab = pseudo_angle(vb.x, vb.y), wb = phi_halfwidth(vb.x, vb.y, win);
+      const Cand ca = window_cands(bins, ma, pab, wb);
+      const Cand cc = window_cands(bins, i, pab, wb);
       for (uint32_t k = gl; k < ca.n(); k += GB) {
         const uint32_t pa = ca.at(k);
         if (bit(used, pa)) continue;
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
           const float dzi = fsub(zi, zl);
           xp = fadd(xl, fmul(t_tx[t], dzi));
           yp = fadd(yl, fmul(t_ty[t], dzi));
-          const Cand cw = window_cands(s_bins, i, pseudo_angle(xl, yl), win);
+          const Cand cw = window_cands(s_bins, i, pseudo_angle(xl, yl), phi_halfwidth(xl, yl, win));
           // this lane's candidates (every GA-th), four at a time
           const uint32_t nw = cw.n();
           for (uint32_t k0 = la; k0 < nw; k0 += 4 * GA) {

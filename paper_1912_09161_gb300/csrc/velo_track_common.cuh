@@ -22,6 +22,19 @@ __device__ __forceinline__ BinWindow bin_window(float pa, float w) {
   return BinWindow{lo & (kNB - 1), cnt};  // kNB is a power of two
 }
 
+// Half-width, in pseudo-angle units, of a window around the hit (x, y) that
+// holds every hit within w radians of it in phi (w: atan(tol) plus a margin).
+// The pseudo-angle moves by 1 / (1 + |sin 2 phi|) per radian and |sin 2 phi|
+// by at most 2 per radian, so over phi +- w it moves by at most
+// w / (1 + max(0, |sin 2 phi| - 2 w)): half of w near the diagonals.  It only
+// decides which bins are visited; the approximate arithmetic stays far inside
+// the margin of w.
+__device__ __forceinline__ float phi_halfwidth(float x, float y, float w) {
+  const float r2 = x * x + y * y;
+  const float s = r2 > 1e-12f ? fminf(__fdividef(2.0f * fabsf(x * y), r2), 1.0f) : 0.0f;
+  return __fdividef(w, 1.0f + fmaxf(0.0f, s - 2.0f * w));
+}
+
 // Candidate positions of module m in the phi window around pa: one or two
 // contiguous ranges (bins[k] = end position of bin k of the event).
 struct Cand {

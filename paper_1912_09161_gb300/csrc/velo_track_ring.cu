@@ -300,7 +300,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         const float dzi = fsub(zi, zl);
         const float xp = fadd(xl, fmul(tx, dzi));
         const float yp = fadd(yl, fmul(ty, dzi));
-        const Cand cw = window_cands(Si.bins, 0, pseudo_angle(xl, yl), win);
+        const Cand cw = window_cands(Si.bins, 0, pseudo_angle(xl, yl), phi_halfwidth(xl, yl, win));
         for (uint32_t k = la; k < cw.n(); k += GA) {
           const uint32_t p = cw.at(k);
           const float2 v = Si.pos[p];
@@ -392,9 +392,9 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         float2 vb = make_float2(0.0f, 0.0f);
         if (has) {
           vb = Sb.pos[qb];
-          const float pab = pseudo_angle(vb.x, vb.y);
-          const Cand ca = window_cands(Sa.bins, 0, pab, win);
-          const Cand cc = window_cands(Si.bins, 0, pab, win);
+          const float pab = pseudo_angle(vb.x, vb.y), wb = phi_halfwidth(vb.x, vb.y, win);
+          const Cand ca = window_cands(Sa.bins, 0, pab, wb);
+          const Cand cc = window_cands(Si.bins, 0, pab, wb);
           for (uint32_t k = gl; k < ca.n(); k += GB) {
             const uint32_t qa = ca.at(k);
             if (bit(Sa.used, qa)) continue;
