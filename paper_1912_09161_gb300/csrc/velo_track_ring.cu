@@ -45,8 +45,10 @@ constexpr int kRingSlots = 4;
 constexpr uint32_t kSlotPos = 0, kSlotPid = 8 * kRingModHits, kSlotBins = kSlotPid + 2 * kRingModHits;
 constexpr uint32_t kSlotUsed = kSlotBins + 2 * kNB, kSlotPend = kSlotUsed + kRingModHits / 8;
 constexpr uint32_t kSlotBytes = kSlotPend + kRingModHits / 8;
-// active-track records, per list: x, y, z, tx, ty (f32), track id (u16), hits, skips (u8)
-constexpr uint32_t kActBytes = kRingMaxAct * (5 * 4 + 2 + 1 + 1);
+// active-track records, per list: x, y, tx, ty (f32), track id (u16), module
+// of the last hit, hits, skips (u8)
+constexpr uint32_t kActBytes = kRingMaxAct * (4 * 4 + 2 + 1 + 1 + 1);
+static_assert(kActBytes % 16 == 0, "second list aligned");
 static_assert(2 * kActBytes >= 3u * 4u * kRingMaxT, "ranking arrays fit the track lists");
 static_assert(kRingSlots * kSlotBytes >= 2u * (kRingMaxH / 8), "seen bitmaps fit the ring");
 
@@ -64,7 +66,7 @@ __host__ __device__ inline RingLayout ring_layout() {
   L.cb = o; o = ralign16(o + 2 * (kMaxSensors + 1));
   L.misc = o; o = ralign16(o + 4 * 32);
   L.scan = o; o = ralign16(o + 4 * 32);
-  L.wbin = o; o = ralign16(o + 3 * 4 * kNB);             // bin counters of up to three warps
+  L.wbin = o; o = ralign16(o + 4 * kNB);                 // bin counters (the binning warp)
   L.blist = o; o = ralign16(o + kRingModHits);            // unused middle hits of the round
   L.stage = o; o = ralign16(o + 8 * kRingModHits);        // raw hits of the next module
   L.slots = o; o = ralign16(o + kRingSlots * kSlotBytes);
@@ -78,20 +80,20 @@ enum RMisc {
 };
 
 struct ActList {
-  float *x, *y, *z, *tx, *ty;
+  float *x, *y, *tx, *ty;
   uint16_t* t;
-  uint8_t *n, *skip;
+  uint8_t *m, *n, *skip;
 };
 
 __device__ __forceinline__ ActList act_list(unsigned char* base) {
   ActList a;
   a.x = (float*)base;
   a.y = a.x + kRingMaxAct;
-  a.z = a.y + kRingMaxAct;
-  a.tx = a.z + kRingMaxAct;
+  a.tx = a.y + kRingMaxAct;
   a.ty = a.tx + kRingMaxAct;
   a.t = (uint16_t*)(a.ty + kRingMaxAct);
-  a.n = (uint8_t*)(a.t + kRingMaxAct);
+  a.m = (uint8_t*)(a.t + kRingMaxAct);
+  a.n = a.m + kRingMaxAct;
   a.skip = a.n + kRingMaxAct;
   return a;
 }
@@ -260,7 +262,9 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   if (warp < 3 && nm - 1 - warp >= 0) {
     const int m = nm - 1 - warp;
     const uint32_t c0 = s_cb[kSPM * m];
-    bin_module(m, s_cb, slots, s_wbin + kNB * warp,
+    // bin counters: the binning warp's own, and for warps 1 and 2 the active
+    // lists, unused until the first round's seeds
+    bin_module(m, s_cb, slots, warp == 0 ? s_wbin : (uint32_t*)(smem + L.act) + kNB * (warp - 1),
                [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
   }
   cp_async_wait_all();
@@ -286,12 +290,13 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       const int la = lane % GA;
       const bool valid = j < nact;
       float xl = 0.0f, yl = 0.0f, zl = 0.0f, tx = 0.0f, ty = 0.0f;
-      uint32_t t = 0, n = 0, sk = 0;
+      uint32_t t = 0, n = 0, sk = 0, mz = 0;
       unsigned long long best = ~0ull;
       if (valid) {
         xl = A.x[j];
         yl = A.y[j];
-        zl = A.z[j];
+        mz = A.m[j];
+        zl = s_z[mz];
         tx = A.tx[j];
         ty = A.ty[j];
         t = A.t[j];
@@ -332,6 +337,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
             xl = v.x;
             yl = v.y;
             zl = zi;
+            mz = (uint32_t)i;
             n = n + 1;
             sk = 0;
             keep = true;
@@ -346,7 +352,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       if (o >= 0) {
         N.x[o] = xl;
         N.y[o] = yl;
-        N.z[o] = zl;
+        N.m[o] = (uint8_t)mz;
         N.tx[o] = tx;
         N.ty[o] = ty;
         N.t[o] = (uint16_t)t;
@@ -460,7 +466,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         if (o >= 0) {
           N.x[o] = vc.x;
           N.y[o] = vc.y;
-          N.z[o] = zi;
+          N.m[o] = (uint8_t)i;
           N.tx[o] = fdiv(fsub(vb.x, vc.x), dzbc);
           N.ty[o] = fdiv(fsub(vb.y, vc.y), dzbc);
           N.t[o] = (uint16_t)t;
