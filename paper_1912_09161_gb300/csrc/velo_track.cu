@@ -237,7 +237,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
   uint16_t* t_pc = (uint16_t*)(smem + L.t_pc);
   uint8_t* t_n = (uint8_t*)(smem + L.t_n);
   uint8_t* t_skip = (uint8_t*)(smem + L.t_skip);
-  uint16_t* act[2] = {(uint16_t*)(smem + L.act0), (uint16_t*)(smem + L.act1)};
   // this CTA's hit slots: kMaxModules positions per candidate
   uint16_t* trk = wk.trk_hits[cls] + (size_t)blockIdx.x * caps.maxt * kMaxModules;
   uint32_t* t_key = (uint32_t*)t_x;    // after the rounds
@@ -340,8 +339,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
         set_bit(used, t_pc[t]);
       }
       const uint32_t nact = s_misc[M_NACT + cur];
-      const uint16_t* alist = act[cur];
-      uint16_t* nlist = act[cur ^ 1];
+      // pointers formed per round (an array indexed by cur would live in
+      // local memory)
+      const uint16_t* alist = (const uint16_t*)(smem + (cur ? L.act1 : L.act0));
+      uint16_t* nlist = (uint16_t*)(smem + (cur ? L.act0 : L.act1));
       // GA lanes per track split its window and agree on the best hit
       for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
         const uint32_t j = j0 + lane / GA;

@@ -211,7 +211,6 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   uint8_t* blist = (uint8_t*)(smem + L.blist);
   float2* stage = (float2*)(smem + L.stage);
   unsigned char* slots = smem + L.slots;
-  const ActList act[2] = {act_list(smem + L.act), act_list(smem + L.act + kActBytes)};
   uint32_t* t_key = (uint32_t*)(smem + L.act);  // after the rounds
   uint32_t* t_rank = t_key + kRingMaxT;
   uint32_t* t_hoff = t_rank + kRingMaxT;         // indexed by rank
@@ -283,8 +282,10 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     // lists the unused middle hits of module i + 1, and warp NW - 1 bins
     // module i - 1 into the free slot.
     const uint32_t nact = s_misc[R_NACT + cur];
-    const ActList& A = act[cur];
-    const ActList& N = act[cur ^ 1];
+    // this round's active list and the next round's (pointers formed per
+    // round: an array of both indexed by cur would live in local memory)
+    const ActList A = act_list(smem + L.act + (cur ? kActBytes : 0u));
+    const ActList N = act_list(smem + L.act + (cur ? 0u : kActBytes));
     for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
       const uint32_t j = j0 + lane / GA;
       const int la = lane % GA;
