@@ -188,11 +188,30 @@ __device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const u
   for (int r = 0; r < R; ++r) nb[r] = 0;
   for (uint32_t d = 1; d < NE; ++d) {
     bool reach = false;
+    // position e + d (e - d) of every register of this lane is held by lane
+    // (lane + d) mod 32 ((lane - d) mod 32), in the register shifted by the
+    // carry: one shuffle per register and direction
+    const uint32_t sf = (lane + d) & 31u, cf = ((uint32_t)lane + d) >> 5;
+    const int tb = lane - (int)d;
+    const uint32_t sb = (uint32_t)tb & 31u;
+    const int cb = tb >> 5;  // 0 or negative
+    uint32_t xf[R], xb[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      xf[j] = __shfl_sync(kFull, k[j], sf);
+      xb[j] = __shfl_sync(kFull, k[j], sb);
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t e = lane + 32u * r;
-      const uint32_t qf = e + d, qb = e - d;  // qb wraps when e < d
-      const uint32_t kf = warp_fetch<R>(k, qf % NE), kb = warp_fetch<R>(k, qb % NE);
+      const uint32_t qf = e + d, qb = e - d;
+      const int rf = r + (int)cf, rb = r + cb;
+      uint32_t kf = kInv, kb = kInv;
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (rf == j) kf = xf[j];
+        if (rb == j) kb = xb[j];
+      }
       if (!valid[r]) continue;
       if (qf < NE && kf != kInv && kf - k[r] <= 513u) {
         reach = true;
