@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
 
 // Lanes per active track in phase A and per middle hit in phase B.
 constexpr int kRingGroupA = 1;
-constexpr int kRingGroupB = 4;
+constexpr int kRingGroupB = 2;
 
 }  // namespace
 
