@@ -163,7 +163,10 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, c
 cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
                         const WorkView& wk, const velo_output& out, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;
-  int blocks = (int)(n_events < 152u * 16u ? n_events : 152u * 16u);
+  // up to 2048 threads' worth of blocks per SM on a 152-SM part (a grid-stride
+  // loop covers any larger batch)
+  constexpr uint32_t kMaxBlocks = 152u * (2048u / kEmitThreads);
+  const int blocks = (int)(n_events < kMaxBlocks ? n_events : kMaxBlocks);
   emit_kernel<<<blocks, kEmitThreads, 0, st>>>(n_events, geo, par, ev, wk, out);
   return cudaGetLastError();
 }
