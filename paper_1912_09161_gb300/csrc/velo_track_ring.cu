@@ -8,8 +8,8 @@
 // slots (each: the module's hits ordered by phi bin, their canonical ids, the
 // bin ends, a used bitmap and a bitmap of the running round's seed hits), the
 // active tracks (double-buffered records), the list of the round's unused
-// middle hits and the next module's raw hits -- about 24 KB per event, so
-// nine events share an SM.  The hits come straight from the clustering output:
+// middle hits and the next module's raw hits -- about 22 KB per event; nine
+// events share an SM (the register budget sets the nine).  The hits come straight from the clustering output:
 //   - round i copies module i - 2's hits into a staging buffer with cp.async
 //     during its phase B;
 //   - round i - 1 bins them by phi into the free slot during its phase A, on
@@ -17,8 +17,9 @@
 // so every hit is read from global memory once.  After the rounds the kernel
 // applies the plain cuts (or the classifier), ranks the kept candidates
 // canonically and writes their hits (module, canonical id) to scratch for the
-// emit kernel, which fits them.  Candidate hit lists (canonical ids, up
-// to kRingTrackHits) and seed records live in the CTA's global region.
+// emit kernel, which fits them.  Candidate hit lists (module << 16 |
+// canonical id, up to kRingTrackHits) and seed records live in the CTA's
+// global region.
 // Events beyond the window's capacities (a module of more than kRingModHits
 // hits, more than kRingMaxAct active tracks, kRingMaxT candidates, kRingMaxH
 // hits, or a candidate of kRingTrackHits hits) go to the retry queue, which a
