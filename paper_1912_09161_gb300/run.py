@@ -1,7 +1,7 @@
 """Reconstructs a synthetic batch on the GPU a few times and prints the timing.
 
     python -m paper_1912_09161_gb300.run [--config I] [--events N] [--steps K] [--warmup W]
-                                         [--graphs] [--timing] [--schedule THREADS,MASK,CONCURRENT]
+                                         [--graphs] [--timing] [--schedule THREADS,MASK,CONCURRENT] [--mlp]
 
 Batch: the generator's configuration I (0: 100 events, 1: 10,000 nominal,
 2: 50,000 of pileup U[1, 20], 3: 1,300, 4: 5,000), optionally cut to N events.
@@ -9,6 +9,9 @@ Inputs are uploaded once; each step is one velo_reconstruct call on one
 stream.  Prints one line per step (CUDA-event time; with --timing also the
 per-kernel times and the events each tracking class took) and the totals of
 the last.
+With --mlp the ghost classifier keeps the candidates (seeded untrained
+weights: every candidate is fitted and scored whatever the weights, so the
+time is that of the classifier path; the kept tracks are not meaningful).
 Used as the fixed command line of kernel profiles.
 """
 from __future__ import annotations
@@ -26,6 +29,7 @@ def main(argv=None) -> int:
     ap.add_argument("--graphs", action="store_true")
     ap.add_argument("--timing", action="store_true")
     ap.add_argument("--schedule", default="")
+    ap.add_argument("--mlp", action="store_true")
     a = ap.parse_args(argv)
 
     import numpy as np
@@ -36,7 +40,12 @@ def main(argv=None) -> int:
     cfg = velo_synth.config(a.config, **({"n_events": a.events} if a.events else {}))
     ev = velo_synth.generate(cfg)
     geom = velo_synth.geometry()
-    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
+    params = V.Params(use_mlp=1) if a.mlp else V.Params()
+    rec = V.Reconstructor(geom, params, max_events=ev.n_events, max_pixels=ev.n_pixels)
+    if a.mlp:
+        from . import ghost
+        w = (ghost.init_params(7).view(np.uint32) >> 16).astype(np.uint16)  # BF16 by truncation
+        rec.set_mlp(w, np.zeros(ghost.N_IN, np.float32), np.ones(ghost.N_IN, np.float32))
     if a.schedule:
         t, m, c = (int(x, 0) for x in a.schedule.split(","))
         rec.set_schedule(t, m, c)
