@@ -45,6 +45,9 @@ CPU_SECONDS = 10.0          # the CPU baseline repeats the sample for about this
 CPU_MAX_PASSES = 30
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "track_kernel_nominal_10k.md")
+# sources of the tracking kernels, in the order the profile summary hashes them
+TRACK_SOURCES = ("velo_track_ring.cu", "velo_track.cu", "velo_track_common.cuh", "velo_internal.cuh",
+                 "velo_device.cuh", "velo_fit.cuh", "velo_mlp.cuh")
 KERNELS_BASE = 4            # clustering, retry pass of the largest class, scan, emit (+ one per class)
 
 
@@ -360,8 +363,7 @@ def run_ours(args):
     desc = rec.describe()
     peak, peak_kind = _measured_peak_hbm()
     achieved = sum(reco_bytes) / (sum(reco_ms) / 1e3) / 1e9
-    traffic = _profile_traffic([os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", f)
-                                for f in ("velo_track_ring.cu", "velo_track.cu")])
+    traffic = _profile_traffic([os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", f) for f in TRACK_SOURCES])
     tot = out.totals.cpu().numpy().view(np.uint32)
     step_bytes = _step_bytes(ev.n_pixels, ev.n_events, geom.n_sensors, int(tot[0]), int(tot[1]))
     stage = [statistics.mean(x[k] for x in stage_ms) for k in range(4)]

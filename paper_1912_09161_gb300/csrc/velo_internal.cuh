@@ -11,7 +11,7 @@ namespace velo {
 constexpr int kMaxModules = 64;
 constexpr int kSPM = 4;                          // sensors per module
 constexpr int kMaxSensors = kMaxModules * kSPM;  // 256
-constexpr int kNB = 128;                         // phi bins per module (a power of two, multiple of 32)
+constexpr int kNB = 256;                         // phi bins per module (a power of two, multiple of 32)
 constexpr uint32_t kNone16 = 0xFFFFu;
 constexpr int kMaxClasses = 4;                   // shared-memory classes of the tracking kernel
 constexpr int kRetryQueue = kMaxClasses;         // events that ran out of storage in their class

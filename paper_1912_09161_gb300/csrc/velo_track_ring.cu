@@ -8,7 +8,7 @@
 // slots (each: the module's hits ordered by phi bin, their canonical ids, the
 // bin ends, a used bitmap and a bitmap of the running round's seed hits), the
 // active tracks (double-buffered records), the list of the round's unused
-// middle hits and the next module's raw hits -- about 22 KB per event; nine
+// middle hits and the next module's raw hits -- about 23 KB per event; nine
 // events share an SM (the register budget sets the nine).  The hits come straight from the clustering output:
 //   - round i copies module i - 2's hits into a staging buffer with cp.async
 //     during its phase B;
@@ -50,6 +50,7 @@ constexpr uint32_t kSlotBytes = kSlotPend + kRingModHits / 8;
 // of the last hit, hits, skips (u8)
 constexpr uint32_t kActBytes = kRingMaxAct * (4 * 4 + 2 + 1 + 1 + 1);
 static_assert(kActBytes % 16 == 0, "second list aligned");
+static_assert(2u * kActBytes >= 2u * 4u * kNB, "two warps' bin counters fit the active lists");
 static_assert(2 * kActBytes >= 3u * 4u * kRingMaxT, "ranking arrays fit the track lists");
 static_assert(kRingSlots * kSlotBytes >= 2u * (kRingMaxH / 8), "seen bitmaps fit the ring");
 
