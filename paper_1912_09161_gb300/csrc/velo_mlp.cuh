@@ -94,29 +94,55 @@ __device__ __forceinline__ void mlp_features(float x, float y, float tx, float t
   f[9] = (float)((mfirst - mlast + 1) - n);
 }
 
+// The two BF16 values of a 32-bit word of the parameter array (element 2q
+// in the low half, 2q + 1 in the high half).
+__device__ __forceinline__ float bf16_lo(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p & 0xFFFF0000u); }
+
 // Logit of the BF16 network: inputs standardised and rounded to BF16, hidden
 // activations ReLU then BF16, sums in FP32 from the bias over ascending
-// inputs.  w: parameters as BF16 bits; mean / istd: standardisation.
+// inputs.  w: parameters as BF16 bits (4-byte aligned; every row starts at an
+// even index, so weights are read in pairs); mean / istd: standardisation.
+// The first layer is unrolled so that its outputs stay in registers; the
+// second runs four units' chains side by side, each in its own fixed order,
+// and adds their output terms in ascending unit order.
 __device__ __forceinline__ float mlp_logit(const float f[kMlpIn], const uint16_t* w, const float* mean,
                                            const float* istd) {
+  static_assert(kMlpIn % 2 == 0 && kMlpH % 4 == 0 && kOffW1 % 2 == 0 && kOffW2 % 2 == 0, "weight pairs");
+  const uint32_t* wp = (const uint32_t*)w;
   float x[kMlpIn];
 #pragma unroll
   for (int i = 0; i < kMlpIn; ++i) x[i] = bf16_round(fmul(fsub(f[i], mean[i]), istd[i]));
   float h1[kMlpH];
-#pragma unroll 4
+#pragma unroll
   for (int j = 0; j < kMlpH; ++j) {
     float acc = bf16_value(w[kOffB1 + j]);
 #pragma unroll
-    for (int i = 0; i < kMlpIn; ++i) acc = fadd(acc, fmul(bf16_value(w[kOffW1 + j * kMlpIn + i]), x[i]));
+    for (int i = 0; i < kMlpIn; i += 2) {
+      const uint32_t p = wp[(kOffW1 + j * kMlpIn + i) / 2];
+      acc = fadd(acc, fmul(bf16_lo(p), x[i]));
+      acc = fadd(acc, fmul(bf16_hi(p), x[i + 1]));
+    }
     h1[j] = bf16_round(fmaxf(acc, 0.0f));
   }
   float out = bf16_value(w[kOffB3]);
-  for (int j = 0; j < kMlpH; ++j) {
-    float acc = bf16_value(w[kOffB2 + j]);
+#pragma unroll 1
+  for (int j0 = 0; j0 < kMlpH; j0 += 4) {
+    float acc[4];
 #pragma unroll
-    for (int k = 0; k < kMlpH; ++k) acc = fadd(acc, fmul(bf16_value(w[kOffW2 + j * kMlpH + k]), h1[k]));
-    const float h2 = bf16_round(fmaxf(acc, 0.0f));
-    out = fadd(out, fmul(bf16_value(w[kOffW3 + j]), h2));
+    for (int u = 0; u < 4; ++u) acc[u] = bf16_value(w[kOffB2 + j0 + u]);
+#pragma unroll
+    for (int k = 0; k < kMlpH; k += 2) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t p = wp[(kOffW2 + (j0 + u) * kMlpH + k) / 2];
+        acc[u] = fadd(acc[u], fmul(bf16_lo(p), h1[k]));
+        acc[u] = fadd(acc[u], fmul(bf16_hi(p), h1[k + 1]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      out = fadd(out, fmul(bf16_value(w[kOffW3 + j0 + u]), bf16_round(fmaxf(acc[u], 0.0f))));
   }
   return out;
 }

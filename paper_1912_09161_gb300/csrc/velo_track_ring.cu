@@ -199,7 +199,9 @@ __device__ __forceinline__ Slot slot_of(unsigned char* slots, int m) {
               (uint32_t*)(s + kSlotUsed), (uint32_t*)(s + kSlotPend)};
 }
 
-template <int GA, int GB>
+// MLP: the classifier keeps the candidates (a separate instantiation, so that
+// the plain kernel carries none of its code or registers).
+template <int GA, int GB, bool MLP>
 __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo, const DevParams& par,
                                              const EventsView& ev, const WorkView& wk, int cls, int qi, uint32_t e,
                                              uint32_t H, uint32_t gbase, uint32_t status, unsigned char* smem) {
@@ -223,7 +225,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   const int ns = geo->n_sensors;
   const int nm = geo->n_modules;
   const float tol = par.tan_phi_tol, win = par.phi_window;
-  const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
+  constexpr bool use_mlp = MLP;
 
   // this CTA's global region
   const RingScratch& R = wk.ring;
@@ -493,11 +495,11 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   // ---- 3. plain cuts or classifier, canonical order -----------------------
   const uint32_t ntr = s_misc[R_NTR];
   const uint32_t nwords = (H + 31) / 32;
-  // position of canonical id k in the clustering output, and its module
-  auto hit_xy = [&](uint32_t k, int& m) -> float2 {
-    const int s = sensor_of(s_cb, ns, k);
-    m = s / kSPM;
-    return wk.prov[__ldg(&so[s]) + (k - s_cb[s])];
+  // position in the clustering output of a candidate hit (module << 16 |
+  // canonical id), and its module
+  auto hit_xy = [&](uint32_t h, int& m) -> float2 {
+    m = (int)(h >> 16);
+    return wk.prov[module_src(s_cb, so, m, h & 0xFFFFu)];
   };
   if (!use_mlp) {
     // plain cuts: >= 4 hits, or 3 hits with a small seed scatter and no hit
@@ -533,7 +535,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       fit_track(
           n,
           [&](uint32_t k, float& x, float& y, int& m) {
-            const float2 v = hit_xy(th[k] & 0xFFFFu, m);
+            const float2 v = hit_xy(th[k], m);
             x = v.x;
             y = v.y;
           },
@@ -604,7 +606,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
 
 // One event per CTA from queue qi (events of up to kRingMaxH hits, clustered
 // by the clustering kernel).
-template <int GA, int GB>
+template <int GA, int GB, bool MLP>
 __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kernel(const DevGeometry* __restrict__ geo,
                                                                      DevParams par, EventsView ev, WorkView wk,
                                                                      int cls, int qi) {
@@ -634,7 +636,7 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
     }
     const uint16_t* cbg = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
     for (int s = tid; s <= ns; s += NT) s_cb[s] = cbg[s];
-    window_event<GA, GB>(geo, par, ev, wk, cls, qi, e, H, gbase, status, smem);
+    window_event<GA, GB, MLP>(geo, par, ev, wk, cls, qi, e, H, gbase, status, smem);
   }
 }
 
@@ -647,19 +649,33 @@ constexpr int kRingGroupB = 2;
 uint32_t ring_smem_bytes() { return ring_layout().total; }
 
 cudaError_t ring_set_smem_limit() {
-  return cudaFuncSetAttribute(track_ring_kernel<kRingGroupA, kRingGroupB>,
+  cudaError_t e = cudaFuncSetAttribute(track_ring_kernel<kRingGroupA, kRingGroupB, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(track_ring_kernel<kRingGroupA, kRingGroupB, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_smem_bytes());
 }
 
+// CTAs per SM of the kernel: the smaller of its two instantiations.
 cudaError_t ring_occupancy(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_ring_kernel<kRingGroupA, kRingGroupB>,
-                                                       kRingThreads, ring_smem_bytes());
+  int a = 0, b = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &a, track_ring_kernel<kRingGroupA, kRingGroupB, false>, kRingThreads, ring_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, track_ring_kernel<kRingGroupA, kRingGroupB, true>,
+                                                      kRingThreads, ring_smem_bytes());
+  *blocks_per_sm = a < b ? a : b;
+  return e;
 }
 
 cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                               int cls, int queue, int n_ctas, cudaStream_t st) {
-  track_ring_kernel<kRingGroupA, kRingGroupB>
-      <<<n_ctas, kRingThreads, ring_smem_bytes(), st>>>(geo, par, ev, wk, cls, queue);
+  if (par.use_mlp && wk.mlp_w != nullptr)
+    track_ring_kernel<kRingGroupA, kRingGroupB, true>
+        <<<n_ctas, kRingThreads, ring_smem_bytes(), st>>>(geo, par, ev, wk, cls, queue);
+  else
+    track_ring_kernel<kRingGroupA, kRingGroupB, false>
+        <<<n_ctas, kRingThreads, ring_smem_bytes(), st>>>(geo, par, ev, wk, cls, queue);
   return cudaGetLastError();
 }
 
