@@ -38,7 +38,6 @@ WORKLOADS = {
     "nominal": (1, "10,000 nominal VELO events (Poisson(7.6) pp vertices x Poisson(20) tracks, ~4.5k pixels/event), seed 1"),
     "uneven": (2, "50,000 VELO events with pileup uniform in [1, 20] vertices (200-7,000 hits/event), seed 2"),
 }
-WORKLOAD = WORKLOADS["nominal"][1]
 REF_SAMPLE = 2000           # events per oracle step of the reference arm
 CPU_SAMPLE = 10000          # events of the CPU-baseline sample (the whole batch)
 CPU_SECONDS = 10.0          # the CPU baseline repeats the sample for about this long
@@ -201,7 +200,8 @@ def run_reference(args):
     import oracle
     import velo_synth
     geom = velo_synth.geometry()
-    ev = velo_synth.generate(velo_synth.config(1, n_events=REF_SAMPLE))
+    cfg_index, workload = WORKLOADS[args.workload]
+    ev = velo_synth.generate(velo_synth.config(cfg_index, n_events=REF_SAMPLE))
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle.reconstruct(geom, ev, n_threads=cores)
@@ -214,9 +214,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "sample_events_per_step": REF_SAMPLE},
+        "config": {"workload": workload, "sample_events_per_step": REF_SAMPLE},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"first {REF_SAMPLE} events of the 10,000-event workload per step"},
+                         "sample": f"first {REF_SAMPLE} events of the workload per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
