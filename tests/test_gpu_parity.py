@@ -9,6 +9,7 @@ import os
 import numpy as np
 import pytest
 
+import hand_events
 import oracle
 import velo_synth
 from parity_util import assert_parity, compare_states
@@ -113,6 +114,26 @@ def test_edge_cases(V, geom):
         g0, g1 = int(res.cluster_off[e]), int(res.cluster_off[e + 1])
         o0, o1 = int(orc4.cluster_off[e]), int(orc4.cluster_off[e + 1])
         assert np.array_equal(res.cl_key[g0:g1], orc4.cl_key[o0:o1])
+
+
+@pytest.mark.parametrize("schedule", [None, (256, 0x10, 1)])
+def test_exact_ties(V, schedule):
+    """Exact ties of the scatter in seeding and in forwarding (exact-float
+    geometry) go to the smaller id on the GPU as in the oracle, in the
+    module-window kernel (default schedule) and in the whole-event kernel
+    (whole-event classes only)."""
+    g = hand_events.exact_geometry()
+    ev = hand_events.pixel_events(g, [hand_events.SEED_TIE, hand_events.FORWARD_TIE])
+    rec = V.Reconstructor(g, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, clusters=True)
+    try:
+        if schedule:
+            rec.set_schedule(*schedule)
+        res = rec.run(V.upload_events(ev), clusters=True, check=False)
+    finally:
+        rec.close()
+    orc = oracle.reconstruct(g, ev)
+    assert orc.n_tracks == 2
+    assert_parity(res, orc)
 
 
 def test_empty_batch(V, geom):

@@ -17,6 +17,7 @@ import math
 import numpy as np
 import pytest
 
+import hand_events
 import oracle
 import oracle.metrics as M
 import velo_synth
@@ -315,27 +316,6 @@ def test_subset_metrics_consistent(geom, cfg0_events):
     assert M.summarize(later, rl.cluster_off, rl.pix_cluster, rl.track_off, rl.hit_off, rl.hit_ids)["efficiency"] > 0.95
 
 
-def _exact_geometry(n_modules=6):
-    """A geometry on which every single-pixel hit position is an exact
-    float32 value: pitch 2^-4 mm, integer sensor origins, sensors aligned with
-    the axes, modules 32 mm apart."""
-    spm = 4
-    ns = n_modules * spm
-    mz = np.arange(n_modules, dtype=np.float32) * np.float32(32.0)
-    ox = np.array([4.0 + 20.0 * (s % 2) for _ in range(n_modules) for s in range(spm)], np.float32)
-    oy = np.array([4.0 + 20.0 * (s // 2) for _ in range(n_modules) for s in range(spm)], np.float32)
-    one, zero = np.ones(ns, np.int8), np.zeros(ns, np.int8)
-    return velo_synth.Geometry(n_modules, spm, 256, 256, 0.0625, mz, ox, oy, one, zero, zero, one)
-
-
-def _pixel_event(g, pixels):
-    """One event from (module, col, row) pixels on sensor 0 of each module."""
-    lists = [[[] for _ in range(g.n_sensors)]]
-    for m, c, r in pixels:
-        lists[0][m * g.sensors_per_module].append((c, r))
-    return velo_synth.make_events(lists, g.n_sensors)
-
-
 def _row_of(r, h):
     return int(r.cl_key[h]) & 0xFF
 
@@ -346,8 +326,8 @@ def test_seed_tie_goes_to_the_smaller_id():
     module-3 hits two rows below and above it have exactly the same scatter
     (0.125 mm squared).  The seed takes the one with the smaller canonical id:
     the lower row."""
-    g = _exact_geometry()
-    ev = _pixel_event(g, [(5, 32, 32), (4, 32, 32), (3, 32, 30), (3, 32, 34)])
+    g = hand_events.exact_geometry()
+    ev = hand_events.pixel_events(g, [hand_events.SEED_TIE])
     p = oracle.Params()
     r = oracle.reconstruct(g, ev, p)
     x, y = r.cl_x.astype(np.float64), r.cl_y.astype(np.float64)
@@ -367,8 +347,8 @@ def test_forward_tie_goes_to_the_smaller_id():
     modules 5, 4, 3 extrapolates exactly into module 2, where two hits two
     rows below and above have the same scatter.  The track takes the lower
     row; the other hit stays unused and seeds nothing."""
-    g = _exact_geometry()
-    ev = _pixel_event(g, [(5, 40, 40), (4, 40, 40), (3, 40, 40), (2, 40, 38), (2, 40, 42)])
+    g = hand_events.exact_geometry()
+    ev = hand_events.pixel_events(g, [hand_events.FORWARD_TIE])
     p = oracle.Params()
     r = oracle.reconstruct(g, ev, p)
     mods = ((r.cl_key >> 16) // g.sensors_per_module).tolist()
