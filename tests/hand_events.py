@@ -5,12 +5,12 @@ import numpy as np
 import velo_synth
 
 
-def exact_geometry(n_modules=6):
+def exact_geometry(n_modules=6, spacing=32.0):
     """Pitch 2^-4 mm, integer sensor origins, sensors aligned with the axes,
-    modules 32 mm apart."""
+    modules `spacing` mm apart (a power of two keeps slopes exact)."""
     spm = 4
     ns = n_modules * spm
-    mz = np.arange(n_modules, dtype=np.float32) * np.float32(32.0)
+    mz = np.arange(n_modules, dtype=np.float32) * np.float32(spacing)
     ox = np.array([4.0 + 20.0 * (s % 2) for _ in range(n_modules) for s in range(spm)], np.float32)
     oy = np.array([4.0 + 20.0 * (s // 2) for _ in range(n_modules) for s in range(spm)], np.float32)
     one, zero = np.ones(ns, np.int8), np.zeros(ns, np.int8)

@@ -357,3 +357,23 @@ def test_forward_tie_goes_to_the_smaller_id():
     in2 = [h for h in range(len(mods)) if mods[h] == 2]
     assert tracks[0][-1] == min(in2) and _row_of(r, tracks[0][-1]) == 38
     assert tracks == brute_force(r.cl_x, r.cl_y, mods, g.module_z, p)
+
+
+def test_seed_slope_cut_on_each_axis():
+    """Reading R7, |tx| and |ty| each at most max_slope (0.4): three exact
+    straight lines through modules 5, 4, 3 with modules 8 mm apart (scatter
+    0).  A line 60 rows (3.75 mm) per module steep in y (ty = 0.47) or in x
+    (tx = 0.47) forms no seed; one 40 rows (2.5 mm) per module steep in y
+    (ty = 0.31) does."""
+    g = hand_events.exact_geometry(spacing=8.0)
+    steep_y = [(5, 32, 160), (4, 32, 100), (3, 32, 40)]
+    steep_x = [(5, 160, 32), (4, 100, 32), (3, 40, 32)]
+    mild_y = [(5, 32, 140), (4, 32, 100), (3, 32, 60)]
+    ev = hand_events.pixel_events(g, [steep_y, steep_x, mild_y])
+    p = oracle.Params(tan_phi_tol=0.3)
+    r = oracle.reconstruct(g, ev, p)
+    assert [len(r.event_tracks(e)) for e in range(3)] == [0, 0, 1]
+    for e in range(3):
+        c0, c1 = int(r.cluster_off[e]), int(r.cluster_off[e + 1])
+        mods = ((r.cl_key[c0:c1] >> 16) // g.sensors_per_module).tolist()
+        assert r.event_tracks(e) == brute_force(r.cl_x[c0:c1], r.cl_y[c0:c1], mods, g.module_z, p)
