@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Sensitivity of the oracle pins: plants one plausible mistake at a time in
-a temporary copy of the oracle (C source) and runs the oracle pins
-(tests/test_oracle_*.py) against it.  Every mutant must fail at least one
+a temporary copy of the oracle (the C reconstruction and the Python
+classifier) and runs the oracle pins (tests/test_oracle_*.py) against it.  Every mutant must fail at least one
 pin, except the ones listed as equivalent (no observable effect).
 
     python tests/oracle_mutations.py        # a few minutes on the CPU
@@ -58,12 +58,44 @@ MUTANTS = [
      "s.c00 = s.c00 + dz * c10n;\n    s.c10 = c10n;\n    s.c11 = s.c11 + dm[k]"),
 ]
 
+# (name, text in oracle/mlp.py, replacement): the classifier's features and
+# BF16 network
+MUTANTS_MLP = [
+    ("first-layer ReLU missing", "        h1[:, j] = bf16_round(np.maximum(acc, f32(0)))", "        h1[:, j] = bf16_round(acc)"),
+    ("second-layer activation not rounded", "        h2j = bf16_round(np.maximum(acc, f32(0)))",
+     "        h2j = np.maximum(acc, f32(0))"),
+    ("inputs not rounded", "    x = bf16_round(normalise(f, mean, istd))", "    x = normalise(f, mean, istd)"),
+    ("second-layer bias dropped", "        acc = np.full(n, b2[j], np.float32)", "        acc = np.zeros(n, np.float32)"),
+    ("chi2 not per ndof", "    f[:, 0] = chi2 / np.asarray(ndof).astype(np.float32)", "    f[:, 0] = chi2"),
+    ("eta argument", "        q = (f32(1.0) + s) / np.where(t > f32(1e-7), t, f32(1.0))",
+     "        q = (f32(1.0) + t) / np.where(t > f32(1e-7), s, f32(1.0))"),
+    ("phi arguments swapped", "    f[:, 8] = atan2_f32(ty, tx)", "    f[:, 8] = atan2_f32(tx, ty)"),
+    ("missed modules off by one", "    f[:, 9] = ((mf - ml + 1) - n).astype(np.float32)",
+     "    f[:, 9] = ((mf - ml) - n).astype(np.float32)"),
+    ("log series coefficient 1/5 as 1/7", "    for c in (_INV[4], _INV[3], _INV[2], _INV[1], _INV[0]):\n        p = p * v + c\n    r =",
+     "    for c in (_INV[4], _INV[3], _INV[3], _INV[1], _INV[0]):\n        p = p * v + c\n    r ="),
+    ("second-layer sum order reversed", "        for k in range(N_H):\n            acc = acc + W2[j, k] * h1[:, k]",
+     "        for k in reversed(range(N_H)):\n            acc = acc + W2[j, k] * h1[:, k]"),
+    ("output bias dropped", "    out = np.full(n, b3[0], np.float32)\n", "    out = np.zeros(n, np.float32)\n"),
+    ("atan reduction constant dropped", "    a = np.where(big, a + _PI6, a).astype(np.float32)",
+     "    a = np.where(big, a, a).astype(np.float32)"),
+    ("BF16 ties away from zero", "    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16", "    b = (b + 0x8000) >> 16"),
+    ("standardisation divides", "    return ((np.asarray(f, np.float32) - mean.astype(np.float32)) * istd.astype(np.float32))",
+     "    return ((np.asarray(f, np.float32) - mean.astype(np.float32)) / istd.astype(np.float32))"),
+    ("first-layer sum order reversed", "        for i in range(N_IN):\n            acc = acc + W1[j, i] * x[:, i]",
+     "        for i in reversed(range(N_IN)):\n            acc = acc + W1[j, i] * x[:, i]"),
+]
+
 # Mutants that cannot change any output:
 #   - duplicates kept in the sorted key list: the flood fill still visits
 #     (and counts) every pixel position once;
 #   - a seed's a hit not marked used: its module never takes part in a later
 #     seed, and forwarding does not look at used flags.
 EQUIVALENT = [
+    # the last term of the log series is below float32 resolution
+    # (2 u^11 / 11 < 8e-10 relative for |u| <= 0.172)
+    ("log series u^11 term dropped", "    for c in (_INV[4], _INV[3], _INV[2], _INV[1], _INV[0]):\n        p = p * v + c\n    r =",
+     "    for c in (_INV[3], _INV[2], _INV[1], _INV[0]):\n        p = p * v + c\n    r =", "mlp.py"),
     ("duplicates kept", "if (i == 0 || keys[i] != keys[i - 1]) keys[nu++] = keys[i];", "keys[nu++] = keys[i];"),
     ("seed a not marked used", "used[seeds[k][0]] = 1; used[seeds[k][1]] = 1;", "used[seeds[k][1]] = 1;"),
 ]
@@ -72,13 +104,13 @@ PINS = ["tests/test_oracle_tracking.py", "tests/test_oracle_cluster.py", "tests/
         "tests/test_oracle_mlp.py"]
 
 
-def run(name, old, new):
+def run(name, old, new, target="velo_oracle.c"):
     with tempfile.TemporaryDirectory() as d:
         for sub in ("oracle", "velo_synth", "tests"):
             shutil.copytree(os.path.join(ROOT, sub), os.path.join(d, sub),
                             ignore=shutil.ignore_patterns("*.so", "__pycache__"))
         shutil.copy(os.path.join(ROOT, "pytest.ini"), d)
-        p = os.path.join(d, "oracle", "velo_oracle.c")
+        p = os.path.join(d, "oracle", target)
         s = open(p).read()
         assert s.count(old) == 1, name
         open(p, "w").write(s.replace(old, new))
@@ -95,10 +127,16 @@ def main() -> int:
         print(f"{'caught' if caught else 'MISSED'}: {name:34s} {failed[:1]}", flush=True)
         if not caught:
             missed.append(name)
-    for name, old, new in EQUIVALENT:
-        caught, _ = run(name, old, new)
+    for name, old, new in MUTANTS_MLP:
+        caught, failed = run(name, old, new, "mlp.py")
+        print(f"{'caught' if caught else 'MISSED'}: {name:34s} {failed[:1]}", flush=True)
+        if not caught:
+            missed.append(name)
+    for name, old, new, *target in EQUIVALENT:
+        caught, _ = run(name, old, new, *target)
         print(f"{'caught' if caught else 'no effect'}: {name} (equivalent)", flush=True)
-    print(f"{len(MUTANTS) - len(missed)} of {len(MUTANTS)} mutants caught")
+    total = len(MUTANTS) + len(MUTANTS_MLP)
+    print(f"{total - len(missed)} of {total} mutants caught")
     return 1 if missed else 0
 
 

@@ -3,7 +3,9 @@
 * the series logarithm and arctangent against numpy's (within a few ulp);
 * the features against float64 formulas (eta = asinh(1/T), phi = atan2);
 * the float64 backward pass against central finite differences;
-* the BF16 forward against a float64 simulation of the same roundings.
+* the BF16 forward against a float64 simulation of the same roundings;
+* the fixed FP32 summation order (bias first, ascending inputs) on hand-built
+  networks whose result depends on that order.
 """
 import numpy as np
 import pytest
@@ -68,14 +70,20 @@ def test_backward_matches_finite_differences():
 
 def test_bf16_forward_matches_rounding_simulation():
     rng = np.random.default_rng(11)
-    p = M.bf16_round(M.init_params(2))
-    f = rng.normal(size=(4000, M.N_IN)).astype(np.float32)
-    mean = np.zeros(M.N_IN, np.float32)
-    istd = np.ones(M.N_IN, np.float32)
+    p = M.init_params(2)
+    W1_, b1_, W2_, b2_, W3_, b3_ = M.split(p)   # views: non-zero biases
+    b1_[:] = rng.normal(0, 0.2, M.N_H)
+    b2_[:] = rng.normal(0, 0.2, M.N_H)
+    b3_[:] = 0.3
+    p = M.bf16_round(p)
+    mean = rng.normal(0, 1, M.N_IN).astype(np.float32)
+    istd = rng.uniform(0.5, 2.0, M.N_IN).astype(np.float32)
+    f = (rng.normal(size=(4000, M.N_IN)) / istd + mean).astype(np.float32)
     got = M.forward_bf16(f, p, mean, istd).astype(np.float64)
-    # float64 sums, BF16 roundings at the same points
+    # float64 sums, BF16 roundings at the same points; the standardisation
+    # (f - mean) * istd in float32 is part of the definition of the inputs
     W1, b1, W2, b2, W3, b3 = M.split(p.astype(np.float64))
-    x = M.bf16_round(f).astype(np.float64)
+    x = M.bf16_round(((f - mean) * istd).astype(np.float32)).astype(np.float64)
     h1 = M.bf16_round(np.maximum(x @ W1.T + b1, 0).astype(np.float32)).astype(np.float64)
     h2 = M.bf16_round(np.maximum(h1 @ W2.T + b2, 0).astype(np.float32)).astype(np.float64)
     ref = h2 @ W3 + b3[0]
@@ -89,3 +97,42 @@ def test_bf16_rounding():
     b = M.bf16_round(v)
     assert b[0] == 1.0 and b[1] == 1.0 and b[2] == np.float32(1.0078125) and b[3] == -2.5
     assert np.all(M.bf16_bits(np.float32([1.0])) == 0x3F80)
+
+
+def _hand_network(layer):
+    """Parameters whose logit shows the FP32 summation order of one layer:
+    three terms 2^24, -2^24 and 1 after a bias of 1.  In the defined order
+    (bias first, then ascending inputs) float32 gives ((1 + 2^24) - 2^24) + 1
+    = 1, since 1 + 2^24 rounds to 2^24 (ties to even); summed in reverse, or
+    with the bias last, it gives 2.  The other layers pass values through
+    (weights 1, biases 0), and every value involved is exact in BF16."""
+    p = np.zeros(M.N_PARAMS, np.float32)
+    W1, b1, W2, b2, W3, b3 = M.split(p)
+    big = np.float32(2.0 ** 24)
+    f = np.zeros((1, M.N_IN), np.float32)
+    if layer == 1:      # unit 0 of layer 1 sums x0 - x1 + x2 with x = (2^24, 2^24, 1)
+        f[0, :3] = (big, big, 1.0)
+        W1[0, :3] = (1.0, -1.0, 1.0)
+        b1[0] = 1.0
+        W2[0, 0] = 1.0
+        W3[0] = 1.0
+    elif layer == 2:    # layer 1 passes (2^24, 2^24, 1); unit 0 of layer 2 sums h0 - h1 + h2
+        f[0, :3] = (big, big, 1.0)
+        W1[0, 0] = W1[1, 1] = W1[2, 2] = 1.0
+        W2[0, :3] = (1.0, -1.0, 1.0)
+        b2[0] = 1.0
+        W3[0] = 1.0
+    else:               # layers 1, 2 pass (2^24, 2^24, 1); the output sums h0 - h1 + h2
+        f[0, :3] = (big, big, 1.0)
+        W1[0, 0] = W1[1, 1] = W1[2, 2] = 1.0
+        W2[0, 0] = W2[1, 1] = W2[2, 2] = 1.0
+        W3[:3] = (1.0, -1.0, 1.0)
+        b3[0] = 1.0
+    return f, p
+
+
+@pytest.mark.parametrize("layer", [1, 2, 3])
+def test_bf16_forward_fixed_summation_order(layer):
+    f, p = _hand_network(layer)
+    out = M.forward_bf16(f, p, np.zeros(M.N_IN, np.float32), np.ones(M.N_IN, np.float32))
+    assert out[0] == np.float32(1.0)
