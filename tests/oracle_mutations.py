@@ -86,6 +86,20 @@ MUTANTS_MLP = [
      "        for i in reversed(range(N_IN)):\n            acc = acc + W1[j, i] * x[:, i]"),
 ]
 
+# (name, text in oracle/metrics.py, replacement): truth matching
+MUTANTS_METRICS = [
+    ("match fraction 0.6", "MATCH_FRACTION = 0.7", "MATCH_FRACTION = 0.6"),
+    ("reconstructible from 2 modules", "    return cnt >= 3", "    return cnt >= 2"),
+    ("clone rate over all tracks", "clone_rate=float(len(matched) - n_unique) / len(matched)",
+     "clone_rate=float(len(matched) - n_unique) / n_tracks"),
+    ("efficiency counts every found particle", "n_found = int((found & rec).sum())", "n_found = int(found.sum())"),
+    ("cluster label ties to the larger index", "order = np.lexsort((uniq[:, 1], -cnt, uniq[:, 0]))",
+     "order = np.lexsort((-uniq[:, 1], -cnt, uniq[:, 0]))"),
+    ("repeated pixel takes the larger index", "order = np.lexsort((labk, u))", "order = np.lexsort((-labk, u))"),
+    ("ghosts counted from matched tracks", "ghost_rate=float((match < 0).sum()) / n_tracks",
+     "ghost_rate=float((match >= 0).sum()) / n_tracks"),
+]
+
 # Mutants that cannot change any output:
 #   - duplicates kept in the sorted key list: the flood fill still visits
 #     (and counts) every pixel position once;
@@ -101,7 +115,7 @@ EQUIVALENT = [
 ]
 
 PINS = ["tests/test_oracle_tracking.py", "tests/test_oracle_cluster.py", "tests/test_oracle_fit.py",
-        "tests/test_oracle_mlp.py"]
+        "tests/test_oracle_mlp.py", "tests/test_oracle_metrics.py"]
 
 
 def run(name, old, new, target="velo_oracle.c"):
@@ -132,10 +146,15 @@ def main() -> int:
         print(f"{'caught' if caught else 'MISSED'}: {name:34s} {failed[:1]}", flush=True)
         if not caught:
             missed.append(name)
+    for name, old, new in MUTANTS_METRICS:
+        caught, failed = run(name, old, new, "metrics.py")
+        print(f"{'caught' if caught else 'MISSED'}: {name:34s} {failed[:1]}", flush=True)
+        if not caught:
+            missed.append(name)
     for name, old, new, *target in EQUIVALENT:
         caught, _ = run(name, old, new, *target)
         print(f"{'caught' if caught else 'no effect'}: {name} (equivalent)", flush=True)
-    total = len(MUTANTS) + len(MUTANTS_MLP)
+    total = len(MUTANTS) + len(MUTANTS_MLP) + len(MUTANTS_METRICS)
     print(f"{total - len(missed)} of {total} mutants caught")
     return 1 if missed else 0
 
