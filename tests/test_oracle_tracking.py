@@ -377,3 +377,18 @@ def test_seed_slope_cut_on_each_axis():
         c0, c1 = int(r.cluster_off[e]), int(r.cluster_off[e + 1])
         mods = ((r.cl_key[c0:c1] >> 16) // g.sensors_per_module).tolist()
         assert r.event_tracks(e) == brute_force(r.cl_x[c0:c1], r.cl_y[c0:c1], mods, g.module_z, p)
+
+
+@pytest.mark.parametrize("n_modules", [3, 4])
+def test_fewest_modules(n_modules):
+    """The smallest geometries: three modules give a single round (one seed,
+    nothing to extend), four give a seed and one extension.  An exact line
+    along the beam through every module is one track holding all its hits."""
+    g = hand_events.exact_geometry(n_modules=n_modules)
+    ev = hand_events.pixel_events(g, [[(m, 50, 60) for m in range(n_modules - 1, -1, -1)]])
+    p = oracle.Params()
+    r = oracle.reconstruct(g, ev, p)
+    mods = ((r.cl_key >> 16) // g.sensors_per_module).tolist()
+    tracks = r.event_tracks(0)
+    assert [[mods[h] for h in t] for t in tracks] == [list(range(n_modules - 1, -1, -1))]
+    assert tracks == brute_force(r.cl_x, r.cl_y, mods, g.module_z, p)
