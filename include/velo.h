@@ -41,8 +41,9 @@ typedef enum velo_status {
 
 /* Per-event status bits (velo_output.event_status). */
 #define VELO_EV_BAD_PIXEL 0x1u    /* pixel(s) outside the sensor were ignored */
-#define VELO_EV_BAD_OFFSETS 0x2u  /* sensor offsets decrease: event skipped */
-#define VELO_EV_OVERFLOW 0x4u     /* event exceeds the per-event working capacity: skipped */
+#define VELO_EV_BAD_OFFSETS 0x2u  /* sensor offsets decrease (or run past the pixel capacity): event skipped */
+#define VELO_EV_OVERFLOW 0x4u     /* event beyond every working capacity (more than 65,504 hits, or more
+                                     than 6,614 track candidates in the global-memory pass): skipped */
 #define VELO_EV_TRUNCATED 0x8u    /* outputs of this event did not fit the caller's buffers */
 
 /* Number of floats per track state (SoA rows of velo_output.states). */
@@ -142,12 +143,24 @@ typedef struct velo_output {
   uint32_t *cl_key;       /* [cap_clusters] sensor << 16 | smallest col*256+row */
 } velo_output;
 
-/* Creates a handle on the current CUDA device; allocates its arena once. */
+/*
+ * Creates a handle on the current CUDA device and allocates, once, all the
+ * device memory it will use (the paper's framework likewise preallocates the
+ * memory of every stream, section 3.2): the arena (geometry, counters,
+ * classifier weights, working storage at the configured capacities), the
+ * per-CTA regions of the tracking kernels, and the regions of the two
+ * global-memory slow paths (sensors of more than 1,000 raw pixels; events
+ * beyond the largest shared-memory tracking class, up to 65,504 hits).
+ * Geometry and parameters are host structs, copied.  Errors: VELO_ERR_INPUT
+ * (invalid geometry or parameters), VELO_ERR_NOMEM, VELO_ERR_CUDA; *out is
+ * then NULL.  velo_destroy frees everything (NULL is a no-op).
+ */
 int velo_create(const velo_geometry *geometry, const velo_params *params,
                 const velo_config *config, velo_handle **out);
 void velo_destroy(velo_handle *h);
 
-/* Bytes of device memory a handle with this configuration holds. */
+/* Bytes of the arena a handle with this configuration holds (the arena of
+ * velo_create, without the per-CTA and slow-path regions).  Host only. */
 int velo_required_bytes(const velo_geometry *geometry, const velo_config *config, size_t *bytes);
 
 /*
@@ -192,12 +205,33 @@ int velo_mlp_get_state(velo_mlp_trainer *t, float *params, uint16_t *params_bf16
                        uint32_t *step);
 int velo_mlp_set_state(velo_mlp_trainer *t, const float *params, const float *m1, const float *m2, uint32_t step);
 
-/* Replaces the method parameters (takes effect at the next call). */
+/*
+ * Working storage a velo_reconstruct call on this batch needs (paper section
+ * 3.2: memory is sized per batch of events): *ws_bytes = the bytes of a
+ * handle arena sized for exactly this batch's events and pixels.  Reads the
+ * batch's first and last sensor offsets from the device (events: device
+ * pointers, as for velo_reconstruct), so it synchronizes the device.
+ * Returns VELO_ERR_NOMEM (with *ws_bytes set) when the batch exceeds the
+ * handle's max_events / max_pixels, VELO_ERR_INPUT for null pointers or
+ * decreasing end offsets, VELO_ERR_CUDA if the read fails.
+ */
+int velo_required(const velo_handle *h, const velo_events *events, size_t *ws_bytes);
+
+/* Replaces the method parameters (section 2.3.1 readings; takes effect at the
+ * next call).  VELO_ERR_INPUT for negative, NaN or infinite values. */
 int velo_set_params(velo_handle *h, const velo_params *params);
 
 /*
- * Reconstructs a batch; enqueues all work on `stream` (a cudaStream_t, 0 for
- * the legacy stream) and returns without waiting.
+ * Reconstructs a batch (paper section 2.3.1: clustering, search by triplet,
+ * simple Kalman fit with the beamline state; section 2.3: one event per CTA);
+ * enqueues all work on `stream` (a cudaStream_t, 0 for the legacy stream) and
+ * returns without waiting.  Inputs and outputs are device pointers owned by
+ * the caller (section 2.2: raw data in, reconstructed objects out).  Host-side
+ * errors are returned at once (VELO_ERR_INPUT for null or incomplete
+ * descriptors, VELO_ERR_NOMEM for more events than max_events, VELO_ERR_STATE
+ * for cluster output on a handle created without VELO_CFG_CLUSTERS,
+ * VELO_ERR_CUDA for a failed launch); device-side problems go to the
+ * per-event status words and velo_sync_status.
  */
 int velo_reconstruct(velo_handle *h, const velo_events *events, const velo_output *out, void *stream);
 
@@ -209,9 +243,12 @@ int velo_reconstruct(velo_handle *h, const velo_events *events, const velo_outpu
 int velo_sync_status(velo_handle *h, void *stream);
 
 /*
- * End-to-end call with HOST buffers: copies the events from host memory
- * (pinned for asynchronous copies), reconstructs, and copies the outputs back
- * into host buffers of the same layout as velo_output.  Synchronous.
+ * End-to-end call with HOST buffers (paper section 2.2: raw data copied to the
+ * GPU, only results copied back): copies the events from host memory (pinned
+ * for asynchronous copies) into a staging buffer of the handle (allocated on
+ * first use), reconstructs, and copies the outputs back into host buffers of
+ * the same layout as velo_output.  Synchronous.  VELO_ERR_CAPACITY when the
+ * caller's host buffers are too small (totals hold the needed sizes).
  */
 int velo_reconstruct_host(velo_handle *h, uint32_t n_events, const uint32_t *sensor_off_host,
                           const uint16_t *col_host, const uint16_t *row_host,
@@ -293,15 +330,22 @@ int velo_describe(const velo_handle *h, char *buf, size_t n);
  * clustering kernel's working memory is a 16 MiB array inside the library,
  * which every GPU that loads the library holds until the process exits.
  *
- * Inputs: the geometry (host pointers), a batch of events (device pointers,
- * as velo_events) of at most 512 events and 1,500,000 pixels, and n_pixels,
- * the batch's pixel count (sensor_off's last entry); larger batches return
- * VELO_ERR_NOMEM without running.  Outputs (device pointers, caller-owned):
- * the canonical cluster list exactly as velo_reconstruct writes it with
- * cluster output on -- cluster_off [n_events + 1], cl_x, cl_y, cl_key
- * [cap_clusters] -- plus event_status [n_events] and totals [4] (totals[2] =
- * clusters needed; totals[3] = error bits).  Enqueued on `stream`; read
- * errors after a stream synchronization from event_status and totals.
+ * Inputs: the geometry (host pointers, copied into the launch itself: no
+ * host buffer needs to outlive the call), a batch of events (device
+ * pointers, as velo_events) of at most 512 events and 1,500,000 pixels, and
+ * n_pixels, the batch's pixel count (sensor_off's last entry); larger
+ * batches return VELO_ERR_NOMEM without running.  The device checks every
+ * event's offsets against the 1,500,000-pixel limit itself, so an
+ * understated n_pixels cannot overrun the array: an event whose pixels end
+ * beyond the limit is skipped and marked VELO_EV_BAD_OFFSETS (totals[3] has
+ * the input-error bit).  A sensor of more than 1,000 raw pixels marks its
+ * event VELO_EV_OVERFLOW (this entry point has no global-memory second
+ * pass).  Outputs (device pointers, caller-owned): the canonical cluster list
+ * exactly as velo_reconstruct writes it with cluster output on --
+ * cluster_off [n_events + 1], cl_x, cl_y, cl_key [cap_clusters] -- plus
+ * event_status [n_events] and totals [4] (totals[2] = clusters needed;
+ * totals[3] = error bits).  Enqueued on `stream`; read errors after a stream
+ * synchronization from event_status and totals.
  *
  * The first call on a device (with that device current) looks up the
  * array's device address and sets the kernel's shared-memory limit; make it

@@ -66,6 +66,9 @@ struct velo_handle {
   // module-window kernel: CTAs per SM and its per-CTA global regions
   int ring_per_sm = 0;
   void* ring_buf = nullptr;
+  // global regions of the slow paths: second clustering pass and the
+  // global-memory tracking pass
+  void* slow_buf = nullptr;
   int smem_sm = 0, smem_optin = 0;
   // captured launch sequences, replayed while the call descriptors match
   bool use_graphs = false;
@@ -284,6 +287,23 @@ int setup_ring(velo_handle* h) {
   return VELO_OK;
 }
 
+// Global regions of the slow paths (kBigCtas clustering regions, kHugeCtas
+// whole-event layouts with their hit slots).
+int setup_slow(velo_handle* h) {
+  const size_t big = align256((size_t)kBigCtas * kBigScratchBytes);
+  const size_t per = huge_region_bytes((uint32_t)kMaxModules);
+  const size_t total = big + (size_t)kHugeCtas * per;
+  cudaError_t e = cudaMalloc(&h->slow_buf, total);
+  if (e != cudaSuccess) {
+    h->slow_buf = nullptr;
+    return fail(VELO_ERR_NOMEM, "cudaMalloc(%zu) (slow paths): %s", total, cudaGetErrorString(e));
+  }
+  h->wk.big_scratch = (unsigned char*)h->slow_buf;
+  h->wk.huge_scratch = (unsigned char*)h->slow_buf + big;
+  h->wk.huge_bytes = per;
+  return VELO_OK;
+}
+
 int build_classes(velo_handle* h, const velo_schedule& sc) {
   if (sc.track_threads != 128 && sc.track_threads != 256)
     return fail(VELO_ERR_INPUT, "schedule: track_threads must be 128 or 256");
@@ -366,6 +386,7 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
   CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[0], st, mark));
   CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, st));
+  CUDA_TRY(launch_cluster_big(h->d_geo, ev, wk, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[1], st, mark));
   if (E) {
     if (h->sched.concurrent) {
@@ -383,6 +404,8 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
     // events that ran out of track storage in their class: largest plan
     const int big = h->n_classes - 1;
     CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[big], big, kRetryQueue, h->threads, h->ctas[big], st));
+    // events beyond every shared-memory class: global-memory pass
+    CUDA_TRY(launch_track_huge(h->d_geo, h->par, ev, wk, big, st));
   }
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[2], st, mark));
   CUDA_TRY(launch_scan(E, wk, out, st));
@@ -473,6 +496,23 @@ int velo_required_bytes(const velo_geometry* geometry, const velo_config* config
   return VELO_OK;
 }
 
+int velo_required(const velo_handle* h, const velo_events* events, size_t* ws_bytes) {
+  if (!h || !events || !ws_bytes) return fail(VELO_ERR_INPUT, "velo_required: null argument");
+  if (!events->sensor_off) return fail(VELO_ERR_INPUT, "velo_required: null sensor offsets");
+  const uint32_t E = events->n_events;
+  const size_t n_off = (size_t)E * (size_t)h->geo.n_sensors + 1;
+  uint32_t ends[2] = {0, 0};
+  CUDA_TRY(cudaMemcpy(&ends[0], events->sensor_off, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(&ends[1], events->sensor_off + (n_off - 1), sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (ends[1] < ends[0]) return fail(VELO_ERR_INPUT, "velo_required: decreasing offsets");
+  const uint64_t P = ends[1];  // pixel arrays are indexed from 0
+  *ws_bytes = plan_fixed().total + plan_work(work_config(E, P)).total;
+  if (E > h->cfg.max_events || P > h->cfg.max_pixels)
+    return fail(VELO_ERR_NOMEM, "velo_required: %u events / %llu pixels exceed the handle's %u / %llu", E,
+                (unsigned long long)P, h->cfg.max_events, (unsigned long long)h->cfg.max_pixels);
+  return VELO_OK;
+}
+
 int velo_create(const velo_geometry* geometry, const velo_params* params, const velo_config* config,
                 velo_handle** out) {
   if (!out) return fail(VELO_ERR_INPUT, "velo_create: null output pointer");
@@ -533,6 +573,8 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     carve_work(h, base + fx.total, h->cfg);
     rc = setup_ring(h);
     if (rc) break;
+    rc = setup_slow(h);
+    if (rc) break;
     h->trk_bytes = trk_bytes_bound(h);
     e = cudaMalloc(&h->trk, h->trk_bytes);
     if (e != cudaSuccess) { rc = fail(VELO_ERR_NOMEM, "cudaMalloc(%zu): %s", h->trk_bytes, cudaGetErrorString(e)); h->trk = nullptr; break; }
@@ -573,6 +615,7 @@ void velo_destroy(velo_handle* h) {
   if (h->stage) cudaFree(h->stage);
   if (h->trk) cudaFree(h->trk);
   if (h->ring_buf) cudaFree(h->ring_buf);
+  if (h->slow_buf) cudaFree(h->slow_buf);
   if (h->h_totals) cudaFreeHost(h->h_totals);
   delete h;
 }
@@ -590,7 +633,12 @@ int velo_describe(const velo_handle* h, char* buf, size_t n) {
                   "\"max_hits\": %u, \"max_tracks\": %u}",
                   k ? ", " : "", h->ring_cls[k] ? "window" : "event", h->ring_cls[k] ? kRingThreads : h->threads,
                   h->per_sm[k], h->ctas[k], h->caps[k].smem, h->caps[k].maxh, h->caps[k].maxt);
-  if (w > 0 && (size_t)w < n) snprintf(buf + w, n - w, "]}");
+  if (w > 0 && (size_t)w < n)
+    w += snprintf(buf + w, n - w,
+                  "], \"slow_paths\": {\"cluster_ctas\": %d, \"cluster_region_bytes\": %zu, \"track_ctas\": %d, "
+                  "\"track_region_bytes\": %zu, \"track_max_hits\": %u, \"track_max_tracks\": %u}}",
+                  kBigCtas, (size_t)kBigScratchBytes, kHugeCtas, (size_t)h->wk.huge_bytes, kHugeMaxH,
+                  huge_caps((uint32_t)h->geo.n_modules).maxt);
   return VELO_OK;
 }
 

@@ -8,7 +8,10 @@
 // pixels in a segment of that many lanes (four, two or one sensor per warp),
 // up to 64 with two pixels per lane.  Up to 256 pixels: keys sorted in
 // registers, union-find in the warp's shared-memory slice; up to 1000 (warp 0
-// only): union-find over unsorted staged pixels.  Every cluster becomes a hit
+// only): union-find over unsorted staged pixels.  An event with a larger
+// sensor goes to a second pass (cluster_big_kernel, a few persistent CTAs)
+// that clusters such sensors with the whole CTA over a 256 x 256 occupancy
+// bitmap, with union-find in the CTA's global region.  Every cluster becomes a hit
 // at a provisional position (the sensor's pixel offset + the cluster's rank
 // by smallest pixel key), which orders hits exactly like their canonical ids;
 // the per-sensor canonical bases and the event's hit count go to global
@@ -23,7 +26,6 @@ namespace velo {
 // Sensors of 33 to 64 pixels: neighbour masks in registers (false) or the
 // sorted union-find of the larger sensors (true).
 constexpr bool kSortedUnionFor64 = false;
-constexpr uint32_t kWarpStage = 1000;  // raw pixels warp 0 can stage for one large sensor
 constexpr uint32_t kMidStage = 256;    // raw pixels of the sorted union-find path
 constexpr uint32_t kAccBytes = 8 * 64; // per-warp packed accumulators
 // Per-warp shared-memory slices: warp 0 stages sensors of up to kWarpStage
@@ -545,6 +547,116 @@ __device__ uint32_t cluster_sensor_mid(const uint16_t* __restrict__ col, const u
   return nroot;
 }
 
+// Union of the components of cells x and y (lock-free on parent cells in
+// global memory): the root with the larger cell goes under the one with the
+// smaller, so parents always lead to smaller cells and every root ends at its
+// component's smallest cell.
+__device__ inline void uf_unite_cell(uint32_t* par, uint32_t x, uint32_t y) {
+  volatile uint32_t* vp = par;
+  while (true) {
+    while (vp[x] != x) x = vp[x];
+    while (vp[y] != y) y = vp[y];
+    if (x == y) return;
+    if (x > y) {
+      const uint32_t t = x;
+      x = y;
+      y = t;
+    }
+    if (atomicCAS(&par[y], y, x) == y) return;
+  }
+}
+
+// Sensors beyond kWarpStage raw pixels (second clustering pass, the whole
+// CTA, one sensor at a time):
+//   - the fired cells c * 256 + r of the sensor's 256 x 256 occupancy bitmap
+//     in shared memory (a repeated pixel sets its bit again);
+//   - every fired cell joins its fired 8-neighbours of larger cell by
+//     union-find on the parent array in the CTA's global region (cell order
+//     is key order: col * 256 + row);
+//   - roots (cells that are their own parent, the smallest key of their
+//     component) in a second bitmap; a root's rank among the sensor's roots
+//     is an exclusive prefix count over the bitmap words plus a population
+//     count within its word;
+//   - member counts and sums accumulated per rank, then one hit per root.
+// fired, roots, pre: kBigCells / 32 words of shared memory each.  Returns the
+// sensor's cluster count on every thread.
+template <int NT>
+__device__ uint32_t cluster_sensor_grid(const uint16_t* __restrict__ col, const uint16_t* __restrict__ row,
+                                        uint32_t a, uint32_t n, int ncols, int nrows, const SensorGeo& g,
+                                        const HitOut& out, uint32_t* fired, uint32_t* roots, uint32_t* pre,
+                                        uint32_t* s_scan, unsigned char* gscr, bool& bad) {
+  constexpr uint32_t W = kBigCells / 32;
+  uint32_t* par = (uint32_t*)gscr;
+  uint32_t* cnt = par + kBigCells;
+  unsigned long long* sum = (unsigned long long*)(cnt + kBigMaxRoots);
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t w = tid; w < W; w += NT) fired[w] = 0;
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += NT) {
+    const uint32_t c = col[a + i], r = row[a + i];
+    if (c < (uint32_t)ncols && r < (uint32_t)nrows) atomicOr(&fired[((c << 8) | r) >> 5], 1u << (r & 31));
+    else bad = true;
+  }
+  __syncthreads();
+  for (uint32_t w = tid; w < W; w += NT)
+    for (uint32_t bits = fired[w]; bits; bits &= bits - 1) {
+      const uint32_t cell = 32 * w + (uint32_t)(__ffs(bits) - 1);
+      par[cell] = cell;
+    }
+  __syncthreads();
+  auto on = [&](uint32_t cell) { return (fired[cell >> 5] >> (cell & 31)) & 1u; };
+  for (uint32_t w = tid; w < W; w += NT)
+    for (uint32_t bits = fired[w]; bits; bits &= bits - 1) {
+      const uint32_t cell = 32 * w + (uint32_t)(__ffs(bits) - 1);
+      const uint32_t c = cell >> 8, r = cell & 255u;
+      if (r < 255u && on(cell + 1)) uf_unite_cell(par, cell, cell + 1);
+      if (c < 255u) {
+        if (r > 0u && on(cell + 255)) uf_unite_cell(par, cell, cell + 255);
+        if (on(cell + 256)) uf_unite_cell(par, cell, cell + 256);
+        if (r < 255u && on(cell + 257)) uf_unite_cell(par, cell, cell + 257);
+      }
+    }
+  __syncthreads();
+  // the forest is final: every fired cell points at its root, roots marked
+  for (uint32_t w = tid; w < W; w += NT) {
+    uint32_t rb = 0;
+    for (uint32_t bits = fired[w]; bits; bits &= bits - 1) {
+      const uint32_t b = (uint32_t)(__ffs(bits) - 1), cell = 32 * w + b;
+      uint32_t root = cell;
+      while (par[root] != root) root = par[root];
+      par[cell] = root;
+      if (root == cell) rb |= 1u << b;
+    }
+    roots[w] = rb;
+    pre[w] = __popc(rb);
+  }
+  const uint32_t R = block_exscan(pre, W, s_scan);
+  for (uint32_t k = tid; k < R; k += NT) {
+    cnt[k] = 0;
+    sum[k] = 0ull;
+  }
+  __syncthreads();
+  for (uint32_t w = tid; w < W; w += NT)
+    for (uint32_t bits = fired[w]; bits; bits &= bits - 1) {
+      const uint32_t cell = 32 * w + (uint32_t)(__ffs(bits) - 1);
+      const uint32_t root = par[cell], rw = root >> 5;
+      const uint32_t rank = pre[rw] + __popc(roots[rw] & ((1u << (root & 31)) - 1u));
+      atomicAdd(&cnt[rank], 1u);
+      atomicAdd(&sum[rank], ((unsigned long long)(cell >> 8) << 32) | (cell & 255u));
+    }
+  __syncthreads();
+  for (uint32_t w = tid; w < W; w += NT) {
+    uint32_t rank = pre[w];
+    for (uint32_t bits = roots[w]; bits; bits &= bits - 1, ++rank) {
+      const uint32_t cell = 32 * w + (uint32_t)(__ffs(bits) - 1);
+      const unsigned long long v = sum[rank];
+      store_cluster(out, g, a + rank, cell, cnt[rank], (uint32_t)(v >> 32), (uint32_t)v);
+    }
+  }
+  __syncthreads();
+  return R;
+}
+
 enum { CM_NEXT = 0, CM_STATUS = 1, CM_CLASS = 8 };  // CM_CLASS..: sensors per size class
 
 // Shared memory for clustering one event.
@@ -560,12 +672,17 @@ struct ClusterSmem {
 // Clusters event e with the whole CTA (NT threads).  On success returns true,
 // with H the event's hit count and status its status bits; cnt[s] is then
 // the canonical id of sensor s's first hit (cnt[ns] = H), also written to
-// the event's canonical bases in global memory.  On failure (bad offsets, a
-// sensor beyond kWarpStage pixels, more than 65535 hits) writes the event's
-// record and returns false.
-template <int NT>
+// the event's canonical bases in global memory.  An event with a sensor
+// beyond kWarpStage pixels is queued for the second pass when there is one
+// (BIG = false, wk.big_scratch set); the second pass (BIG = true) clusters
+// such sensors with the whole CTA (gscr: its global region).  On failure (bad
+// offsets, a sensor beyond kWarpStage pixels with no second pass, more than
+// 65535 hits) writes the event's record and returns false; a deferred event
+// returns false without a record.
+template <int NT, bool BIG>
 __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsView& ev, const WorkView& wk,
-                              uint32_t e, const ClusterSmem& S, uint32_t& H_out, uint32_t& status_out) {
+                              uint32_t e, const ClusterSmem& S, uint32_t& H_out, uint32_t& status_out,
+                              unsigned char* gscr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = geo->n_sensors, ncols = geo->n_cols, nrows = geo->n_rows;
   unsigned char* slice = S.warps + (warp == 0 ? 0u : kBigSlice + (uint32_t)(warp - 1) * kSmallSlice);
@@ -606,7 +723,21 @@ __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsV
   }
   __syncthreads();
   const bool big = s_misc[CM_CLASS + 6] != 0;
-  if (!big) {
+  const bool defer = big && !BIG;  // uniform over the CTA
+  if (BIG && big) {
+    // sensors beyond kWarpStage pixels, one at a time with the whole CTA;
+    // the warps' slices are free until the work loop below
+    uint32_t* fired = (uint32_t*)S.warps;
+    for (uint32_t j = 0; j < s_misc[CM_CLASS + 6]; ++j) {
+      const uint32_t s = S.list[6 * kMaxSensors + j];
+      const uint32_t a = s_soff[s], n = s_soff[s + 1] - a;
+      const uint32_t nroot = cluster_sensor_grid<NT>(col, row, a, n, ncols, nrows, sensor_geo(geo, (int)s), out, fired,
+                                                     fired + kBigCells / 32, fired + kBigCells / 16, S.scan, gscr, bad);
+      if (tid == 0) s_cnt[s] = nroot;
+    }
+    __syncthreads();
+  }
+  if (!defer) {
     // the largest sensors, one at a time on warp 0 (its slice stages them)
     if (warp == 0) {
       for (uint32_t j = 0; j < s_misc[CM_CLASS + 5]; ++j) {
@@ -651,10 +782,15 @@ __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsV
     }
   }
   if (__any_sync(kFull, bad) && lane == 0) atomicOr(&s_misc[CM_STATUS], VELO_EV_BAD_PIXEL);
-  if (__syncthreads_or(big)) {  // a sensor beyond the staging capacity
+  if (__syncthreads_or(defer)) {  // a sensor beyond the warp paths
     if (tid == 0) {
-      wk.rec[e] = EventRec{0, 0, 0, VELO_EV_OVERFLOW | s_misc[CM_STATUS], 0, 0, gbase, 0};
-      atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+      if (wk.big_scratch) {
+        const uint32_t pos = atomicAdd(&wk.cnt->queue_len[kBigSensorQueue], 1u);
+        wk.queue[kBigSensorQueue][pos] = e;
+      } else {
+        wk.rec[e] = EventRec{0, 0, 0, VELO_EV_OVERFLOW | s_misc[CM_STATUS], 0, 0, gbase, 0};
+        atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+      }
     }
     return false;
   }
@@ -700,6 +836,23 @@ __host__ __device__ inline ClusterLayout cluster_layout(int n_threads) {
 
 uint32_t cluster_smem_bytes(int n_threads) { return cluster_layout(n_threads).total; }
 
+// Queues a clustered event for the first tracking class that holds its H
+// hits; beyond every class, for the global-memory pass if there is one.
+__device__ inline void queue_event(const WorkView& wk, uint32_t e, uint32_t gbase, uint32_t H, uint32_t st) {
+  int cls = 0;
+  while (cls < wk.n_classes && H > wk.class_maxh[cls]) ++cls;
+  int q = cls;
+  if (cls >= wk.n_classes) q = (wk.huge_scratch && H <= kHugeMaxH) ? kHugeQueue : -1;
+  if (q < 0) {
+    atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
+    wk.rec[e] = EventRec{0, 0, 0, st | VELO_EV_OVERFLOW, 0, 0, gbase, 0};
+  } else {
+    wk.rec[e] = EventRec{0, 0, H, st, 0, 0, gbase, 0};
+    const uint32_t pos = atomicAdd(&wk.cnt->queue_len[q], 1u);
+    wk.queue[q][pos] = e;
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
                                                      WorkView wk) {
@@ -709,26 +862,45 @@ __global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometr
                       (uint32_t*)(smem + L.scan), (uint8_t*)(smem + L.lists), smem + L.warps};
   for (uint32_t e = blockIdx.x; e < ev.n_events; e += gridDim.x) {
     uint32_t H = 0, st = 0;
-    if (!cluster_event<NT>(geo, ev, wk, e, S, H, st)) continue;
-    if (threadIdx.x == 0) {
-      const uint32_t gbase = ev.sensor_off[(size_t)e * geo->n_sensors];
-      int cls = 0;
-      while (cls < wk.n_classes && H > wk.class_maxh[cls]) ++cls;
-      if (cls >= wk.n_classes) {
-        atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);
-        wk.rec[e] = EventRec{0, 0, 0, st | VELO_EV_OVERFLOW, 0, 0, gbase, 0};
-      } else {
-        wk.rec[e] = EventRec{0, 0, H, st, 0, 0, gbase, 0};
-        const uint32_t pos = atomicAdd(&wk.cnt->queue_len[cls], 1u);
-        wk.queue[cls][pos] = e;
-      }
-    }
+    if (!cluster_event<NT, false>(geo, ev, wk, e, S, H, st, nullptr)) continue;
+    if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, st);
   }
 }
 
+// Second pass: persistent CTAs take the events queued for a sensor beyond
+// kWarpStage pixels and cluster them whole, with such sensors on the grid
+// path (each CTA has its own global region).
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) cluster_big_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
+                                                            WorkView wk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_ticket;
+  const ClusterLayout L = cluster_layout(NT);
+  const ClusterSmem S{(uint32_t*)(smem + L.soff), (uint32_t*)(smem + L.ccnt), (uint32_t*)(smem + L.misc),
+                      (uint32_t*)(smem + L.scan), (uint8_t*)(smem + L.lists), smem + L.warps};
+  unsigned char* gscr = wk.big_scratch + (size_t)blockIdx.x * kBigScratchBytes;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&wk.cnt->ticket[kBigSensorQueue], 1u);
+    __syncthreads();
+    const uint32_t q = s_ticket;
+    if (q >= *(volatile uint32_t*)&wk.cnt->queue_len[kBigSensorQueue]) break;
+    const uint32_t e = wk.queue[kBigSensorQueue][q];
+    uint32_t H = 0, st = 0;
+    if (!cluster_event<NT, true>(geo, ev, wk, e, S, H, st, gscr)) continue;
+    if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, st);
+  }
+}
+
+static_assert(3u * (kBigCells / 32) * 4u <= cluster_warps_bytes(kClusterThreads / 32),
+              "the grid path's bitmaps fit the warps' slices");
+
 cudaError_t cluster_set_smem_limit(int n_threads) {
   if (n_threads != kClusterThreads) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(cluster_kernel<kClusterThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(cluster_kernel<kClusterThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)cluster_smem_bytes(n_threads));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(cluster_big_kernel<kClusterThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)cluster_smem_bytes(n_threads));
 }
 
@@ -738,6 +910,12 @@ cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const W
   if (n_threads != kClusterThreads) return cudaErrorInvalidValue;
   const unsigned grid = ev.n_events < 65535u * 4 ? ev.n_events : 65535u * 4;
   cluster_kernel<kClusterThreads><<<grid, kClusterThreads, cluster_smem_bytes(n_threads), st>>>(geo, ev, wk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_big(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, cudaStream_t st) {
+  if (ev.n_events == 0 || !wk.big_scratch) return cudaSuccess;
+  cluster_big_kernel<kClusterThreads><<<kBigCtas, kClusterThreads, cluster_smem_bytes(kClusterThreads), st>>>(geo, ev, wk);
   return cudaGetLastError();
 }
 

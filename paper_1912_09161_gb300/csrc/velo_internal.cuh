@@ -15,7 +15,9 @@ constexpr int kNB = 256;                         // phi bins per module (a power
 constexpr uint32_t kNone16 = 0xFFFFu;
 constexpr int kMaxClasses = 4;                   // shared-memory classes of the tracking kernel
 constexpr int kRetryQueue = kMaxClasses;         // events that ran out of storage in their class
-constexpr int kQueues = kMaxClasses + 1;
+constexpr int kHugeQueue = kMaxClasses + 1;      // events beyond every shared-memory class (global-memory pass)
+constexpr int kBigSensorQueue = kMaxClasses + 2; // events with a sensor beyond the warp paths (second clustering pass)
+constexpr int kQueues = kMaxClasses + 3;
 constexpr int kMlpIn = 10, kMlpH = 32;
 constexpr int kMlpParams = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1441
 constexpr int kMlpNormOffset = (2 * kMlpParams + 15) & ~15;  // byte offset of the float normalisation
@@ -49,6 +51,20 @@ struct DevParams {
   float mlp_logit_threshold;  // keep a candidate when its classifier logit >= this
   float phi_window;  // half-width of the phi window in pseudo-angle units (>= atan(tol))
 };
+
+// Global-memory slow paths.  Sensors of more than kWarpStage raw pixels are
+// clustered by a second clustering pass (kBigCtas CTAs) over a 256 x 256
+// occupancy bitmap with union-find in a per-CTA global region; events beyond
+// every shared-memory tracking class run in a global-memory instance of the
+// whole-event tracking kernel (kHugeCtas CTAs, kHugeMaxH hits: canonical ids
+// are 16-bit).
+constexpr uint32_t kWarpStage = 1000;    // raw pixels of the largest sensor the warp paths take
+constexpr int kBigCtas = 16;
+constexpr uint32_t kBigCells = 256 * 256;   // sensor cells (col * 256 + row)
+constexpr uint32_t kBigMaxRoots = 128 * 128; // components of an 8-connected 256 x 256 sensor, at most
+constexpr size_t kBigScratchBytes = 4ull * kBigCells + 4ull * kBigMaxRoots + 8ull * kBigMaxRoots;
+constexpr int kHugeCtas = 8;
+constexpr uint32_t kHugeMaxH = 65504;
 
 // Per-event working capacities of one tracking-kernel class.
 struct Caps {
@@ -124,6 +140,10 @@ struct WorkView {
   // max_tracks candidates per CTA, one region per CTA of the class
   uint16_t* trk_hits[kMaxClasses];
   RingScratch ring;
+  // slow paths (null: not available, such events are flagged VELO_EV_OVERFLOW)
+  unsigned char* big_scratch;    // [kBigCtas][kBigScratchBytes]
+  unsigned char* huge_scratch;   // [kHugeCtas][huge_bytes]: whole-event layout, then hit slots
+  uint64_t huge_bytes;
   uint32_t cap_tracks, cap_hits;
   // scratch clusters (canonical, at the event's pixel base), may be null
   float* cl_x;
@@ -140,6 +160,8 @@ uint32_t cluster_smem_bytes(int n_threads);
 cudaError_t cluster_set_smem_limit(int n_threads);
 cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, int n_threads,
                            cudaStream_t st);
+// Second clustering pass over the events queued for a sensor beyond kWarpStage pixels.
+cudaError_t launch_cluster_big(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, cudaStream_t st);
 
 // Tracking kernel (velo_track.cu).
 Caps make_caps(uint32_t smem_budget, uint32_t n_modules, int n_threads);
@@ -147,6 +169,12 @@ cudaError_t track_set_smem_limit(int n_threads, int bytes);
 cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm);
 cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                          const Caps& caps, int cls, int queue, int n_threads, int n_ctas, cudaStream_t st);
+// Global-memory pass of the whole-event kernel over the huge queue (capacities
+// huge_caps(n_modules); working memory in wk.huge_scratch).
+Caps huge_caps(uint32_t n_modules);
+size_t huge_region_bytes(uint32_t n_modules);
+cudaError_t launch_track_huge(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
+                              int cls, cudaStream_t st);
 
 // Module-window tracking kernel (velo_track_ring.cu).
 uint32_t ring_smem_bytes();

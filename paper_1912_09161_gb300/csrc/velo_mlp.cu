@@ -156,15 +156,17 @@ __global__ void __launch_bounds__(kGradThreads)
 __global__ void mlp_reduce_kernel(const float* __restrict__ partial, uint32_t nblk, float* __restrict__ grad,
                                   int adam, float* __restrict__ master, float* __restrict__ m1,
                                   float* __restrict__ m2, uint16_t* __restrict__ wbf, float lr, float b1, float b2,
-                                  float c1, float c2, float eps) {
+                                  float omb1, float omb2, float c1, float c2, float eps) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= kPartial) return;
   float g = 0.0f;
   for (uint32_t b = 0; b < nblk; ++b) g += partial[(size_t)b * kPartial + p];
   grad[p] = g;
   if (!adam || p >= kMlpParams) return;
-  const float m = b1 * m1[p] + (1.0f - b1) * g;
-  const float v = b2 * m2[p] + (1.0f - b2) * g * g;
+  // omb1 = 1 - beta1 and omb2 = 1 - beta2, rounded once from double (1.0f -
+  // 0.999f would be 1.3e-5 off 0.001)
+  const float m = b1 * m1[p] + omb1 * g;
+  const float v = b2 * m2[p] + omb2 * g * g;
   m1[p] = m;
   m2[p] = v;
   const float w = master[p] - lr * (m * c1) / (sqrtf(v * c2) + eps);
@@ -267,7 +269,8 @@ int velo_mlp_step(velo_mlp_trainer* t, const float* features, const float* label
   const float c2 = (float)(1.0 / (1.0 - pow(b2, (double)t->step)));
   const uint32_t nblk = (n + kGradThreads - 1) / kGradThreads;
   mlp_reduce_kernel<<<(kPartial + 255) / 256, 256, 0, st>>>(t->partial, nblk, t->grad, 1, t->master, t->m1, t->m2,
-                                                             t->wbf, lr, (float)b1, (float)b2, c1, c2, 1e-8f);
+                                                             t->wbf, lr, (float)b1, (float)b2, (float)(1.0 - b1),
+                                                             (float)(1.0 - b2), c1, c2, 1e-8f);
   MLP_TRY(cudaGetLastError());
   return VELO_OK;
 }
@@ -280,7 +283,7 @@ int velo_mlp_gradient(velo_mlp_trainer* t, const float* features, const float* l
   if (rc != VELO_OK) return rc;
   const uint32_t nblk = (n + kGradThreads - 1) / kGradThreads;
   mlp_reduce_kernel<<<(kPartial + 255) / 256, 256, 0, st>>>(t->partial, nblk, t->grad, 0, nullptr, nullptr, nullptr,
-                                                             nullptr, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
+                                                             nullptr, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f);
   MLP_TRY(cudaGetLastError());
   float buf[kPartial];
   MLP_TRY(cudaMemcpyAsync(buf, t->grad, sizeof(buf), cudaMemcpyDeviceToHost, st));

@@ -113,6 +113,17 @@ bool geometry_valid(const velo_geometry* g) {
   return true;
 }
 
+// Writes the geometry into the static array.  The geometry travels as this
+// kernel's parameter (a copy taken at launch), so the call issues no copy
+// from pageable host memory: nothing waits for the stream, and no host
+// buffer has to outlive the call.
+__global__ void static_geometry_kernel(const __grid_constant__ DevGeometry g, DevGeometry* __restrict__ dst) {
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&g);
+  uint32_t* out = reinterpret_cast<uint32_t*>(dst);
+  for (uint32_t i = threadIdx.x; i < sizeof(DevGeometry) / 4; i += blockDim.x) out[i] = src[i];
+}
+static_assert(sizeof(DevGeometry) % 4 == 0, "geometry copied by words");
+
 // Exclusive scan of the per-event cluster counts (one block).
 __global__ void static_scan_kernel(uint32_t n_events, const EventRec* rec, uint32_t* cluster_off, uint32_t* totals,
                                    uint32_t cap_clusters, const Counters* cnt) {
@@ -219,7 +230,8 @@ extern "C" int velo_cluster_static(const velo_geometry* geometry, const velo_eve
   wk.cap_pixels = kStaticMaxPixels;
   const EventsView ev{E, events->sensor_off, events->col, events->row};
 
-  cudaError_t e = cudaMemcpyAsync(b + kOffGeo, &g, sizeof(g), cudaMemcpyHostToDevice, st);
+  static_geometry_kernel<<<1, 256, 0, st>>>(g, (DevGeometry*)(b + kOffGeo));
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(wk.cnt, 0, sizeof(Counters), st);
   if (e == cudaSuccess) e = launch_cluster((const DevGeometry*)(b + kOffGeo), ev, wk, 256, st);
   if (e == cudaSuccess) {
@@ -233,8 +245,6 @@ extern "C" int velo_cluster_static(const velo_geometry* geometry, const velo_eve
                                              out->cl_key, out->event_status);
     e = cudaGetLastError();
   }
-  // The host copy of the geometry is pageable: the copy above has been staged
-  // before cudaMemcpyAsync returned, so `g` may go out of scope.
   if (e != cudaSuccess) return report(VELO_ERR_CUDA, "velo_cluster_static: %s", cudaGetErrorString(e));
   return VELO_OK;
 }

@@ -211,13 +211,18 @@ __device__ __forceinline__ bool phase_b(int i, uint32_t kb0, uint32_t kb1, const
   return ovf;
 }
 
-template <int NT, int GA, int GB>
-__global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry* __restrict__ geo, DevParams par,
-                                                   EventsView ev, WorkView wk, Caps caps, int cls, int qi) {
-  extern __shared__ __align__(16) unsigned char smem[];
+// GLOBAL: the global-memory pass for events beyond every shared-memory
+// class; the same layout lives in the CTA's region of wk.huge_scratch, with
+// the hit slots after it.
+template <int NT, int GA, int GB, bool GLOBAL>
+__global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const DevGeometry* __restrict__ geo,
+                                                                        DevParams par, EventsView ev, WorkView wk,
+                                                                        Caps caps, int cls, int qi) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
   constexpr int NW = NT / 32;
   const uint32_t nm = (uint32_t)geo->n_modules;
   const Layout L = make_layout(caps.maxh, caps.maxt, nm, NW);
+  unsigned char* smem = GLOBAL ? wk.huge_scratch + (size_t)blockIdx.x * wk.huge_bytes : smem_dyn;
   float* s_z = (float*)(smem + L.z);
   uint16_t* s_cb = (uint16_t*)(smem + L.cb);
   uint16_t* s_bins = (uint16_t*)(smem + L.bins);
@@ -238,7 +243,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) track_kernel(const DevGeometry*
   uint8_t* t_n = (uint8_t*)(smem + L.t_n);
   uint8_t* t_skip = (uint8_t*)(smem + L.t_skip);
   // this CTA's hit slots: kMaxModules positions per candidate
-  uint16_t* trk = wk.trk_hits[cls] + (size_t)blockIdx.x * caps.maxt * kMaxModules;
+  uint16_t* trk = GLOBAL ? (uint16_t*)(smem + ((L.total + 255u) & ~255u))
+                         : wk.trk_hits[cls] + (size_t)blockIdx.x * caps.maxt * kMaxModules;
   uint32_t* t_key = (uint32_t*)t_x;    // after the rounds
   uint32_t* t_rank = (uint32_t*)t_y;
   uint32_t* t_hoff = (uint32_t*)t_z;   // indexed by rank
@@ -548,25 +554,47 @@ constexpr int kGroupB = 4;
 cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                          const Caps& caps, int cls, int queue, int n_threads, int n_ctas, cudaStream_t st) {
   switch (n_threads) {
-    case 128: track_kernel<128, kGroupA, kGroupB><<<n_ctas, 128, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
-    case 256: track_kernel<256, kGroupA, kGroupB><<<n_ctas, 256, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
+    case 128: track_kernel<128, kGroupA, kGroupB, false><<<n_ctas, 128, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
+    case 256: track_kernel<256, kGroupA, kGroupB, false><<<n_ctas, 256, caps.smem, st>>>(geo, par, ev, wk, caps, cls, queue); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
+Caps huge_caps(uint32_t n_modules) {
+  Caps c{};
+  c.maxh = kHugeMaxH;
+  c.maxt = caps_maxt(kHugeMaxH);
+  c.smem = make_layout(c.maxh, c.maxt, n_modules, 256 / 32).total;
+  return c;
+}
+
+size_t huge_region_bytes(uint32_t n_modules) {
+  const Caps c = huge_caps(n_modules);
+  const size_t layout = ((size_t)c.smem + 255) & ~(size_t)255;
+  return (layout + (size_t)c.maxt * kMaxModules * sizeof(uint16_t) + 255) & ~(size_t)255;
+}
+
+cudaError_t launch_track_huge(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
+                              int cls, cudaStream_t st) {
+  if (ev.n_events == 0 || !wk.huge_scratch) return cudaSuccess;
+  const Caps c = huge_caps((uint32_t)kMaxModules);  // layout of the largest geometry: a superset
+  track_kernel<256, kGroupA, kGroupB, true><<<kHugeCtas, 256, 0, st>>>(geo, par, ev, wk, c, cls, kHugeQueue);
+  return cudaGetLastError();
+}
+
 cudaError_t track_set_smem_limit(int n_threads, int bytes) {
   switch (n_threads) {
-    case 128: return cudaFuncSetAttribute(track_kernel<128, kGroupA, kGroupB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    case 256: return cudaFuncSetAttribute(track_kernel<256, kGroupA, kGroupB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 128: return cudaFuncSetAttribute(track_kernel<128, kGroupA, kGroupB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    case 256: return cudaFuncSetAttribute(track_kernel<256, kGroupA, kGroupB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm) {
   switch (n_threads) {
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<128, kGroupA, kGroupB>, 128, smem);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<256, kGroupA, kGroupB>, 256, smem);
+    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<128, kGroupA, kGroupB, false>, 128, smem);
+    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, track_kernel<256, kGroupA, kGroupB, false>, 256, smem);
   }
   return cudaErrorInvalidValue;
 }

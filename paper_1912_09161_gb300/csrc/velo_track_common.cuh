@@ -84,12 +84,16 @@ __device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* l
 }
 
 // An event that runs out of storage in its class goes to the retry queue,
-// which the largest class drains after all classes finish; running out there
-// marks the event.
+// which the largest shared-memory class drains after all classes finish;
+// running out there sends it to the global-memory pass (when the handle has
+// one), and running out in that pass marks the event.
 __device__ inline void defer_or_fail(const WorkView& wk, int queue, uint32_t e, uint32_t gbase, uint32_t H, uint32_t status) {
-  if (queue != kRetryQueue) {
-    const uint32_t pos = atomicAdd(&wk.cnt->queue_len[kRetryQueue], 1u);
-    wk.queue[kRetryQueue][pos] = e;
+  int next = -1;
+  if (queue < kRetryQueue) next = kRetryQueue;
+  else if (queue == kRetryQueue && wk.huge_scratch && H <= kHugeMaxH) next = kHugeQueue;
+  if (next >= 0) {
+    const uint32_t pos = atomicAdd(&wk.cnt->queue_len[next], 1u);
+    wk.queue[next][pos] = e;
   } else {
     wk.rec[e] = EventRec{0, 0, H, status | VELO_EV_OVERFLOW, 0, 0, gbase, 0};
     atomicOr(&wk.cnt->error, (uint32_t)kErrCapacity);

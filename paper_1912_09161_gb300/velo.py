@@ -24,7 +24,7 @@ VELO_OK, VELO_ERR_INPUT, VELO_ERR_CAPACITY, VELO_ERR_NOMEM, VELO_ERR_TIMEOUT, VE
 EV_BAD_PIXEL, EV_BAD_OFFSETS, EV_OVERFLOW, EV_TRUNCATED = 1, 2, 4, 8
 CFG_CLUSTERS = 1
 
-EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_set_params", "velo_reconstruct",
+EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_required", "velo_set_params", "velo_reconstruct",
             "velo_sync_status", "velo_reconstruct_host", "velo_describe", "velo_set_timing", "velo_get_stats", "velo_cluster_static",
             "velo_set_schedule", "velo_get_schedule", "velo_autotune", "velo_set_graphs", "velo_set_mlp",
             "velo_mlp_create", "velo_mlp_destroy", "velo_mlp_step", "velo_mlp_gradient", "velo_mlp_logits",
@@ -132,6 +132,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.velo_destroy.argtypes = [vp]
     lib.velo_destroy.restype = None
     lib.velo_required_bytes.argtypes = [P(velo_geometry), P(velo_config), P(ctypes.c_size_t)]
+    lib.velo_required.argtypes = [vp, P(velo_events), P(ctypes.c_size_t)]
+    lib.velo_required.restype = ctypes.c_int
     lib.velo_set_params.argtypes = [vp, P(velo_params)]
     lib.velo_reconstruct.argtypes = [vp, P(velo_events), P(velo_output), vp]
     lib.velo_sync_status.argtypes = [vp, vp]
@@ -376,6 +378,16 @@ def velo_required_bytes(geometry, config: velo_config) -> int:
     return int(n.value)
 
 
+def velo_required(h, events: DeviceEvents) -> tuple[int, int]:
+    """(status, bytes): working storage a call on this batch needs; status is
+    VELO_ERR_NOMEM when the batch exceeds the handle's capacities."""
+    n = ctypes.c_size_t()
+    rc = int(load_library(False).velo_required(h, ctypes.byref(events.to_c()), ctypes.byref(n)))
+    if rc not in (VELO_OK, VELO_ERR_NOMEM):
+        _check(rc, "velo_required")
+    return rc, int(n.value)
+
+
 def velo_set_params(h, params: Params):
     _check(load_library(False).velo_set_params(h, ctypes.byref(params.to_c())), "velo_set_params")
 
@@ -448,15 +460,18 @@ def velo_describe(h) -> dict:
     return json.loads(buf.value.decode())
 
 
-def velo_cluster_static(geometry, events: DeviceEvents, out: "DeviceOutput", stream: int = 0):
+def velo_cluster_static(geometry, events: DeviceEvents, out: "DeviceOutput", stream: int = 0,
+                        n_pixels: int | None = None):
     """Clusters a batch without allocating device memory (see velo.h).
 
-    ``out`` supplies cluster_off, cl_x, cl_y, cl_key, event_status and totals."""
+    ``out`` supplies cluster_off, cl_x, cl_y, cl_key, event_status and totals;
+    ``n_pixels`` defaults to the length of the pixel arrays."""
     lib = load_library()
     gc, keep = _geometry_c(geometry)
     oc = velo_cluster_output(out.cap_clusters, _ptr(out.cluster_off), _ptr(out.cl_x), _ptr(out.cl_y),
                              _ptr(out.cl_key), _ptr(out.event_status), _ptr(out.totals))
-    n_pixels = int(events.col.numel())
+    if n_pixels is None:
+        n_pixels = int(events.col.numel())
     _check(lib.velo_cluster_static(ctypes.byref(gc), ctypes.byref(events.to_c()), n_pixels, ctypes.byref(oc),
                                    ctypes.c_void_p(stream)), "velo_cluster_static")
     del keep

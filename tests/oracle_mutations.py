@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """Sensitivity of the oracle pins: plants one plausible mistake at a time in
-a temporary copy of the oracle (the C reconstruction and the Python
-classifier) and runs the oracle pins (tests/test_oracle_*.py) against it.  Every mutant must fail at least one
+a temporary copy of the oracle (the C reconstruction, the Python classifier
+with its Adam optimiser, and the truth matching) and runs the oracle pins
+(tests/test_oracle_*.py) against it.  Every mutant must fail at least one
 pin, except the ones listed as equivalent (no observable effect).
 
     python tests/oracle_mutations.py        # a few minutes on the CPU
@@ -84,6 +85,14 @@ MUTANTS_MLP = [
      "    return ((np.asarray(f, np.float32) - mean.astype(np.float32)) / istd.astype(np.float32))"),
     ("first-layer sum order reversed", "        for i in range(N_IN):\n            acc = acc + W1[j, i] * x[:, i]",
      "        for i in reversed(range(N_IN)):\n            acc = acc + W1[j, i] * x[:, i]"),
+    # the optimiser of the training step
+    ("Adam betas swapped", "self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps",
+     "self.lr, self.b1, self.b2, self.eps = lr, b2, b1, eps"),
+    ("Adam first moment not bias-corrected", "        mh = self.m / (1 - self.b1 ** self.t)", "        mh = self.m"),
+    ("Adam second moment not bias-corrected", "        vh = self.v / (1 - self.b2 ** self.t)", "        vh = self.v"),
+    ("Adam eps inside the square root", "self.w -= self.lr * mh / (np.sqrt(vh) + self.eps)",
+     "self.w -= self.lr * mh / np.sqrt(vh + self.eps)"),
+    ("Adam second moment of |g|", "(1 - self.b2) * g * g", "(1 - self.b2) * np.abs(g)"),
 ]
 
 # (name, text in oracle/metrics.py, replacement): truth matching

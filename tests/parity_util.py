@@ -3,15 +3,16 @@
 State tolerance (fitted states, single precision): |g - o| <= 1e-5 * max(|o|, floor),
 with per-quantity floors so that values that cross zero (x, y at the beamline
 are ~0.04 mm) are compared on the scale of the quantity, not of the value:
-x, y 1e-2 mm; z 1 mm; slopes 1e-3; covariances 1e-5 * the matching
-variance scale; chi2 1.  Both sides evaluate the same single-precision
+x, y 1e-3 mm; z 1e-2 mm; slopes 1e-5; covariances 1e-5 * the matching
+variance scale; chi2 1e-3.  Both sides evaluate the same single-precision
 operations in the same order, so agreement is expected to be exact; the
-tolerance is the contract.
+tolerance is the contract, and ``assert_parity`` also counts the states that
+are bit-identical.
 """
 import numpy as np
 
 REL = 1e-5
-FLOORS = np.array([1e-2, 1e-2, 1.0, 1e-3, 1e-3, 0, 0, 0, 0, 0, 0, 1.0, 0.0], np.float64)
+FLOORS = np.array([1e-3, 1e-3, 1e-2, 1e-5, 1e-5, 0, 0, 0, 0, 0, 0, 1e-3, 0.0], np.float64)
 
 
 def state_tolerance(o: np.ndarray) -> np.ndarray:
@@ -43,8 +44,9 @@ def compare_states(g: np.ndarray, o: np.ndarray, cols=range(12)):
     return ok, exact, worst
 
 
-def assert_parity(gpu, orc, events_idx=None, check_clusters=True, check_states=True):
-    """Bit-exact clusters and track hit lists; states within tolerance.
+def assert_parity(gpu, orc, events_idx=None, check_clusters=True, check_states=True, exact_states=True):
+    """Bit-exact clusters and track hit lists; states within tolerance and,
+    with ``exact_states`` (the default), bit-identical as well.
 
     ``gpu`` is a HostResult, ``orc`` an OracleResult over the same events (or
     over a subset given by ``events_idx`` -- GPU event indices in order)."""
@@ -71,4 +73,6 @@ def assert_parity(gpu, orc, events_idx=None, check_clusters=True, check_states=T
             o0, o1 = int(orc.track_off[k]), int(orc.track_off[k + 1])
             ok, exact, worst = compare_states(gpu.states[g0:g1], orc.states[o0:o1])
             assert ok, f"event {e}: states outside tolerance (worst {worst:.3g} x tol)"
+            if exact_states:
+                assert exact == g1 - g0, f"event {e}: {g1 - g0 - exact} states not bit-identical (worst {worst:.3g} x tol)"
             assert np.array_equal(gpu.ndof[g0:g1].astype(np.uint32), orc.ndof[o0:o1]), f"event {e}: ndof"

@@ -68,10 +68,52 @@ def test_gradient_matches_oracle(env, train_set):
     g, loss = tr.gradient(torch.from_numpy(f[idx]).cuda(), torch.from_numpy(y[idx]).cuda())
     x = M.bf16_round(M.normalise(f[idx], mean, istd)).astype(np.float64)
     loss64, g64 = M.backward64(x, y[idx], M.bf16_round(p0).astype(np.float64))
-    rel = np.linalg.norm(g - g64) / np.linalg.norm(g64)
-    cos = float(g @ g64 / (np.linalg.norm(g) * np.linalg.norm(g64)))
-    assert rel < 2e-2 and cos > 0.9995, (rel, cos)
+    # every one of the 1441 entries: 1e-2 relative, 1e-3 of the largest
+    # entry absolute (the GPU rounds the activations to BF16 in the forward
+    # pass; the float64 reference does not)
+    tol = 1e-2 * np.abs(g64) + 1e-3 * np.max(np.abs(g64))
+    bad = np.nonzero(np.abs(g - g64) > tol)[0]
+    assert bad.size == 0, [(int(i), float(g[i]), float(g64[i])) for i in bad[:5]]
     assert loss == pytest.approx(loss64, rel=1e-2)
+    tr.close()
+
+
+def test_adam_step_matches_oracle(env, train_set):
+    """Four training steps on fixed batches.  Before each step the batch
+    gradient is read back (velo_mlp_gradient runs the same deterministic
+    kernels as the step); the oracle's Adam, started from the GPU's previous
+    master weights and moments, applies it; the GPU's new master weights,
+    both moments and the BF16 copy must match element by element.  The float32
+    update against the float64 optimiser: 1e-6 of the terms' magnitudes (a
+    few float32 roundings).  The gradient itself is checked against float64
+    backpropagation in the test above."""
+    V, ghost, torch, geom = env
+    f, y = train_set
+    mean, istd = ghost.standardisation(f)
+    p0 = ghost.init_params(11)
+    tr = ghost.Trainer(p0, mean, istd, 1024)
+    prev = tr.state()
+    rng = np.random.default_rng(12)
+    lr = 1e-3
+    for k in range(4):
+        idx = rng.choice(len(y), 1024, replace=False)
+        fd, yd = torch.from_numpy(f[idx]).cuda(), torch.from_numpy(y[idx]).cuda()
+        g, _ = tr.gradient(fd, yd)
+        tr.step(fd, yd, lr)
+        st = tr.state()
+        assert st.step == k + 1
+        opt = M.Adam(prev.params.astype(np.float64), lr=lr)
+        opt.m, opt.v, opt.t = prev.m1.astype(np.float64), prev.m2.astype(np.float64), k
+        g64 = g.astype(np.float64)
+        opt.step(g64)
+        checks = (("m1", st.m1, opt.m, 0.9 * np.abs(prev.m1) + 0.1 * np.abs(g64)),
+                  ("m2", st.m2, opt.v, 0.999 * prev.m2 + 0.001 * g64 * g64),
+                  ("w", st.params, opt.w, np.abs(prev.params) + lr))
+        for name, got, want, scale in checks:
+            bad = np.nonzero(np.abs(got.astype(np.float64) - want) > 1e-6 * scale + 1e-30)[0]
+            assert bad.size == 0, (k, name, [(int(i), float(got[i]), float(want[i])) for i in bad[:4]])
+        assert np.array_equal(st.params_bf16, M.bf16_bits(st.params))
+        prev = st
     tr.close()
 
 

@@ -95,25 +95,120 @@ def test_edge_cases(V, geom):
     ev2[17] = [(int(c), int(r)) for c, r in rng.integers(0, 40, (600, 2))]
     lists.append(ev2)
     lists.append([[(int(c), int(r))] for c, r in rng.integers(0, 256, (ns, 2))])  # one pixel per sensor
-    ev4 = [[] for _ in range(ns)]                                           # beyond the per-sensor limit
+    ev4 = [[] for _ in range(ns)]                                           # beyond the warp paths (1,000 pixels)
     ev4[3] = [(int(c), int(r)) for c, r in rng.integers(0, 256, (1200, 2))]
     lists.append(ev4)
     ev = velo_synth.make_events(lists, ns)
     orc = oracle.reconstruct(geom, ev)
     res = _run(V, geom, ev)
     assert res.event_status[1] & 1 and orc.event_status[1] & 1
-    assert res.event_status[0] == 0 and res.event_status[2] == 0 and res.event_status[3] == 0
-    # a sensor of more than 1000 raw pixels is a documented capacity limit:
-    # that event alone is flagged and skipped, the others are unaffected
-    assert res.event_status[4] == 4 and res.track_off[5] == res.track_off[4]
-    assert res.cluster_off[5] == res.cluster_off[4]
-    sub = velo_synth.make_events(lists[:4], ns)
-    orc4 = oracle.reconstruct(geom, sub)
-    for e in range(4):
-        assert res.event_tracks(e) == orc4.event_tracks(e)
-        g0, g1 = int(res.cluster_off[e]), int(res.cluster_off[e + 1])
-        o0, o1 = int(orc4.cluster_off[e]), int(orc4.cluster_off[e + 1])
-        assert np.array_equal(res.cl_key[g0:g1], orc4.cl_key[o0:o1])
+    # every event, the one with a 1,200-pixel sensor included (second
+    # clustering pass), equals the oracle; nothing is skipped
+    assert list(res.event_status) == [0, 1, 0, 0, 0]
+    assert_parity(res, orc)
+
+
+def test_big_sensors(V, geom, cfg0_events):
+    """Sensors beyond the warp paths go to the second clustering pass: a full
+    sensor with every pixel repeated (one cluster of 65,536 pixels), a
+    checkerboard (16,384 single-pixel clusters, so the event also outgrows
+    every shared-memory tracking class), random fills of 30 % and 2 %, and
+    1,001 pixels, each on top of a nominal event; the oracle's flood fill
+    decides."""
+    ns = geom.n_sensors
+    rng = np.random.default_rng(5)
+
+    def nominal(e):
+        base = cfg0_events.subset(e, e + 1)
+        return [[(int(base.col[k]), int(base.row[k])) for k in range(int(base.sensor_off[s]), int(base.sensor_off[s + 1]))]
+                for s in range(ns)]
+
+    full = [(c, r) for c in range(256) for r in range(256)]
+    fills = [
+        (5, full + full[::7]),
+        (60, [(c, r) for c in range(0, 256, 2) for r in range(0, 256, 2)]),
+        (101, [(int(c), int(r)) for c, r in np.argwhere(rng.random((256, 256)) < 0.3)]),
+        (150, [(int(c), int(r)) for c, r in np.argwhere(rng.random((256, 256)) < 0.02)]),
+        (207, [(int(c), int(r)) for c, r in rng.integers(0, 256, (1001, 2))]),
+    ]
+    lists = []
+    for k, (s, px) in enumerate(fills):
+        ev = nominal(k)
+        order = rng.permutation(len(px))
+        ev[s] = ev[s] + [px[i] for i in order]
+        lists.append(ev)
+    ev = velo_synth.make_events(lists, ns)
+    orc = oracle.reconstruct(geom, ev, n_threads=NCPU)
+    assert int(orc.cluster_off[2] - orc.cluster_off[1]) > 16384
+    res = _run(V, geom, ev)
+    assert int(res.totals[3]) == 0 and np.all(res.event_status == 0)
+    assert_parity(res, orc)
+
+
+def test_huge_event(V, geom):
+    """Events of 80 and 120 pp vertices (more than 14,016 hits: beyond the
+    largest shared-memory tracking class) run in the global-memory pass and
+    equal the oracle."""
+    cfg = velo_synth.SynthConfig(n_events=2, seed=43, pileup_lo=80, pileup_hi=120, n_threads=2)
+    ev = velo_synth.generate(cfg)
+    orc = oracle.reconstruct(geom, ev, n_threads=NCPU)
+    assert np.all(np.diff(orc.cluster_off.astype(np.int64)) > 14016)
+    res = _run(V, geom, ev)
+    assert int(res.totals[3]) == 0 and np.all(res.event_status == 0)
+    assert_parity(res, orc)
+
+
+@pytest.mark.parametrize("n_modules", [3, 4])
+def test_fewest_modules(V, n_modules):
+    """Three modules: a single round (one seed, nothing to extend); four: a
+    seed and one extension.  Exact lines along the beam through every module,
+    and a second line two rows off in the last module (a forwarding choice)."""
+    g = hand_events.exact_geometry(n_modules=n_modules)
+    line = [(m, 50, 60) for m in range(n_modules - 1, -1, -1)]
+    ev = hand_events.pixel_events(g, [line, line + [(0, 50, 62)], [(m, 90, 20) for m in range(n_modules)]])
+    orc = oracle.reconstruct(g, ev)
+    assert orc.n_tracks == 3
+    for schedule in (None, (256, 0x10, 1)):
+        rec = V.Reconstructor(g, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, clusters=True)
+        try:
+            if schedule:
+                rec.set_schedule(*schedule)
+            res = rec.run(V.upload_events(ev), clusters=True, check=False)
+        finally:
+            rec.close()
+        assert_parity(res, orc)
+
+
+def test_seed_slope_cut_on_each_axis(V):
+    """Exact straight lines steep in y only, in x only (|t| = 0.47 > 0.4: no
+    seed) and mildly steep in y (0.31: one track), as in the oracle pin."""
+    g = hand_events.exact_geometry(spacing=8.0)
+    steep_y = [(5, 32, 160), (4, 32, 100), (3, 32, 40)]
+    steep_x = [(5, 160, 32), (4, 100, 32), (3, 40, 32)]
+    mild_y = [(5, 32, 140), (4, 32, 100), (3, 32, 60)]
+    ev = hand_events.pixel_events(g, [steep_y, steep_x, mild_y])
+    p = oracle.Params(tan_phi_tol=0.3)
+    orc = oracle.reconstruct(g, ev, p)
+    assert [len(orc.event_tracks(e)) for e in range(3)] == [0, 0, 1]
+    res = _run(V, g, ev, _gpu_params(p))
+    assert_parity(res, orc)
+
+
+def test_reconstruct_host_matches_oracle(V, geom, cfg0_events, cfg0_oracle):
+    """The host-buffer entry point (copies in, reconstruction, copies out)
+    gives the oracle's clusters, tracks and states."""
+    ev = cfg0_events
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, clusters=True)
+    try:
+        ct, ch, cc = V.suggested_caps(ev.n_events, ev.n_pixels)
+        host = V.alloc_output(ev.n_events, ct, ch, cc, device="cpu")
+        rc = V.velo.velo_reconstruct_host(rec.handle, ev.n_events, np.ascontiguousarray(ev.sensor_off, np.uint32),
+                                          np.ascontiguousarray(ev.col, np.uint16), np.ascontiguousarray(ev.row, np.uint16),
+                                          host.to_c())
+    finally:
+        rec.close()
+    assert rc == V.velo.VELO_OK
+    assert_parity(host.to_host(ev.n_events), cfg0_oracle)
 
 
 @pytest.mark.parametrize("schedule", [None, (256, 0x10, 1)])
@@ -185,6 +280,37 @@ def test_config1_full_size_sampled(V, geom):
     rng = np.random.default_rng(7)
     sample = np.sort(rng.choice(ev.n_events, 200, replace=False))
     sample = np.unique(np.concatenate([sample, [0, ev.n_events - 1]]))
+    for e in sample:
+        orc = oracle.reconstruct(geom, ev.subset(int(e), int(e) + 1))
+        assert_parity(res, orc, events_idx=[int(e)])
+
+
+def test_config2_full_size_sampled(V, geom):
+    """The 50,000-event uneven batch (pileup uniform in [1, 20]) in the
+    benchmark's launch configuration (autotuned schedule, CUDA-graph replay on
+    a side stream); the oracle recomputes about 200 sampled events one by one,
+    the smallest and largest events included."""
+    import torch
+    ev = velo_synth.generate(velo_synth.config(2))
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, clusters=True)
+    try:
+        d = V.upload_events(ev)
+        ct, ch, cc = V.suggested_caps(ev.n_events, ev.n_pixels)
+        out = V.alloc_output(ev.n_events, ct, ch, cc)
+        stream = torch.cuda.Stream()
+        rec.autotune(d, out, stream.cuda_stream)
+        rec.set_graphs(True)
+        for _ in range(2):
+            rec.reconstruct(d, out, stream.cuda_stream)
+        assert rec.sync_status(stream.cuda_stream) == V.velo.VELO_OK
+        res = out.to_host(ev.n_events)
+    finally:
+        rec.close()
+    assert int(res.totals[3]) == 0 and np.all(res.event_status == 0)
+    ppe = ev.pixels_per_event()
+    rng = np.random.default_rng(8)
+    sample = np.sort(rng.choice(ev.n_events, 200, replace=False))
+    sample = np.unique(np.concatenate([sample, [0, ev.n_events - 1, int(np.argmin(ppe)), int(np.argmax(ppe))]]))
     for e in sample:
         orc = oracle.reconstruct(geom, ev.subset(int(e), int(e) + 1))
         assert_parity(res, orc, events_idx=[int(e)])

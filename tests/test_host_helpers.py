@@ -43,10 +43,19 @@ def test_latency_summary_percentiles():
     assert s["max_ms"] == 100.0
 
 
-def test_profile_traffic_needs_the_profiled_sources():
+def test_profile_traffic_needs_the_profiled_sources(tmp_path, monkeypatch):
+    """The bench reports the ncu DRAM traffic only while the summary's source
+    hash matches the kernel sources (a summary written here with the current
+    hash, then a changed set of sources)."""
+    import hashlib
     srcs = [os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", f) for f in bench.TRACK_SOURCES]
-    traffic = bench._profile_traffic(srcs)
-    assert traffic is not None and traffic > 0
+    h = hashlib.sha256()
+    for f in srcs:
+        h.update(open(f, "rb").read())
+    summary = tmp_path / "summary.md"
+    summary.write_text(f"kernel_source_sha256: {h.hexdigest()[:16]}\ntraffic_bytes_per_launch: 4.5e8\n")
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(summary))
+    assert bench._profile_traffic(srcs) == 4.5e8
     # any other set of sources (a kernel changed since the capture) reports none
     assert bench._profile_traffic(srcs[::-1]) is None
     assert bench._profile_traffic(srcs[:2]) is None

@@ -136,3 +136,41 @@ def test_bf16_forward_fixed_summation_order(layer):
     f, p = _hand_network(layer)
     out = M.forward_bf16(f, p, np.zeros(M.N_IN, np.float32), np.ones(M.N_IN, np.float32))
     assert out[0] == np.float32(1.0)
+
+
+def test_adam_matches_torch_optimizer():
+    """The oracle's Adam against torch.optim.Adam (an independent
+    implementation of the same update) over several steps of random
+    gradients, in float64: moments with bias correction, eps outside the
+    square root."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(21)
+    w0 = rng.normal(0, 0.3, 200)
+    opt = M.Adam(w0.copy(), lr=1e-2)
+    p = torch.tensor(w0.copy(), dtype=torch.float64, requires_grad=True)
+    ref = torch.optim.Adam([p], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for k in range(6):
+        # gradients over many decades, so that eps matters for the small ones
+        g = rng.normal(0, 1, 200) * 10.0 ** rng.uniform(-6, 0, 200)
+        w = opt.step(g)
+        p.grad = torch.tensor(g, dtype=torch.float64)
+        ref.step()
+        assert np.allclose(w, p.detach().numpy(), rtol=1e-12, atol=1e-15), k
+    st = ref.state[p]
+    assert np.allclose(opt.m, st["exp_avg"].numpy(), rtol=1e-12, atol=0)
+    assert np.allclose(opt.v, st["exp_avg_sq"].numpy(), rtol=1e-12, atol=0)
+
+
+def test_adam_constant_gradient_steps():
+    """With a constant gradient g the bias-corrected moments are exactly g
+    and g^2 at every step, so every update is lr * g / (|g| + eps): steps of
+    lr for large |g|, and of lr |g| / eps for |g| far below eps."""
+    g = np.array([2.0, -0.5, 1e-3, 1e-12, 0.0])
+    opt = M.Adam(np.zeros(5), lr=1e-3)
+    for t in range(1, 8):
+        before = opt.w.copy()
+        opt.step(g)
+        step = opt.w - before
+        want = -1e-3 * g / (np.abs(g) + 1e-8)
+        assert np.allclose(step, want, rtol=1e-9, atol=1e-18), t
+    assert opt.t == 7
