@@ -6,8 +6,9 @@ fitted states within the stated tolerance.  It shares no code with the GPU
 library and is imported only by ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py``.
 
-``velo_oracle.c`` holds the reconstruction; ``metrics.py`` the truth matching
-(section 3.1 definitions); ``mlp.py`` the ghost-classifier reference.
+``velo_oracle.c`` holds the reconstruction; ``pv_oracle.c`` the primary-vertex
+finding of section 2.3.1; ``metrics.py`` the truth matching (section 3.1
+definitions); ``mlp.py`` the ghost-classifier reference.
 """
 from __future__ import annotations
 
@@ -22,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "velo_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "pv_oracle.c"))
 _LIB = os.path.join(_HERE, "_velo_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -47,6 +49,13 @@ class _Params(ctypes.Structure):
                 ("max_scatter_3hit", ctypes.c_float), ("max_skipped", ctypes.c_uint32),
                 ("sigma_meas", ctypes.c_float), ("pt_nominal", ctypes.c_float),
                 ("ms_coeff", ctypes.c_float)]
+
+
+class _PVParams(ctypes.Structure):
+    _fields_ = [("z_min", ctypes.c_float), ("bin_width", ctypes.c_float), ("n_bins", ctypes.c_uint32),
+                ("window", ctypes.c_uint32), ("min_peak", ctypes.c_uint32), ("min_sep", ctypes.c_uint32),
+                ("max_r2", ctypes.c_float), ("chi2_cut", ctypes.c_float), ("n_iter", ctypes.c_uint32),
+                ("min_weight", ctypes.c_float), ("merge_dz", ctypes.c_float), ("max_vertices", ctypes.c_uint32)]
 
 
 class _Opts(ctypes.Structure):
@@ -76,9 +85,9 @@ CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast
 def build(force: bool = False) -> str:
     """Compiles ``velo_oracle.c`` (plain C, no FMA contraction)."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        if force or not os.path.exists(_LIB) or any(os.path.getmtime(_LIB) < os.path.getmtime(f) for f in _SRCS):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+            subprocess.check_call(["gcc", *CFLAGS, *_SRCS, "-o", tmp, "-lm"])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -96,6 +105,9 @@ def _load():
         lib.oracle_fit.argtypes = [_P(_Geo), _P(_Params), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                    ctypes.c_void_p]
+        lib.oracle_pv.argtypes = [_P(_PVParams), ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_pv.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -215,3 +227,67 @@ def fit(geom, x, y, module, params: Params | None = None):
                    len(x), st.ctypes.data, nd.ctypes.data)
     del keep
     return st, int(nd[0])
+
+
+PV_NOUT = 10
+PV_NAMES = ("x", "y", "z", "cxx", "cyy", "czz", "cxy", "cxz", "cyz", "weight")
+PV_STATUS_CAPACITY = 1
+
+
+@dataclasses.dataclass
+class PVParams:
+    """Primary-vertex finding parameters (mm); defaults: the frozen readings."""
+    z_min: float = -300.0
+    bin_width: float = 0.25
+    n_bins: int = 2400
+    window: int = 2
+    min_peak: int = 3
+    min_sep: int = 4
+    max_r2: float = 0.25
+    chi2_cut: float = 9.0
+    n_iter: int = 12
+    min_weight: float = 3.0
+    merge_dz: float = 1.0
+    max_vertices: int = 64
+
+    def _c(self) -> _PVParams:
+        p = _PVParams()
+        for name, _ in _PVParams._fields_:
+            setattr(p, name, getattr(self, name))
+        return p
+
+
+@dataclasses.dataclass
+class PVResult:
+    n_events: int
+    pv_off: np.ndarray     # uint32 [n_events + 1]
+    pv: np.ndarray         # float32 [n_vertices, 10]: x, y, z, cxx, cyy, czz, cxy, cxz, cyz, weight sum
+    status: np.ndarray     # uint32 [n_events]
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self.pv_off[-1])
+
+    def event_vertices(self, e: int) -> np.ndarray:
+        return self.pv[int(self.pv_off[e]):int(self.pv_off[e + 1])]
+
+
+def find_pvs(track_off, states, params: PVParams | None = None) -> PVResult:
+    """Primary vertices of every event from its tracks' beamline states
+    (``states``: [n_tracks, >= 11] float32, rows x, y, z, tx, ty, c00, c20,
+    c22, c11, c31, c33 as in the reconstruction's output)."""
+    lib = _load()
+    params = params or PVParams()
+    to = np.ascontiguousarray(track_off, np.uint32)
+    n_events = len(to) - 1
+    st = np.zeros((max(int(to[-1]), 1), NSTATE), np.float32)
+    src = np.asarray(states, np.float32)
+    st[:len(src), :min(src.shape[1], NSTATE)] = src[:, :NSTATE]
+    pv_off = np.zeros(n_events + 1, np.uint32)
+    pv = np.zeros((max(n_events * params.max_vertices, 1), PV_NOUT), np.float32)
+    status = np.zeros(max(n_events, 1), np.uint32)
+    rc = lib.oracle_pv(ctypes.byref(params._c()), n_events, to.ctypes.data, st.ctypes.data, pv_off.ctypes.data,
+                       pv.ctypes.data, status.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_pv: bad parameters")
+    return PVResult(n_events, pv_off, pv[:int(pv_off[-1])].copy(), status[:n_events].copy())

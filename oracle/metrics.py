@@ -123,3 +123,70 @@ def track_match(events, result) -> np.ndarray:
     """Matched particle per track of an ``OracleResult``-like object."""
     cl_label = cluster_labels(events, result.cluster_off, result.pix_cluster)
     return match_tracks(result.track_off, result.hit_off, result.hit_ids, result.cluster_off, cl_label)
+
+
+# --- primary vertices (section 3.1: a reconstructed PV matches a simulated
+# one when their distance is below five times the reconstructed PV's z
+# uncertainty) ---------------------------------------------------------------
+PV_MATCH_SIGMAS = 5.0
+PV_MIN_TRACKS = 4   # a simulated PV counts when it has this many reconstructible particles
+
+
+def pv_summary(events, pv_off, pv, min_tracks: int = PV_MIN_TRACKS) -> dict:
+    """PV efficiency, fake rate and resolution of reconstructed vertices
+    (``pv``: [n, >= 6] rows x, y, z, cxx, cyy, czz, ... per event range
+    ``pv_off``) against the generator's vertices.
+
+    Readings where the paper is silent: the distance is the z distance; a
+    simulated PV is reconstructible with at least ``min_tracks``
+    reconstructible particles; matching is one to one, taking compatible
+    (simulated, reconstructed) pairs in increasing distance; efficiency is
+    over reconstructible simulated PVs, the fake rate over reconstructed PVs
+    that match no simulated PV.  Also returns efficiency by multiplicity
+    (reconstructible particles of the simulated PV)."""
+    rec = reconstructible(events)
+    mult = np.bincount(events.part_vertex[rec].astype(np.int64), minlength=len(events.vtx_z))
+    n_ev = len(pv_off) - 1
+    matched_mc = np.zeros(len(events.vtx_z), bool)
+    n_fake = 0
+    dz, dx, pulls = [], [], []
+    v_lo = np.searchsorted(events.vtx_event, np.arange(n_ev), side="left")
+    v_hi = np.searchsorted(events.vtx_event, np.arange(n_ev), side="right")
+    for e in range(n_ev):
+        R = np.asarray(pv[int(pv_off[e]):int(pv_off[e + 1])], np.float64)
+        mc = np.arange(v_lo[e], v_hi[e])
+        sz = np.sqrt(np.maximum(R[:, 5], 0.0)) if len(R) else np.zeros(0)
+        pairs = []
+        for j, k in enumerate(mc):
+            d = np.abs(R[:, 2] - events.vtx_z[k]) if len(R) else np.zeros(0)
+            for r in np.nonzero(d < PV_MATCH_SIGMAS * sz)[0]:
+                pairs.append((float(d[r]), j, int(r)))
+        pairs.sort()
+        used_mc, used_r = set(), set()
+        for d, j, r in pairs:
+            if j in used_mc or r in used_r:
+                continue
+            used_mc.add(j)
+            used_r.add(r)
+            k = mc[j]
+            matched_mc[k] = True
+            dz.append(R[r, 2] - events.vtx_z[k])
+            dx.append(R[r, 0] - events.vtx_x[k])
+            pulls.append((R[r, 2] - events.vtx_z[k]) / sz[r])
+        n_fake += len(R) - len(used_r)
+    good = mult >= min_tracks
+    n_rec_pv = int(pv_off[-1])
+    by_mult = {}
+    for lo, hi in ((4, 10), (10, 20), (20, 40), (40, 10**9)):
+        sel = (mult >= lo) & (mult < hi)
+        if sel.any():
+            by_mult[f"{lo}-{hi if hi < 10**9 else 'inf'}"] = float(matched_mc[sel].mean())
+    return dict(
+        n_mc=int(good.sum()), n_reco=n_rec_pv,
+        efficiency=float(matched_mc[good].mean()) if good.any() else float("nan"),
+        fake_rate=n_fake / n_rec_pv if n_rec_pv else 0.0,
+        sigma_z_mm=float(np.std(dz)) if dz else float("nan"),
+        sigma_x_mm=float(np.std(dx)) if dx else float("nan"),
+        pull_z_width=float(np.std(pulls)) if pulls else float("nan"),
+        efficiency_by_multiplicity=by_mult,
+    )

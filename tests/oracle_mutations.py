@@ -109,6 +109,27 @@ MUTANTS_METRICS = [
      "ghost_rate=float((match >= 0).sum()) / n_tracks"),
 ]
 
+# (name, text in oracle/pv_oracle.c, replacement): primary-vertex finding
+MUTANTS_PV = [
+    ("Tukey weight not squared", "  float u = 1.0f - chi2 / cut;\n  return u * u;", "  float u = 1.0f - chi2 / cut;\n  return u;"),
+    ("weight without the share", "float w = (t * t) / tsum[i];", "float w = t;"),
+    ("position variance without the correlation",
+     "return (cpp + dz * (cpt + cpt)) + (dz * dz) * ctt;", "return cpp + (dz * dz) * ctt;"),
+    ("z step sign", "float dz = ((px * V->bx + py * V->by) - V->bt) / D;",
+     "float dz = (V->bt - (px * V->bx + py * V->by)) / D;"),
+    ("x variance without the z term", "o[3] = 1.0f / V->sxx + (px * px) / D;", "o[3] = 1.0f / V->sxx;"),
+    ("merge rule off", "if (fabsf(vtx[u].z - vtx[v].z) < p->merge_dz &&", "if (fabsf(vtx[u].z - vtx[v].z) < 0.0f &&"),
+    ("equal peaks: the larger bin dominates", "(win[c] == win[b] && c < b)", "(win[c] == win[b] && c > b)"),
+    ("beam-axis cut on x only", "if (!(s[0] * s[0] + s[1] * s[1] < p->max_r2)) continue;",
+     "if (!(s[0] * s[0] < p->max_r2)) continue;"),
+    ("histogram bin rounded", "hist[(uint32_t)u] += 1;", "hist[(uint32_t)(u + 0.5f)] += 1;"),
+    ("no suppression of nearby seeds", "if (dominated) continue;", "if (0) continue;"),
+    ("peak at the first bin of its run", "  return b == p0 + (p1 - p0) / 2;", "  return b == p0;"),
+    ("shoulders are peaks", "  if (p0 > 0 && win[p0 - 1] > win[b]) return 0;\n", ""),
+    ("kept with any weight", "int ok = V->sxx > 0.0f && V->syy > 0.0f && V->sw >= p->min_weight;",
+     "int ok = V->sxx > 0.0f && V->syy > 0.0f;"),
+]
+
 # Mutants that cannot change any output:
 #   - duplicates kept in the sorted key list: the flood fill still visits
 #     (and counts) every pixel position once;
@@ -124,7 +145,7 @@ EQUIVALENT = [
 ]
 
 PINS = ["tests/test_oracle_tracking.py", "tests/test_oracle_cluster.py", "tests/test_oracle_fit.py",
-        "tests/test_oracle_mlp.py", "tests/test_oracle_metrics.py"]
+        "tests/test_oracle_mlp.py", "tests/test_oracle_metrics.py", "tests/test_oracle_pv.py"]
 
 
 def run(name, old, new, target="velo_oracle.c"):
@@ -160,10 +181,15 @@ def main() -> int:
         print(f"{'caught' if caught else 'MISSED'}: {name:34s} {failed[:1]}", flush=True)
         if not caught:
             missed.append(name)
+    for name, old, new in MUTANTS_PV:
+        caught, failed = run(name, old, new, "pv_oracle.c")
+        print(f"{'caught' if caught else 'MISSED'}: {name:34s} {failed[:1]}", flush=True)
+        if not caught:
+            missed.append(name)
     for name, old, new, *target in EQUIVALENT:
         caught, _ = run(name, old, new, *target)
         print(f"{'caught' if caught else 'no effect'}: {name} (equivalent)", flush=True)
-    total = len(MUTANTS) + len(MUTANTS_MLP) + len(MUTANTS_METRICS)
+    total = len(MUTANTS) + len(MUTANTS_MLP) + len(MUTANTS_METRICS) + len(MUTANTS_PV)
     print(f"{total - len(missed)} of {total} mutants caught")
     return 1 if missed else 0
 
