@@ -321,6 +321,74 @@ int velo_get_stats(velo_handle *h, velo_stats *out);
 int velo_describe(const velo_handle *h, char *buf, size_t n);
 
 /*
+ * Primary-vertex finding (paper section 2.3.1, last step: vertices from a
+ * histogram of the tracks' closest approach to the beamline; every track is
+ * weighted to every vertex, so all candidates are fitted in parallel).  It
+ * runs on reconstructed tracks: `tracks` is a velo_output that a
+ * velo_reconstruct call filled (device pointers; track_off, states and
+ * cap_tracks are read), n_events its event count.  Per event:
+ *   - tracks whose beamline state lies within sqrt(max_r2) of the beam axis
+ *     fill a histogram of their beamline z (n_bins bins of bin_width from
+ *     z_min);
+ *   - window counts (bins within `window`); a peak is the middle bin of a run
+ *     of equal counts (>= min_peak) with lower counts on both sides; a peak
+ *     seeds a vertex unless a peak within min_sep bins has a larger count (or
+ *     an equal count and a smaller bin); seeds in increasing z, on the axis;
+ *   - n_iter fit rounds: t_iv = (1 - chi2_iv / chi2_cut)^2 below the cut,
+ *     with chi2_iv the squared distance of track i's line from vertex v at the
+ *     vertex's z over its position variance there (x and y); weight w_iv =
+ *     t_iv^2 / sum_u t_iu; each vertex moves by its weighted least-squares
+ *     step in (x, y, z);
+ *   - kept: weight sum >= min_weight, positive-definite normal matrix, and no
+ *     stronger kept vertex closer than merge_dz in z.
+ * Output (device pointers, caller-owned): pv_off [n_events + 1]; pv
+ * [VELO_PV_NOUT][cap_vertices] SoA rows x, y, z, cxx, cyy, czz, cxy, cxz,
+ * cyz, weight sum (in seed order per event); status [n_events] VELO_PV_*
+ * bits; totals [2] = vertices, error bits (VELO_ERR_CAPACITY's bit when
+ * cap_vertices is too small: pv_off is complete, rows beyond the capacity
+ * are not written).  Every step is single precision in a fixed order, so the
+ * vertices do not depend on the launch.  The first call (and a call with more
+ * events or a larger cap_tracks than any before) allocates the handle's
+ * vertex working storage; the work is then enqueued on `stream`.  Errors:
+ * VELO_ERR_INPUT (null pointers, parameters out of range: n_bins <= 2560,
+ * max_vertices <= 64), VELO_ERR_NOMEM, VELO_ERR_CUDA.
+ */
+#define VELO_PV_NOUT 10
+#define VELO_PV_CAPACITY 0x1u  /* more seeds than max_vertices: the first ones (in z) were fitted */
+#define VELO_PV_SKIPPED 0x2u   /* the event's tracks lie beyond cap_tracks: no vertices */
+
+typedef struct velo_pv_params {
+  float z_min;           /* lower edge of the histogram (mm) */
+  float bin_width;       /* mm */
+  uint32_t n_bins;       /* at most 2560 */
+  uint32_t window;       /* half-width of the counting window (bins) */
+  uint32_t min_peak;     /* tracks in the window of a peak, at least */
+  uint32_t min_sep;      /* a peak suppresses weaker peaks within this many bins */
+  float max_r2;          /* x^2 + y^2 of a track's beamline state below this (mm^2) */
+  float chi2_cut;        /* Tukey cut */
+  uint32_t n_iter;       /* fit rounds */
+  float min_weight;      /* weight sum of a kept vertex, at least */
+  float merge_dz;        /* mm */
+  uint32_t max_vertices; /* seeds per event, at most 64 */
+} velo_pv_params;
+
+typedef struct velo_pv_output {
+  uint32_t cap_vertices;
+  uint32_t *pv_off;   /* [n_events + 1] */
+  float *pv;          /* [VELO_PV_NOUT][cap_vertices] */
+  uint32_t *status;   /* [n_events] VELO_PV_* bits */
+  uint32_t *totals;   /* [2] */
+} velo_pv_output;
+
+/* Default parameters (the frozen readings): z from -300 mm in 2400 bins of
+ * 0.25 mm, window 2, min_peak 3, min_sep 4, max_r2 0.25 mm^2, chi2_cut 9,
+ * 12 rounds, min_weight 3, merge_dz 1 mm, 64 vertices. */
+void velo_pv_default_params(velo_pv_params *params);
+
+int velo_find_pvs(velo_handle *h, uint32_t n_events, const velo_output *tracks, const velo_pv_params *params,
+                  const velo_pv_output *out, void *stream);
+
+/*
  * Clustering with no device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when
  * they need hits -- a host framework that owns a fixed device pool and

@@ -69,6 +69,10 @@ struct velo_handle {
   // global regions of the slow paths: second clustering pass and the
   // global-memory tracking pass
   void* slow_buf = nullptr;
+  // primary-vertex working storage (allocated by velo_find_pvs when needed)
+  void* pv_work = nullptr;
+  uint32_t pv_events = 0;
+  uint64_t pv_tracks = 0;
   int smem_sm = 0, smem_optin = 0;
   // captured launch sequences, replayed while the call descriptors match
   bool use_graphs = false;
@@ -616,6 +620,7 @@ void velo_destroy(velo_handle* h) {
   if (h->trk) cudaFree(h->trk);
   if (h->ring_buf) cudaFree(h->ring_buf);
   if (h->slow_buf) cudaFree(h->slow_buf);
+  if (h->pv_work) cudaFree(h->pv_work);
   if (h->h_totals) cudaFreeHost(h->h_totals);
   delete h;
 }
@@ -791,6 +796,52 @@ int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_outpu
   }
   if (h->use_graphs && st != nullptr) return enqueue_graph(h, *events, *out, ev, wk, st);
   return enqueue(h, ev, wk, *out, st, false);
+}
+
+void velo_pv_default_params(velo_pv_params* p) {
+  if (!p) return;
+  p->z_min = -300.0f;
+  p->bin_width = 0.25f;
+  p->n_bins = 2400;
+  p->window = 2;
+  p->min_peak = 3;
+  p->min_sep = 4;
+  p->max_r2 = 0.25f;
+  p->chi2_cut = 9.0f;
+  p->n_iter = 12;
+  p->min_weight = 3.0f;
+  p->merge_dz = 1.0f;
+  p->max_vertices = 64;
+}
+
+int velo_find_pvs(velo_handle* h, uint32_t n_events, const velo_output* tracks, const velo_pv_params* params,
+                  const velo_pv_output* out, void* stream) {
+  if (!h || !tracks || !params || !out) return fail(VELO_ERR_INPUT, "velo_find_pvs: null argument");
+  if (!tracks->track_off || !tracks->states) return fail(VELO_ERR_INPUT, "velo_find_pvs: null track arrays");
+  if (!out->pv_off || !out->status || !out->totals || (out->cap_vertices && !out->pv))
+    return fail(VELO_ERR_INPUT, "velo_find_pvs: null output arrays");
+  if (!pv_params_ok(*params)) return fail(VELO_ERR_INPUT, "velo_find_pvs: parameters out of range");
+  const uint32_t need_e = n_events > h->pv_events ? n_events : h->pv_events;
+  const uint64_t need_t = tracks->cap_tracks > h->pv_tracks ? tracks->cap_tracks : h->pv_tracks;
+  if (!h->pv_work || need_e > h->pv_events || need_t > h->pv_tracks) {
+    if (h->pv_work) {
+      CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+      cudaFree(h->pv_work);
+      h->pv_work = nullptr;
+    }
+    const size_t bytes = pv_work_bytes(need_e ? need_e : 1, need_t ? need_t : 1);
+    cudaError_t e = cudaMalloc(&h->pv_work, bytes);
+    if (e != cudaSuccess) {
+      h->pv_work = nullptr;
+      h->pv_events = 0;
+      h->pv_tracks = 0;
+      return fail(VELO_ERR_NOMEM, "velo_find_pvs: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    h->pv_events = need_e ? need_e : 1;
+    h->pv_tracks = need_t ? need_t : 1;
+  }
+  CUDA_TRY(launch_pv(h->pv_work, h->pv_events, h->pv_tracks, n_events, *params, *tracks, *out, (cudaStream_t)stream));
+  return VELO_OK;
 }
 
 int velo_sync_status(velo_handle* h, void* stream) {

@@ -630,6 +630,7 @@ __device__ uint32_t cluster_sensor_grid(const uint16_t* __restrict__ col, const 
     roots[w] = rb;
     pre[w] = __popc(rb);
   }
+  __syncthreads();  // the scan reads words other threads wrote
   const uint32_t R = block_exscan(pre, W, s_scan);
   for (uint32_t k = tid; k < R; k += NT) {
     cnt[k] = 0;

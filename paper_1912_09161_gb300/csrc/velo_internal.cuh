@@ -188,6 +188,15 @@ cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output
 cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
                         const WorkView& wk, const velo_output& out, cudaStream_t st);
 
+// Primary-vertex finding (velo_pv.cu): working bytes for up to max_events
+// events and max_tracks tracks (per-track sums, per-event vertex slots and
+// counts, 256-byte aligned in that order), parameter check, and the launch
+// sequence (vertex kernel, scan, compaction).
+bool pv_params_ok(const velo_pv_params& p);
+size_t pv_work_bytes(uint32_t max_events, uint64_t max_tracks);
+cudaError_t launch_pv(void* work, uint32_t max_events, uint64_t max_tracks, uint32_t n_events,
+                      const velo_pv_params& p, const velo_output& tracks, const velo_pv_output& out, cudaStream_t st);
+
 // Working storage of a handle outside its own arena (serving): the capacities
 // a call of n_events / n_pixels gets, the bytes they take, and the rebinding
 // of the handle's working storage to `base` (256-byte aligned, work_bytes long).

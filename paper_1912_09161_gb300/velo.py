@@ -31,7 +31,10 @@ EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_required
             "velo_mlp_get_state", "velo_mlp_set_state", "velo_server_create", "velo_server_destroy",
             "velo_server_request_bytes", "velo_server_set_mlp", "velo_server_submit", "velo_server_poll",
             "velo_server_result", "velo_server_release", "velo_server_status", "velo_server_replay",
-            "velo_last_error", "velo_version")
+            "velo_pv_default_params", "velo_find_pvs", "velo_last_error", "velo_version")
+PV_NOUT = 10
+PV_NAMES = ("x", "y", "z", "cxx", "cyy", "czz", "cxy", "cxz", "cyz", "weight")
+PV_CAPACITY, PV_SKIPPED = 1, 2
 
 
 class VeloError(RuntimeError):
@@ -94,6 +97,18 @@ class velo_output(ctypes.Structure):
                 ("ndof", ctypes.c_void_p), ("event_status", ctypes.c_void_p), ("totals", ctypes.c_void_p),
                 ("cluster_off", ctypes.c_void_p), ("cl_x", ctypes.c_void_p), ("cl_y", ctypes.c_void_p),
                 ("cl_key", ctypes.c_void_p)]
+
+
+class velo_pv_params(ctypes.Structure):
+    _fields_ = [("z_min", ctypes.c_float), ("bin_width", ctypes.c_float), ("n_bins", ctypes.c_uint32),
+                ("window", ctypes.c_uint32), ("min_peak", ctypes.c_uint32), ("min_sep", ctypes.c_uint32),
+                ("max_r2", ctypes.c_float), ("chi2_cut", ctypes.c_float), ("n_iter", ctypes.c_uint32),
+                ("min_weight", ctypes.c_float), ("merge_dz", ctypes.c_float), ("max_vertices", ctypes.c_uint32)]
+
+
+class velo_pv_output(ctypes.Structure):
+    _fields_ = [("cap_vertices", ctypes.c_uint32), ("pv_off", ctypes.c_void_p), ("pv", ctypes.c_void_p),
+                ("status", ctypes.c_void_p), ("totals", ctypes.c_void_p)]
 
 
 class velo_server_config(ctypes.Structure):
@@ -179,6 +194,10 @@ def load_library(build: bool = True) -> ctypes.CDLL:
                  "velo_server_poll", "velo_server_result", "velo_server_release", "velo_server_status",
                  "velo_server_replay"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.velo_pv_default_params.argtypes = [P(velo_pv_params)]
+    lib.velo_pv_default_params.restype = None
+    lib.velo_find_pvs.argtypes = [vp, ctypes.c_uint32, P(velo_output), P(velo_pv_params), P(velo_pv_output), vp]
+    lib.velo_find_pvs.restype = ctypes.c_int
     lib.velo_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.velo_describe.restype = ctypes.c_int
     lib.velo_last_error.restype = ctypes.c_char_p
@@ -477,6 +496,86 @@ def velo_cluster_static(geometry, events: DeviceEvents, out: "DeviceOutput", str
     del keep
 
 
+@dataclasses.dataclass
+class PVParams:
+    """Primary-vertex finding parameters (mm); the defaults are the frozen readings."""
+    z_min: float = -300.0
+    bin_width: float = 0.25
+    n_bins: int = 2400
+    window: int = 2
+    min_peak: int = 3
+    min_sep: int = 4
+    max_r2: float = 0.25
+    chi2_cut: float = 9.0
+    n_iter: int = 12
+    min_weight: float = 3.0
+    merge_dz: float = 1.0
+    max_vertices: int = 64
+
+    def to_c(self) -> velo_pv_params:
+        p = velo_pv_params()
+        for name, _ in velo_pv_params._fields_:
+            setattr(p, name, getattr(self, name))
+        return p
+
+
+@dataclasses.dataclass
+class DevicePVOutput:
+    """Caller-owned primary-vertex output on the device (torch tensors)."""
+    cap_vertices: int
+    pv_off: object
+    pv: object
+    status: object
+    totals: object
+
+    def to_c(self) -> velo_pv_output:
+        return velo_pv_output(self.cap_vertices, _ptr(self.pv_off), _ptr(self.pv), _ptr(self.status),
+                              _ptr(self.totals))
+
+    def to_host(self, n_events: int) -> "HostPV":
+        tot = self.totals.cpu().numpy().view(np.uint32).copy()
+        n = min(int(tot[0]), self.cap_vertices)
+        return HostPV(n_events, self.pv_off[:n_events + 1].cpu().numpy().view(np.uint32).copy(),
+                      self.pv[:, :n].cpu().numpy().T.copy(),
+                      self.status[:n_events].cpu().numpy().view(np.uint32).copy(), tot)
+
+
+@dataclasses.dataclass
+class HostPV:
+    n_events: int
+    pv_off: np.ndarray
+    pv: np.ndarray          # float32 [n_vertices, 10]
+    status: np.ndarray
+    totals: np.ndarray
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self.pv_off[-1])
+
+    def event_vertices(self, e: int) -> np.ndarray:
+        return self.pv[int(self.pv_off[e]):int(self.pv_off[e + 1])]
+
+
+def alloc_pv_output(n_events: int, cap_vertices: int, device="cuda") -> DevicePVOutput:
+    import torch
+    i32 = dict(dtype=torch.int32, device=device)
+    return DevicePVOutput(cap_vertices, torch.zeros(n_events + 1, **i32),
+                          torch.zeros((PV_NOUT, max(cap_vertices, 1)), dtype=torch.float32, device=device),
+                          torch.zeros(max(n_events, 1), **i32), torch.zeros(2, **i32))
+
+
+def velo_pv_default_params() -> velo_pv_params:
+    p = velo_pv_params()
+    load_library().velo_pv_default_params(ctypes.byref(p))
+    return p
+
+
+def velo_find_pvs(h, n_events: int, tracks: "DeviceOutput", params: PVParams, out: DevicePVOutput, stream: int = 0):
+    tc, pc, oc = tracks.to_c(), params.to_c(), out.to_c()
+    _check(load_library(False).velo_find_pvs(h, n_events, ctypes.byref(tc), ctypes.byref(pc), ctypes.byref(oc),
+                                             ctypes.c_void_p(stream)), "velo_find_pvs")
+
+
 def velo_version() -> str:
     return load_library().velo_version().decode()
 
@@ -538,6 +637,15 @@ class Reconstructor:
 
     def sync_status(self, stream: int = 0) -> int:
         return velo_sync_status(self.handle, stream)
+
+    def find_pvs(self, n_events: int, tracks: DeviceOutput, params: PVParams | None = None, cap_vertices: int = 0,
+                 stream: int = 0) -> HostPV:
+        """Primary vertices of reconstructed tracks (device output of
+        ``reconstruct``); copies the result to host numpy arrays."""
+        cap = cap_vertices or 64 * max(n_events, 1)
+        out = alloc_pv_output(n_events, cap, device=tracks.track_off.device)
+        velo_find_pvs(self.handle, n_events, tracks, params or PVParams(), out, stream)
+        return out.to_host(n_events)
 
     def run(self, events: DeviceEvents, clusters: bool = False, stream: int = 0, check: bool = True) -> HostResult:
         """Reconstructs and copies the result to host numpy arrays."""
