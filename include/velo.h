@@ -45,6 +45,7 @@ typedef enum velo_status {
 #define VELO_EV_OVERFLOW 0x4u     /* event beyond every working capacity (more than 65,504 hits, or more
                                      than 6,614 track candidates in the global-memory pass): skipped */
 #define VELO_EV_TRUNCATED 0x8u    /* outputs of this event did not fit the caller's buffers */
+#define VELO_EV_GEC 0x10u         /* removed by the global event cut (more raw pixels than gec_max_pixels) */
 
 /* Number of floats per track state (SoA rows of velo_output.states). */
 #define VELO_NSTATE 13
@@ -90,6 +91,9 @@ typedef struct velo_params {
   float ms_coeff;         /* slope kick per module crossed: ms_coeff * 1e-3 * sin(theta) / pt_nominal */
   uint32_t use_mlp;            /* 1: keep candidates by the ghost classifier instead of the plain cuts */
   float mlp_logit_threshold;   /* keep a candidate when its classifier logit >= this (score = sigmoid) */
+  uint32_t gec_max_pixels;     /* global event cut (paper section 2.3: the busiest events are removed
+                                  before any reconstruction): an event of more raw pixels than this is
+                                  marked VELO_EV_GEC and yields nothing; 0 = off */
 } velo_params;
 
 /* Handle capacities (velo_create).  Zero fields take defaults. */

@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
                 ("max_scatter_seed", ctypes.c_float), ("max_scatter_fwd", ctypes.c_float),
                 ("max_scatter_3hit", ctypes.c_float), ("max_skipped", ctypes.c_uint32),
                 ("sigma_meas", ctypes.c_float), ("pt_nominal", ctypes.c_float),
-                ("ms_coeff", ctypes.c_float)]
+                ("ms_coeff", ctypes.c_float), ("gec_max_pixels", ctypes.c_uint32)]
 
 
 class _PVParams(ctypes.Structure):
@@ -124,6 +124,7 @@ class Params:
     sigma_meas: float = 0.055 / math.sqrt(12.0)
     pt_nominal: float = 0.4
     ms_coeff: float = 1.0
+    gec_max_pixels: int = 0
 
     def _c(self) -> _Params:
         p = _Params()

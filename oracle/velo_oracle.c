@@ -32,6 +32,10 @@
  *   - plain cuts: keep tracks of >= 4 hits; keep a 3-hit track only if its seed
  *     scatter is below max_scatter_3hit and none of its hits is on another
  *     track;
+ *   - the global event cut (section 2.3: the busiest events are removed
+ *     before any reconstruction) is read as a cut on the event's raw pixel
+ *     count: above gec_max_pixels (when non-zero) the event gets status 0x10
+ *     and no clusters or tracks;
  *   - the fit runs from the highest-z hit toward lower z, starting from the
  *     exact two-hit state; the scattering noise uses the polar angle of the
  *     unweighted least-squares line through all hits; the final state is
@@ -66,6 +70,7 @@ typedef struct or_params {
   float sigma_meas;
   float pt_nominal;
   float ms_coeff;
+  uint32_t gec_max_pixels;   /* global event cut on raw pixels, 0 = off */
 } or_params;
 
 typedef struct or_options {
@@ -526,11 +531,20 @@ typedef struct {
 
 static void run_event(const job_t *j, uint32_t e, evwork *w) {
   const uint32_t ns = j->g->n_modules * j->g->sensors_per_module;
+  const uint32_t *so = j->sensor_off + (size_t)e * ns;
   w->status = 0;
-  cluster_event(j->g, j->sensor_off + (size_t)e * ns, j->col, j->row, j->pix_cluster, w);
-  uint64_t sh = j->o->shuffle_seed ? j->o->shuffle_seed * 1000003ULL + e : 0;
-  track_event(j->g, j->p, sh, w);
-  select_tracks(j->p, j->o->all_candidates, w);
+  if (j->p->gec_max_pixels && so[ns] - so[0] > j->p->gec_max_pixels) {
+    /* removed by the global event cut: no clusters, no tracks */
+    w->status = 0x10u;
+    w->nc = 0;
+    w->nout = 0;
+    for (uint32_t i = so[0]; i < so[ns]; ++i) j->pix_cluster[i] = -1;
+  } else {
+    cluster_event(j->g, so, j->col, j->row, j->pix_cluster, w);
+    uint64_t sh = j->o->shuffle_seed ? j->o->shuffle_seed * 1000003ULL + e : 0;
+    track_event(j->g, j->p, sh, w);
+    select_tracks(j->p, j->o->all_candidates, w);
+  }
   evout *o = &j->out[e];
   o->status = w->status;
   o->nc = w->nc;

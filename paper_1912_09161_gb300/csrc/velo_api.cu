@@ -136,6 +136,7 @@ DevParams to_dev(const velo_params& p) {
   d.ms_coeff = p.ms_coeff;
   d.use_mlp = p.use_mlp;
   d.mlp_logit_threshold = p.mlp_logit_threshold;
+  d.gec_max_pixels = p.gec_max_pixels;
   // The pseudo-angle moves by at most one unit per radian, so a window of
   // atan(tol) plus a margin for rounding covers every phi-compatible hit.
   double w = atan((double)fabsf(p.tan_phi_tol)) + 1e-3;
@@ -389,8 +390,8 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
   const bool tm = h->timing;
   CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[0], st, mark));
-  CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, st));
-  CUDA_TRY(launch_cluster_big(h->d_geo, ev, wk, st));
+  CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, h->par.gec_max_pixels, st));
+  CUDA_TRY(launch_cluster_big(h->d_geo, ev, wk, h->par.gec_max_pixels, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[1], st, mark));
   if (E) {
     if (h->sched.concurrent) {

@@ -683,7 +683,7 @@ struct ClusterSmem {
 template <int NT, bool BIG>
 __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsView& ev, const WorkView& wk,
                               uint32_t e, const ClusterSmem& S, uint32_t& H_out, uint32_t& status_out,
-                              unsigned char* gscr) {
+                              unsigned char* gscr, uint32_t gec_max_pixels) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = geo->n_sensors, ncols = geo->n_cols, nrows = geo->n_rows;
   unsigned char* slice = S.warps + (warp == 0 ? 0u : kBigSlice + (uint32_t)(warp - 1) * kSmallSlice);
@@ -709,6 +709,12 @@ __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsV
       wk.rec[e] = EventRec{0, 0, 0, VELO_EV_BAD_OFFSETS, 0, 0, gbase, 0};
       atomicOr(&wk.cnt->error, (uint32_t)kErrInput);
     }
+    return false;
+  }
+  // global event cut (paper section 2.3): the busiest events are removed
+  // before any reconstruction; not an error
+  if (gec_max_pixels && so[ns] - gbase > gec_max_pixels) {
+    if (tid == 0) wk.rec[e] = EventRec{0, 0, 0, VELO_EV_GEC, 0, 0, gbase, 0};
     return false;
   }
   const uint16_t* col = ev.col + gbase;
@@ -856,14 +862,14 @@ __device__ inline void queue_event(const WorkView& wk, uint32_t e, uint32_t gbas
 
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
-                                                     WorkView wk) {
+                                                     WorkView wk, uint32_t gec) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ClusterLayout L = cluster_layout(NT);
   const ClusterSmem S{(uint32_t*)(smem + L.soff), (uint32_t*)(smem + L.ccnt), (uint32_t*)(smem + L.misc),
                       (uint32_t*)(smem + L.scan), (uint8_t*)(smem + L.lists), smem + L.warps};
   for (uint32_t e = blockIdx.x; e < ev.n_events; e += gridDim.x) {
     uint32_t H = 0, st = 0;
-    if (!cluster_event<NT, false>(geo, ev, wk, e, S, H, st, nullptr)) continue;
+    if (!cluster_event<NT, false>(geo, ev, wk, e, S, H, st, nullptr, gec)) continue;
     if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, st);
   }
 }
@@ -873,7 +879,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometr
 // path (each CTA has its own global region).
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) cluster_big_kernel(const DevGeometry* __restrict__ geo, EventsView ev,
-                                                            WorkView wk) {
+                                                            WorkView wk, uint32_t gec) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ uint32_t s_ticket;
   const ClusterLayout L = cluster_layout(NT);
@@ -888,7 +894,7 @@ __global__ void __launch_bounds__(NT, 1) cluster_big_kernel(const DevGeometry* _
     if (q >= *(volatile uint32_t*)&wk.cnt->queue_len[kBigSensorQueue]) break;
     const uint32_t e = wk.queue[kBigSensorQueue][q];
     uint32_t H = 0, st = 0;
-    if (!cluster_event<NT, true>(geo, ev, wk, e, S, H, st, gscr)) continue;
+    if (!cluster_event<NT, true>(geo, ev, wk, e, S, H, st, gscr, gec)) continue;
     if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, st);
   }
 }
@@ -906,17 +912,20 @@ cudaError_t cluster_set_smem_limit(int n_threads) {
 }
 
 cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, int n_threads,
-                           cudaStream_t st) {
+                           uint32_t gec_max_pixels, cudaStream_t st) {
   if (ev.n_events == 0) return cudaSuccess;
   if (n_threads != kClusterThreads) return cudaErrorInvalidValue;
   const unsigned grid = ev.n_events < 65535u * 4 ? ev.n_events : 65535u * 4;
-  cluster_kernel<kClusterThreads><<<grid, kClusterThreads, cluster_smem_bytes(n_threads), st>>>(geo, ev, wk);
+  cluster_kernel<kClusterThreads><<<grid, kClusterThreads, cluster_smem_bytes(n_threads), st>>>(geo, ev, wk,
+                                                                                                 gec_max_pixels);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cluster_big(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, cudaStream_t st) {
+cudaError_t launch_cluster_big(const DevGeometry* geo, const EventsView& ev, const WorkView& wk,
+                               uint32_t gec_max_pixels, cudaStream_t st) {
   if (ev.n_events == 0 || !wk.big_scratch) return cudaSuccess;
-  cluster_big_kernel<kClusterThreads><<<kBigCtas, kClusterThreads, cluster_smem_bytes(kClusterThreads), st>>>(geo, ev, wk);
+  cluster_big_kernel<kClusterThreads><<<kBigCtas, kClusterThreads, cluster_smem_bytes(kClusterThreads), st>>>(
+      geo, ev, wk, gec_max_pixels);
   return cudaGetLastError();
 }
 

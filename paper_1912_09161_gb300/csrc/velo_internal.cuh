@@ -50,6 +50,7 @@ struct DevParams {
   uint32_t use_mlp;
   float mlp_logit_threshold;  // keep a candidate when its classifier logit >= this
   float phi_window;  // half-width of the phi window in pseudo-angle units (>= atan(tol))
+  uint32_t gec_max_pixels;  // global event cut on raw pixels (0: off)
 };
 
 // Global-memory slow paths.  Sensors of more than kWarpStage raw pixels are
@@ -158,10 +159,12 @@ struct WorkView {
 // Clustering kernel (velo_cluster.cu).
 uint32_t cluster_smem_bytes(int n_threads);
 cudaError_t cluster_set_smem_limit(int n_threads);
+// gec_max_pixels: events of more raw pixels are marked VELO_EV_GEC and skipped (0: no cut).
 cudaError_t launch_cluster(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, int n_threads,
-                           cudaStream_t st);
+                           uint32_t gec_max_pixels, cudaStream_t st);
 // Second clustering pass over the events queued for a sensor beyond kWarpStage pixels.
-cudaError_t launch_cluster_big(const DevGeometry* geo, const EventsView& ev, const WorkView& wk, cudaStream_t st);
+cudaError_t launch_cluster_big(const DevGeometry* geo, const EventsView& ev, const WorkView& wk,
+                               uint32_t gec_max_pixels, cudaStream_t st);
 
 // Tracking kernel (velo_track.cu).
 Caps make_caps(uint32_t smem_budget, uint32_t n_modules, int n_threads);

@@ -233,7 +233,7 @@ extern "C" int velo_cluster_static(const velo_geometry* geometry, const velo_eve
   static_geometry_kernel<<<1, 256, 0, st>>>(g, (DevGeometry*)(b + kOffGeo));
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemsetAsync(wk.cnt, 0, sizeof(Counters), st);
-  if (e == cudaSuccess) e = launch_cluster((const DevGeometry*)(b + kOffGeo), ev, wk, 256, st);
+  if (e == cudaSuccess) e = launch_cluster((const DevGeometry*)(b + kOffGeo), ev, wk, 256, 0u, st);
   if (e == cudaSuccess) {
     static_scan_kernel<<<1, 1024, 0, st>>>(E, wk.rec, out->cluster_off, out->totals, out->cap_clusters, wk.cnt);
     e = cudaGetLastError();

@@ -21,7 +21,7 @@ NSTATE = 13
 STATE_NAMES = ("x", "y", "z", "tx", "ty", "c00", "c20", "c22", "c11", "c31", "c33", "chi2", "score")
 
 VELO_OK, VELO_ERR_INPUT, VELO_ERR_CAPACITY, VELO_ERR_NOMEM, VELO_ERR_TIMEOUT, VELO_ERR_CUDA, VELO_ERR_STATE = range(7)
-EV_BAD_PIXEL, EV_BAD_OFFSETS, EV_OVERFLOW, EV_TRUNCATED = 1, 2, 4, 8
+EV_BAD_PIXEL, EV_BAD_OFFSETS, EV_OVERFLOW, EV_TRUNCATED, EV_GEC = 1, 2, 4, 8, 16
 CFG_CLUSTERS = 1
 
 EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_required", "velo_set_params", "velo_reconstruct",
@@ -57,7 +57,7 @@ class velo_params(ctypes.Structure):
                 ("max_scatter_3hit", ctypes.c_float), ("max_skipped", ctypes.c_uint32),
                 ("sigma_meas", ctypes.c_float), ("pt_nominal", ctypes.c_float),
                 ("ms_coeff", ctypes.c_float), ("use_mlp", ctypes.c_uint32),
-                ("mlp_logit_threshold", ctypes.c_float)]
+                ("mlp_logit_threshold", ctypes.c_float), ("gec_max_pixels", ctypes.c_uint32)]
 
 
 class velo_config(ctypes.Structure):
@@ -229,6 +229,7 @@ class Params:
     ms_coeff: float = 1.0
     use_mlp: int = 0
     mlp_logit_threshold: float = 0.0
+    gec_max_pixels: int = 0
 
     def to_c(self) -> velo_params:
         p = velo_params()

@@ -28,7 +28,7 @@ class Params(ctypes.Structure):
     _fields_ = [("max_slope", c_f32), ("tan_phi_tol", c_f32), ("max_scatter_seed", c_f32),
                 ("max_scatter_fwd", c_f32), ("max_scatter_3hit", c_f32), ("max_skipped", c_u32),
                 ("sigma_meas", c_f32), ("pt_nominal", c_f32), ("ms_coeff", c_f32), ("use_mlp", c_u32),
-                ("mlp_logit_threshold", c_f32)]
+                ("mlp_logit_threshold", c_f32), ("gec_max_pixels", c_u32)]
 
 
 class Config(ctypes.Structure):
@@ -76,7 +76,7 @@ def test_c_abi_direct(lib):
                                               geom.row_dy.astype(np.int8))]
     g = Geometry(geom.n_modules, geom.sensors_per_module, geom.n_cols, geom.n_rows, geom.pitch,
                  *[a.ctypes.data for a in keep])
-    p = Params(0.4, np.tan(0.05), 0.1, 0.1, 0.02, 1, 0.055 / np.sqrt(12.0), 0.4, 1.0, 0, 0.0)
+    p = Params(0.4, np.tan(0.05), 0.1, 0.1, 0.02, 1, 0.055 / np.sqrt(12.0), 0.4, 1.0, 0, 0.0, 0)
     cfg = Config(ev.n_events, ev.n_pixels, 0, 0, 1)
     h = vp()
     assert lib.velo_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(cfg), ctypes.byref(h)) == 0

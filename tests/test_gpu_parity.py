@@ -24,7 +24,7 @@ def _gpu_params(p: oracle.Params):
     return V.Params(max_slope=p.max_slope, tan_phi_tol=p.tan_phi_tol, max_scatter_seed=p.max_scatter_seed,
                     max_scatter_fwd=p.max_scatter_fwd, max_scatter_3hit=p.max_scatter_3hit,
                     max_skipped=p.max_skipped, sigma_meas=p.sigma_meas, pt_nominal=p.pt_nominal,
-                    ms_coeff=p.ms_coeff)
+                    ms_coeff=p.ms_coeff, gec_max_pixels=p.gec_max_pixels)
 
 
 @pytest.fixture(scope="module")
@@ -314,3 +314,19 @@ def test_config2_full_size_sampled(V, geom):
     for e in sample:
         orc = oracle.reconstruct(geom, ev.subset(int(e), int(e) + 1))
         assert_parity(res, orc, events_idx=[int(e)])
+
+
+def test_global_event_cut(V, geom):
+    """The global event cut at the 90th percentile of the uneven batch's pixel
+    counts: the busiest events are marked VELO_EV_GEC with nothing out, every
+    other event equals the oracle under the same cut."""
+    ev = velo_synth.generate(velo_synth.config(2, n_events=300))
+    cut = int(np.percentile(ev.pixels_per_event(), 90))
+    p = oracle.Params(gec_max_pixels=cut)
+    orc = oracle.reconstruct(geom, ev, p, n_threads=NCPU)
+    res = _run(V, geom, ev, _gpu_params(p))
+    over = ev.pixels_per_event() > cut
+    assert 20 <= over.sum() <= 40
+    assert np.all(res.event_status[over] == V.velo.EV_GEC) and np.all(res.event_status[~over] == 0)
+    assert int(res.totals[3]) == 0
+    assert_parity(res, orc)

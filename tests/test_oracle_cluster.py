@@ -128,3 +128,33 @@ def test_generated_event_clusters(geom, cfg0_events, cfg0_oracle):
             sc = np.array([lab[c, rr] for c, rr in pix])
             assert len(set(zip(ids.tolist(), sc.tolist()))) == lab.max() == len(set(ids.tolist()))
             assert np.all((r.cl_key[base + ids] >> 16) == s)
+
+
+def test_global_event_cut():
+    """Global event cut (section 2.3, read on the VELO raw size): an event of
+    more raw pixels than the cut has status 0x10 and no clusters or tracks,
+    its pixels no cluster; every other event is exactly what a run without
+    the cut gives."""
+    import velo_synth
+    geom = velo_synth.geometry()
+    ev = velo_synth.generate(velo_synth.config(2, n_events=40))
+    ppe = ev.pixels_per_event()
+    cut = int(np.percentile(ppe, 75))
+    plain = oracle.reconstruct(geom, ev)
+    r = oracle.reconstruct(geom, ev, oracle.Params(gec_max_pixels=cut))
+    over = ppe > cut
+    assert over.any() and not over.all()
+    assert np.array_equal(r.event_status[over], np.full(over.sum(), 0x10))
+    for e in range(ev.n_events):
+        if over[e]:
+            assert r.cluster_off[e + 1] == r.cluster_off[e] and r.track_off[e + 1] == r.track_off[e]
+            p0, p1 = ev.event_pixel_range(e)
+            assert np.all(r.pix_cluster[p0:p1] == -1)
+        else:
+            assert r.event_tracks(e) == plain.event_tracks(e) and r.event_status[e] == plain.event_status[e]
+            c0, c1 = int(r.cluster_off[e]), int(r.cluster_off[e + 1])
+            d0 = int(plain.cluster_off[e])
+            assert np.array_equal(r.cl_key[c0:c1], plain.cl_key[d0:d0 + c1 - c0])
+    # a cut at the largest event keeps everything
+    r2 = oracle.reconstruct(geom, ev, oracle.Params(gec_max_pixels=int(ppe.max())))
+    assert np.array_equal(r2.track_off, plain.track_off)
