@@ -4,11 +4,17 @@
 One step = one call of the library's ``velo_reconstruct`` over the whole
 batch (clustering, triplet seeding and following, cuts, fit, output
 compaction) with the raw pixels already resident in device memory.  Prints
-one JSON line (see the keys below), which also carries the serving loop's
-p50 / p99 batch latency under Poisson arrivals (``serving``) and the ghost
-rate of the benchmarked tracks.
+one JSON line (see the keys below), which also carries:
+  - ``serving``: the continuous-batching server's capacity and its p50 / p99
+    batch latency under Poisson arrivals at 1.2x and 0.8x of it;
+  - ``pv``: primary-vertex finding on the batch's tracks (time, efficiency);
+  - ``uneven``: the 50,000-event uneven batch (rate, stage split, the global
+    event cut's gain, rate per occupancy bin);
+  - ``classifier``: the ghost-classifier path (trained here on the GPU): rate
+    and efficiency / ghost / clone rates against the plain cuts;
+  - the ghost rate of the benchmarked tracks and the oracle's CPU rate.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--serve-seconds S]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--serve-seconds S] [--no-legs]
 
 Workload: 10,000 synthetic events (seed 1; each rank r of a multi-GPU run
 takes seed 1 + 100 r, so per-GPU work is fixed: weak scaling).
@@ -47,7 +53,8 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "track_kernel_nominal_10k.md")
 # sources of the tracking kernels, in the order the profile summary hashes them
 TRACK_SOURCES = ("velo_track_ring.cu", "velo_track.cu", "velo_track_common.cuh", "velo_internal.cuh",
                  "velo_device.cuh", "velo_fit.cuh", "velo_mlp.cuh")
-KERNELS_BASE = 4            # clustering, retry pass of the largest class, scan, emit (+ one per class)
+KERNELS_BASE = 6            # clustering and its second pass, retry and global-memory tracking passes, scan, emit
+                            # (+ one per class)
 
 
 def _dist():
@@ -223,10 +230,11 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline(geom, ev, gpu_result=None) -> dict:
+def cpu_baseline(geom, ev, gpu_result=None, keep=None) -> dict:
     """The oracle timed on the host cores over a sample of the workload.  Its
     clusters also give the truth match of the GPU tracks of the same events
-    (tracking efficiency, ghost and clone rates)."""
+    (tracking efficiency, ghost and clone rates).  ``keep`` (a dict) receives
+    the oracle's result of the sample."""
     import oracle
     import oracle.metrics as MET
     cores = os.cpu_count() or 1
@@ -244,6 +252,8 @@ def cpu_baseline(geom, ev, gpu_result=None) -> dict:
         q = MET.summarize(sub, r.cluster_off, r.pix_cluster, gpu_result.track_off, gpu_result.hit_off,
                           gpu_result.hit_ids)
         out["gpu_track_quality"] = {k: q[k] for k in ("efficiency", "ghost_rate", "clone_rate")}
+    if keep is not None:
+        keep["oracle"] = r
     return out
 
 
@@ -251,13 +261,14 @@ def serving(geom, seconds: float, n_slots: int = 8) -> dict:
     """Continuous-batching serving loop on the 5,000-event seed-4 sample:
     batches of 100-5,000 events cut from it, arriving as a Poisson process.
 
-    sustainable rate = events/s of one slot working through a backlog of such
-    batches one after another (copy in, reconstruct, copy out, next): the rate
-    a server without continuous batching sustains.  The continuous-batching
-    server (n_slots slots, pool = 4 batches of the maximum size, so that memory
-    decides admission for large batches) then serves Poisson arrivals at 1.2x
-    that rate for ``seconds`` and at 0.8x for a quarter of it; latency is from
-    a batch's arrival to its results in host memory."""
+    capacity = events/s of the continuous-batching server (n_slots slots, pool
+    = 4 batches of the maximum size, so that memory decides admission for
+    large batches) working through a backlog of such batches; the server then
+    serves Poisson arrivals at 1.2x its capacity for ``seconds`` (an overload:
+    the queue grows, and the latency is mostly queueing) and at 0.8x for a
+    quarter of it; latency is from a batch's arrival to its results in host
+    memory.  The rate of one slot working through the backlog batch after
+    batch (a server without continuous batching) is kept beside them."""
     import velo_synth
     from paper_1912_09161_gb300 import serve
     ev = velo_synth.generate(velo_synth.config(4))
@@ -278,9 +289,10 @@ def serving(geom, seconds: float, n_slots: int = 8) -> dict:
     capacity = b.events / wall
     out = {"workload": "batches of 100-5,000 events (uniform) cut from 5,000 nominal events, seed 4; "
                        "Poisson arrivals", "n_slots": n_slots, "pool_bytes": 4 * need_max,
-           "sustainable_events_per_s": round(serial, 1), "burst_capacity_events_per_s": round(capacity, 1)}
+           "serial_one_slot_events_per_s": round(serial, 1), "burst_capacity_events_per_s": round(capacity, 1)}
+    out["load_reference"] = "continuous-batching capacity (burst_capacity_events_per_s)"
     for name, factor, dur, seed in (("load_1.2x", 1.2, seconds, 4), ("load_0.8x", 0.8, seconds / 4, 5)):
-        tr = serve.poisson_trace(factor * serial, dur, 100, 5000, E, seed=seed)
+        tr = serve.poisson_trace(factor * capacity, dur, 100, 5000, E, seed=seed)
         lat, wall = srv.replay(pool, tr, timeout_s=4 * dur + 60)
         st = srv.status()
         res = serve.latency_summary(lat, tr.events, wall)
@@ -289,6 +301,224 @@ def serving(geom, seconds: float, n_slots: int = 8) -> dict:
         out[name] = res
     srv.close()
     return out
+
+
+def gather_events(ev, order):
+    """A batch of the events of ``ev`` in the given order (host arrays; no
+    truth): sensor offsets rebased, pixels gathered event by event."""
+    import dataclasses
+    ns = ev.n_sensors
+    so = ev.sensor_off.astype(np.int64)
+    starts, ends = so[:-1:ns][order], so[ns::ns][order]
+    counts = ends - starts
+    new_start = np.concatenate([[0], np.cumsum(counts)])
+    idx = np.repeat(starts - new_start[:-1], counts) + np.arange(int(counts.sum()))
+    offs = np.zeros(len(order) * ns + 1, np.int64)
+    for k, e in enumerate(order):
+        offs[k * ns:(k + 1) * ns] = so[e * ns:(e + 1) * ns] - so[e * ns] + new_start[k]
+    offs[-1] = new_start[-1]
+    empty = np.zeros(0)
+    return dataclasses.replace(ev, n_events=len(order), sensor_off=offs.astype(np.uint32), col=ev.col[idx],
+                               row=ev.row[idx], pix_label=ev.pix_label[idx])
+
+
+def timed_calls(rec, d, out, sptr, stream, flush, steps: int, warmup: int) -> tuple[list, list]:
+    """Step times (ms, CUDA events on the call's stream, L2 flushed before
+    each step) and the per-call statistics of ``steps`` reconstructions."""
+    import torch
+    for _ in range(warmup):
+        rec.reconstruct(d, out, sptr)
+    rec.sync_status(sptr)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    stats = []
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        starts[k].record(stream)
+        rec.reconstruct(d, out, sptr)
+        ends[k].record(stream)
+        stats.append(rec.stats())
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)], stats
+
+
+def _stage(stats: list) -> dict:
+    return {name: statistics.mean(x["ms"][k] for x in stats)
+            for k, name in enumerate(("cluster", "track", "scan", "emit"))}
+
+
+def uneven_leg(V, geom, dev, stream, flush, steps: int, warmup: int) -> dict:
+    """The 50,000-event uneven batch (pileup uniform in [1, 20]): autotuned
+    schedule, graph replay, stage split; the same batch with the global event
+    cut at the 90th percentile of its pixel counts (rate over all events,
+    removed ones included, as the paper counts it); and the rate per
+    occupancy bin (the batch sorted by pixel count, each bin one call)."""
+    import velo_synth
+    ev = velo_synth.generate(velo_synth.config(2))
+    ns, E = ev.n_sensors, ev.n_events
+    ppe = ev.pixels_per_event()
+    rec = V.Reconstructor(geom, V.Params(), max_events=E, max_pixels=ev.n_pixels)
+    sptr = stream.cuda_stream
+    try:
+        d = V.upload_events(ev, dev)
+        ct, ch, _ = V.suggested_caps(E, ev.n_pixels)
+        out = V.alloc_output(E, ct, ch, 0, device=dev)
+        tuned, _ = rec.autotune(d, out, sptr)
+        rec.set_graphs(True)
+        rec.set_timing(True)
+        ms, st = timed_calls(rec, d, out, sptr, stream, flush, steps, warmup)
+        res = {"workload": WORKLOADS["uneven"][1], "n_events": E, "pixels_per_event": float(ppe.mean()),
+               "value": E / (statistics.mean(ms) / 1e3), "unit": UNIT, "ms_per_step": statistics.mean(ms),
+               "stage_ms": _stage(st), "schedule": tuned}
+        cut = int(np.percentile(ppe, 90))
+        rec.set_params(V.Params(gec_max_pixels=cut))
+        ms_g, st_g = timed_calls(rec, d, out, sptr, stream, flush, steps, warmup)
+        kept = float((ppe <= cut).mean())
+        res["gec"] = {"max_pixels": cut, "kept_fraction": kept, "value": E / (statistics.mean(ms_g) / 1e3),
+                      "ms_per_step": statistics.mean(ms_g), "stage_ms": _stage(st_g),
+                      "gain": statistics.mean(ms) / statistics.mean(ms_g) - 1.0}
+        rec.set_params(V.Params())
+    finally:
+        rec.close()
+    # throughput per occupancy bin: the batch sorted by pixel count
+    order = np.argsort(ppe, kind="stable")
+    srt = gather_events(ev, order)
+    sp = ppe[order]
+    rec = V.Reconstructor(geom, V.Params(), max_events=E, max_pixels=srt.n_pixels)
+    bins = []
+    try:
+        d = V.upload_events(srt, dev)
+        ct, ch, _ = V.suggested_caps(E, srt.n_pixels)
+        out = V.alloc_output(E, ct, ch, 0, device=dev)
+        rec.set_graphs(True)
+        rec.set_timing(True)
+        edges = [0, 2000, 3000, 4000, 5000, 6000, 7000, 8000, 10000, 1 << 30]
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            i0, i1 = int(np.searchsorted(sp, lo)), int(np.searchsorted(sp, hi))
+            if i1 - i0 < 200:
+                continue
+            sub = V.DeviceEvents(i1 - i0, d.sensor_off[i0 * ns:], d.col, d.row)
+            ms_b, st_b = timed_calls(rec, sub, out, sptr, stream, flush, max(3, steps // 2), 2)
+            bins.append({"pixels": [lo, hi if hi < (1 << 30) else None], "events": i1 - i0,
+                         "mean_pixels": float(sp[i0:i1].mean()), "events_per_s": (i1 - i0) / (statistics.mean(ms_b) / 1e3),
+                         "stage_ms": _stage(st_b)})
+    finally:
+        rec.close()
+    res["by_occupancy"] = bins
+    return res
+
+
+def classifier_leg(V, geom, ev, d, dev, stream, flush, steps: int, warmup: int, orc) -> dict:
+    """The ghost-classifier path on the nominal batch: the network trained on
+    the GPU (200,000 pre-cut oracle candidates of seed-3 events labelled by
+    truth), its logit threshold chosen on 500 validation events so that the
+    efficiency stays within 0.1 % of the plain cuts, then the rate and the
+    efficiency, ghost and clone rates against the plain cuts on the same
+    events (truth matched through the oracle's clusters, which equal the
+    GPU's)."""
+    import oracle
+    import oracle.metrics as MET
+    import oracle.mlp as M
+    import velo_synth
+    from paper_1912_09161_gb300 import ghost
+    cores = os.cpu_count() or 1
+    allc = velo_synth.generate(velo_synth.config(3, n_events=1920))
+    train, val = allc.subset(0, 1420), allc.subset(1420, 1920)
+    rt = oracle.reconstruct(geom, train, all_candidates=True, n_threads=cores)
+    f, y = M.training_set(geom, train, rt)
+    t0 = time.perf_counter()
+    tr = ghost.train(f, y, epochs=20, seed=3, device=dev)
+    train_s = time.perf_counter() - t0
+    stt = tr.state()
+    tr.close()
+    pb = (stt.params_bf16.astype(np.uint32) << 16).view(np.float32)
+    rv = oracle.reconstruct(geom, val, all_candidates=True, n_threads=cores)
+    fv, keep_plain, _ = M.candidate_table(geom, val, rv)
+    lg = M.forward_bf16(fv, pb, stt.mean, stt.istd)
+    base = MET.summarize(val, rv.cluster_off, rv.pix_cluster, rv.track_off, rv.hit_off, rv.hit_ids, keep=keep_plain)
+    thr = 0.0
+    for t in np.arange(-2.0, 4.01, 0.125):
+        s = MET.summarize(val, rv.cluster_off, rv.pix_cluster, rv.track_off, rv.hit_off, rv.hit_ids, keep=lg >= t)
+        if s["efficiency"] >= base["efficiency"] - 0.001:
+            thr = float(np.float32(t))
+    E = ev.n_events
+    rec = V.Reconstructor(geom, V.Params(use_mlp=1, mlp_logit_threshold=thr), max_events=E, max_pixels=ev.n_pixels)
+    sptr = stream.cuda_stream
+    try:
+        rec.set_mlp(stt.params_bf16, stt.mean, stt.istd)
+        ct, ch, _ = V.suggested_caps(E, ev.n_pixels)
+        out = V.alloc_output(E, ct, ch, 0, device=dev)
+        rec.set_graphs(True)
+        rec.set_timing(True)
+        ms, st = timed_calls(rec, d, out, sptr, stream, flush, steps, warmup)
+        res_m = out.to_host(E)
+    finally:
+        rec.close()
+    plain = V.Reconstructor(geom, V.Params(), max_events=E, max_pixels=ev.n_pixels)
+    try:
+        res_p = plain.run(d, stream=sptr)
+    finally:
+        plain.close()
+    q = {}
+    for name, r in (("plain", res_p), ("classifier", res_m)):
+        s = MET.summarize(ev, orc.cluster_off, orc.pix_cluster, r.track_off, r.hit_off, r.hit_ids)
+        q[name] = {k: s[k] for k in ("efficiency", "ghost_rate", "clone_rate", "n_tracks")}
+    return {"training": {"candidates": int(len(y)), "epochs": 20, "seconds": round(train_s, 2)},
+            "logit_threshold": thr, "value": E / (statistics.mean(ms) / 1e3), "unit": UNIT,
+            "ms_per_step": statistics.mean(ms), "stage_ms": _stage(st), "quality": q,
+            "efficiency_change": q["classifier"]["efficiency"] - q["plain"]["efficiency"],
+            "ghost_rate_change": q["classifier"]["ghost_rate"] - q["plain"]["ghost_rate"]}
+
+
+def pv_leg(V, rec, ev, out, dev, stream, steps: int) -> dict:
+    """Primary-vertex finding (section 2.3.1) on the nominal batch's tracks:
+    device time per call (CUDA events) and PV efficiency against the
+    generator's vertices (section 3.1 matching)."""
+    import torch
+    import oracle.metrics as MET
+    E = ev.n_events
+    pvo = V.velo.alloc_pv_output(E, 64 * E, device=dev)
+    params = V.velo.PVParams()
+    sptr = stream.cuda_stream
+    V.velo.velo_find_pvs(rec.handle, E, out, params, pvo, sptr)
+    torch.cuda.synchronize()
+    t0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        t0[k].record(stream)
+        V.velo.velo_find_pvs(rec.handle, E, out, params, pvo, sptr)
+        t1[k].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in zip(t0, t1))
+    h = pvo.to_host(E)
+    s = MET.pv_summary(ev, h.pv_off, h.pv)
+    return {"ms_per_call": ms, "events_per_s": E / (ms / 1e3), "vertices": h.n_vertices,
+            "efficiency": s["efficiency"], "fake_rate": s["fake_rate"], "sigma_z_um": 1e3 * s["sigma_z_mm"],
+            "sigma_x_um": 1e3 * s["sigma_x_mm"], "efficiency_by_multiplicity": s["efficiency_by_multiplicity"],
+            "kernels_per_call": 3}
+
+
+def alu_bound(work: dict, n_events: int, n_sm: int, sm_mhz, track_ms: float, emit_ms: float) -> dict:
+    """The single-precision arithmetic of the method on this batch (the
+    oracle's work counts: the search by triplet with an exact phi index, and
+    the fit of the output tracks) against the FP32 peak of the GPU's CUDA
+    cores (SMs x 128 lanes x 2 flops per fused multiply-add x the sampled SM
+    clock).  The path's arithmetic is explicitly rounded operation by
+    operation, so it cannot fuse: its attainable rate is half that peak."""
+    import oracle
+    f = oracle.algorithmic_flops(work)
+    mhz = float(sm_mhz) if sm_mhz else 2070.0
+    peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+    search = f["search"] / (track_ms / 1e3) / 1e12
+    fit = f["fit"] / (emit_ms / 1e3) / 1e12
+    return {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+            "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (sampled)",
+            "tracking": {"achieved": search, "frac": search / peak, "flops": f["search"],
+                         "flops_per_event": f["search"] / n_events},
+            "fit_in_emit": {"achieved": fit, "frac": fit / peak, "flops": f["fit"],
+                            "flops_per_event": f["fit"] / n_events},
+            "work": work}
 
 
 def run_ours(args):
@@ -348,6 +578,8 @@ def run_ours(args):
     value = aggregate_rate(ws, ev.n_events, args.steps, total_s)
 
     gpu_res = out.to_host(ev.n_events) if rank == 0 and ws == 1 else None
+    legs = rank == 0 and ws == 1 and not args.no_legs
+    pv_res = pv_leg(V, rec, ev, out, dev, stream, max(3, args.steps // 2)) if legs else None
 
     # end to end: through the serving API (the batch as a backlog of
     # requests, copies overlapping other requests' kernels), and through the
@@ -392,10 +624,19 @@ def run_ours(args):
     }
     line["serving"] = serve_res
     if ws == 1:
-        line["cpu_baseline"] = cpu_baseline(geom, ev.subset(0, min(ev.n_events, N_EVENTS)), gpu_res)
+        kept = {}
+        line["cpu_baseline"] = cpu_baseline(geom, ev.subset(0, min(ev.n_events, N_EVENTS)), gpu_res, kept)
         q = line["cpu_baseline"].get("gpu_track_quality")
         if q:
             line["ghost_rate"] = q["ghost_rate"]
+        if "oracle" in kept:
+            line["roofline"]["alu"] = alu_bound(kept["oracle"].work, ev.n_events, desc["sms"],
+                                                line["clocks"].get("sm_mhz"), statistics.mean(reco_ms), stage[3])
+        if legs:
+            line["pv"] = pv_res
+            line["uneven"] = uneven_leg(V, geom, dev, stream, flush, max(3, args.steps // 2), 3)
+            line["classifier"] = classifier_leg(V, geom, ev, d, dev, stream, flush, max(3, args.steps // 2), 3,
+                                                kept["oracle"])
     line["p99_latency_ms"] = serve_res["load_1.2x"]["p99_ms"]
     print(json.dumps(line), flush=True)
     return 0
@@ -473,7 +714,9 @@ def main():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="nominal",
                     help="nominal: the 10,000-event throughput batch; uneven: 50,000 events of mixed pileup")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
-                    help="duration of the Poisson arrival stream at 1.2x the sustainable rate")
+                    help="duration of the Poisson arrival stream at 1.2x the server's capacity")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the PV, uneven-batch and classifier legs (the headline line only)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -32,6 +32,27 @@ NSTATE = 13
 STATE_NAMES = ("x", "y", "z", "tx", "ty", "c00", "c20", "c22", "c11", "c31", "c33", "chi2", "score")
 FLAG_KEEP = 1
 FLAG_3HIT = 2
+# Work counts of a reconstruction (the search by triplet with an exact phi
+# index, and the fit of the output tracks), and the single-precision
+# operations each unit costs as the method is written: an extrapolation of a
+# track's last two hits (3 sub, 2 div, 1 sub, 2 mul, 2 add); a candidate hit
+# (phi test: 5 mul, 1 add, 1 sub; scatter: 2 sub, 2 mul, 1 add); a seed pair
+# (phi test 7; slopes 2 sub, 2 div) and, within the slope cut, its
+# extrapolation (2 mul, 2 add); a seed triple (phi test 7, scatter 5); a fit
+# per hit (least-squares line 12, two Kalman updates of 27) and per track
+# (means, slopes, scattering, start state and beamline step, about 40).
+WORK_NAMES = ("fwd_tracks", "fwd_candidates", "seed_middle_hits", "seed_pairs", "seed_pairs_in_slope",
+              "seed_triples", "fit_hits", "fit_tracks")
+WORK_FLOPS = {"fwd_tracks": 10, "fwd_candidates": 12, "seed_middle_hits": 0, "seed_pairs": 11,
+              "seed_pairs_in_slope": 4, "seed_triples": 12, "fit_hits": 66, "fit_tracks": 40}
+
+
+def algorithmic_flops(work: dict) -> dict:
+    """Single-precision operations of the method's work counts: search by
+    triplet, fit, and total."""
+    search = sum(WORK_FLOPS[k] * work[k] for k in WORK_NAMES[:6])
+    fit = WORK_FLOPS["fit_hits"] * work["fit_hits"] + WORK_FLOPS["fit_tracks"] * work["fit_tracks"]
+    return {"search": search, "fit": fit, "total": search + fit}
 
 
 class _Geo(ctypes.Structure):
@@ -76,7 +97,7 @@ class _Result(ctypes.Structure):
                 ("states", _P(ctypes.c_float)), ("ndof", _P(ctypes.c_uint32)),
                 ("flags", _P(ctypes.c_uint32)), ("seed_s", _P(ctypes.c_float)),
                 ("event_status", _P(ctypes.c_uint32)), ("n_pixels", ctypes.c_uint64),
-                ("pix_cluster", _P(ctypes.c_int32))]
+                ("pix_cluster", _P(ctypes.c_int32)), ("work", ctypes.c_uint64 * 8)]
 
 
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-pthread"]
@@ -160,6 +181,7 @@ class OracleResult:
     seed_s: np.ndarray
     event_status: np.ndarray
     pix_cluster: np.ndarray  # int32 [n_pixels] event-local cluster id per raw pixel
+    work: dict | None = None  # the method's work counts (see algorithmic_flops)
 
     @property
     def n_tracks(self) -> int:
@@ -206,7 +228,8 @@ def reconstruct(geom, events, params: Params | None = None, n_threads: int = 1,
             states=arr(r.states, nt * NSTATE, np.float32, (nt, NSTATE)),
             ndof=arr(r.ndof, nt, np.uint32), flags=arr(r.flags, nt, np.uint32),
             seed_s=arr(r.seed_s, nt, np.float32), event_status=arr(r.event_status, ne, np.uint32),
-            pix_cluster=arr(r.pix_cluster, int(r.n_pixels), np.int32))
+            pix_cluster=arr(r.pix_cluster, int(r.n_pixels), np.int32),
+            work=dict(zip(WORK_NAMES, (int(x) for x in r.work))))
     finally:
         lib.oracle_free(ctypes.byref(r))
     del keep

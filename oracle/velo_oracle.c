@@ -51,6 +51,15 @@
 
 #define OR_MAX_MODULES 64
 #define OR_NSTATE 13
+/* Work counters of the search by triplet and the fit (the method's own work
+ * with an exact phi index: only phi-compatible hits are examined), summed
+ * over the events of a call:
+ *   0 phase-A track extrapolations, 1 phase-A phi-compatible candidates,
+ *   2 phase-B unused middle hits, 3 phase-B (b, a) pairs with a unused and
+ *   phi-compatible, 4 of those within the slope cut (extrapolated),
+ *   5 phase-B (b, a, c) triples with c unused and phi-compatible with b,
+ *   6 hits of output tracks (fitted), 7 output tracks. */
+#define OR_NWORK 8
 
 typedef struct or_geometry {
   uint32_t n_modules, sensors_per_module, n_cols, n_rows;
@@ -96,6 +105,7 @@ typedef struct or_result {
   uint32_t *event_status; /* bit 0: input error (pixel outside the sensor) */
   uint64_t n_pixels;
   int32_t *pix_cluster;   /* [n_pixels] event-local cluster id of each raw pixel, -1 if invalid */
+  uint64_t work[OR_NWORK];
 } or_result;
 
 /* ------------------------------------------------------------------------ */
@@ -116,6 +126,7 @@ typedef struct {
   uint32_t nout;
   uint32_t *out_idx;
   uint32_t *keep;
+  uint64_t work[OR_NWORK];
   uint32_t status;
 } evwork;
 
@@ -277,6 +288,7 @@ static void track_event(const or_geometry *g, const or_params *p, uint64_t shuff
       uint32_t t = tord[k];
       append[t] = -1;
       if (!w->active[t]) continue;
+      w->work[0]++;
       int32_t l = w->hits[t][w->n[t] - 1], q = w->hits[t][w->n[t] - 2];
       float zl = Z[w->module[l]], zq = Z[w->module[q]];
       float tx = (w->x[q] - w->x[l]) / (zq - zl);
@@ -289,6 +301,7 @@ static void track_event(const or_geometry *g, const or_params *p, uint64_t shuff
       for (uint32_t j = 0; j < h1 - h0; ++j) {
         uint32_t h = h0 + ord[j];
         if (!phi_ok(w->x[l], w->y[l], w->x[h], w->y[h], p->tan_phi_tol)) continue;
+        w->work[1]++;
         float dx = w->x[h] - xp;
         float dy = w->y[h] - yp;
         float s = dx * dx + dy * dy;
@@ -326,16 +339,19 @@ static void track_event(const or_geometry *g, const or_params *p, uint64_t shuff
     for (uint32_t kb = 0; kb < b1 - b0; ++kb) {
       uint32_t b = b0 + ord[kb];
       if (used[b]) continue;
+      w->work[2]++;
       int32_t ba = -1, bc = -1;
       float bs = 0.0f;
       for (uint32_t ka = 0; ka < a1 - a0; ++ka) {
         uint32_t a = a0 + ord2[ka];
         if (used[a]) continue;
         if (!phi_ok(w->x[a], w->y[a], w->x[b], w->y[b], p->tan_phi_tol)) continue;
+        w->work[3]++;
         float dzab = Z[i + 2] - Z[i + 1];
         float tx = (w->x[a] - w->x[b]) / dzab;
         float ty = (w->y[a] - w->y[b]) / dzab;
         if (fabsf(tx) > p->max_slope || fabsf(ty) > p->max_slope) continue;
+        w->work[4]++;
         float dzc = Z[i] - Z[i + 1];
         float xp = w->x[b] + tx * dzc;
         float yp = w->y[b] + ty * dzc;
@@ -343,6 +359,7 @@ static void track_event(const or_geometry *g, const or_params *p, uint64_t shuff
           uint32_t c = h0 + ord3[kc];
           if (used[c]) continue;
           if (!phi_ok(w->x[b], w->y[b], w->x[c], w->y[c], p->tan_phi_tol)) continue;
+          w->work[5]++;
           float dx = w->x[c] - xp;
           float dy = w->y[c] - yp;
           float s = dx * dx + dy * dy;
@@ -527,6 +544,7 @@ typedef struct {
   uint32_t e0, e1;
   evout *out;
   int32_t *pix_cluster;
+  uint64_t work[OR_NWORK];
 } job_t;
 
 static void run_event(const job_t *j, uint32_t e, evwork *w) {
@@ -571,6 +589,8 @@ static void run_event(const job_t *j, uint32_t e, evwork *w) {
     o->tn[k] = w->n[t];
     for (uint32_t h = 0; h < w->n[t]; ++h) o->th[hp++] = (uint32_t)w->hits[t][h];
     fit_track(j->g, j->p, w, w->hits[t], w->n[t], o->ts + (size_t)k * OR_NSTATE, &o->tndof[k]);
+    w->work[6] += w->n[t];
+    w->work[7]++;
     o->tflags[k] = (w->keep[t] ? 1u : 0u) | (w->n[t] == 3 ? 2u : 0u);
     o->tseed[k] = w->seed_s[t];
   }
@@ -581,6 +601,7 @@ static void *run_job(void *arg) {
   evwork w;
   memset(&w, 0, sizeof(w));
   for (uint32_t e = j->e0; e < j->e1; ++e) run_event(j, e, &w);
+  memcpy(j->work, w.work, sizeof(w.work));
   free(w.x); free(w.y); free(w.key); free(w.npix); free(w.module);
   free(w.hits); free(w.n); free(w.skip); free(w.active); free(w.seed_s);
   free(w.out_idx); free(w.keep);
@@ -608,7 +629,7 @@ int oracle_reconstruct(const or_geometry *g, const or_params *p, const or_option
   pthread_t *th = calloc(nt, sizeof(pthread_t));
   for (uint32_t t = 0; t < nt; ++t) {
     jobs[t] = (job_t){g, p, o, sensor_off, col, row, (uint32_t)((uint64_t)n_events * t / nt),
-                      (uint32_t)((uint64_t)n_events * (t + 1) / nt), out, r->pix_cluster};
+                      (uint32_t)((uint64_t)n_events * (t + 1) / nt), out, r->pix_cluster, {0}};
     if (nt == 1) run_job(&jobs[t]);
     else pthread_create(&th[t], NULL, run_job, &jobs[t]);
   }
@@ -616,6 +637,8 @@ int oracle_reconstruct(const or_geometry *g, const or_params *p, const or_option
     for (uint32_t t = 0; t < nt; ++t) pthread_join(th[t], NULL);
 
   r->n_events = n_events;
+  for (uint32_t t = 0; t < nt; ++t)
+    for (int k = 0; k < OR_NWORK; ++k) r->work[k] += jobs[t].work[k];
   for (uint32_t e = 0; e < n_events; ++e) {
     r->n_clusters += out[e].nc; r->n_tracks += out[e].nt; r->n_track_hits += out[e].nh;
   }

@@ -392,3 +392,32 @@ def test_fewest_modules(n_modules):
     tracks = r.event_tracks(0)
     assert [[mods[h] for h in t] for t in tracks] == [list(range(n_modules - 1, -1, -1))]
     assert tracks == brute_force(r.cl_x, r.cl_y, mods, g.module_z, p)
+
+
+def test_work_counts_by_hand():
+    """The work counters (the method's own work with an exact phi index),
+    counted by hand on the exact-tie events.  Seed tie (hits in modules 5, 4
+    and two in 3): round 3 seeds with one middle hit, one pair, two triples;
+    rounds 2 and 1 extend the track into empty modules (two extrapolations, no
+    candidates) and round 2 has one unused middle hit with no partner.
+    Forward tie (5, 4, 3 and two in 2): one seed triple; the track is
+    extrapolated in rounds 2, 1 and 0, with two candidates in round 2; round 1
+    has one unused middle hit."""
+    g = hand_events.exact_geometry()
+    want = [dict(fwd_tracks=2, fwd_candidates=0, seed_middle_hits=2, seed_pairs=1, seed_pairs_in_slope=1,
+                 seed_triples=2, fit_hits=3, fit_tracks=1),
+            dict(fwd_tracks=3, fwd_candidates=2, seed_middle_hits=2, seed_pairs=1, seed_pairs_in_slope=1,
+                 seed_triples=1, fit_hits=4, fit_tracks=1)]
+    for hits, w in zip((hand_events.SEED_TIE, hand_events.FORWARD_TIE), want):
+        r = oracle.reconstruct(g, hand_events.pixel_events(g, [hits]))
+        assert r.work == w
+
+
+def test_work_counts_independent_of_schedule(geom, cfg0_events, cfg0_oracle):
+    ev = cfg0_events.subset(0, 40)
+    a = oracle.reconstruct(geom, ev, n_threads=1)
+    b = oracle.reconstruct(geom, ev, n_threads=7, shuffle_seed=5)
+    assert a.work == b.work and a.work["fit_tracks"] == a.n_tracks
+    assert a.work["fit_hits"] == int(a.hit_off[-1])
+    f = oracle.algorithmic_flops(a.work)
+    assert f["total"] == f["search"] + f["fit"] > 0
