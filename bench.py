@@ -16,8 +16,11 @@ one JSON line (see the keys below), which also carries:
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--serve-seconds S] [--no-legs]
 
-Workload: 10,000 synthetic events (seed 1; each rank r of a multi-GPU run
-takes seed 1 + 100 r, so per-GPU work is fixed: weak scaling).
+Workload: 10,000 synthetic events (seed 1).  On N GPUs (``--scaling
+strong``, the default) the batch is split into N event ranges of equal pixel
+counts, one per rank, and the rate counts the whole batch over the slowest
+rank's time; with ``--scaling weak`` each rank r takes its own batch of seed
+1 + 100 r instead.  No collective is on the data path either way.
 ``--impl reference`` times the CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -89,6 +92,20 @@ def shard_config(cfg_index: int, rank: int):
     import velo_synth
     cfg = velo_synth.config(cfg_index)
     return velo_synth.config(cfg_index, seed=cfg.seed + 100 * rank)
+
+
+def rank_workload(cfg_index: int, rank: int, world_size: int, scaling: str):
+    """(events of this rank, events of the whole job per step).  Strong
+    scaling: one batch split into contiguous event ranges of equal pixel
+    counts (shard.partition); weak: a batch of its own per rank."""
+    import velo_synth
+    from paper_1912_09161_gb300 import shard
+    if scaling == "weak" or world_size == 1:
+        ev = velo_synth.generate(shard_config(cfg_index, rank))
+        return ev, ev.n_events * world_size
+    full = velo_synth.generate(velo_synth.config(cfg_index))
+    e0, e1 = shard.partition(full.sensor_off, full.n_sensors, world_size)[rank]
+    return full.subset(e0, e1), full.n_events
 
 
 def aggregate_rate(world_size: int, events_per_rank: int, steps: int, slowest_s: float) -> float:
@@ -220,7 +237,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "sample_events_per_step": REF_SAMPLE},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"first {REF_SAMPLE} events of the workload per step"},
@@ -533,7 +550,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     geom = velo_synth.geometry()
     cfg_index, workload = WORKLOADS[args.workload]
-    ev = velo_synth.generate(shard_config(cfg_index, rank))
+    ev, job_events = rank_workload(cfg_index, rank, ws, args.scaling)
     V.load_library()
     rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
     d = V.upload_events(ev, dev)
@@ -575,7 +592,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     rc = rec.sync_status(sptr)
     total_s = _max_over_ranks(sum(step_ms) / 1e3, dist)
-    value = aggregate_rate(ws, ev.n_events, args.steps, total_s)
+    value = aggregate_rate(1, job_events, args.steps, total_s)
 
     gpu_res = out.to_host(ev.n_events) if rank == 0 and ws == 1 else None
     legs = rank == 0 and ws == 1 and not args.no_legs
@@ -584,9 +601,9 @@ def run_ours(args):
     # end to end: through the serving API (the batch as a backlog of
     # requests, copies overlapping other requests' kernels), and through the
     # synchronous host-buffer entry point
-    single = _e2e(V, rec, ev, dev, args, dist, ws, sptr)
+    single = _e2e(V, rec, ev, dev, args, dist, job_events, sptr)
     tot = out.totals.cpu().numpy().view(np.uint32)
-    e2e = _e2e_server(geom, ev, args, dist, ws, int(tot[0]), int(tot[1]))
+    e2e = _e2e_server(geom, ev, args, dist, job_events, int(tot[0]), int(tot[1]))
     e2e["single_call"] = single
 
     # continuous-batching serving loop (per GPU; every rank serves its own stream)
@@ -603,12 +620,13 @@ def run_ours(args):
         return 0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True, "scaling": args.scaling,
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload, "n_events": ev.n_events, "pixels_per_event": ev.n_pixels / ev.n_events,
+        "config": {"workload": workload, "n_events": job_events, "events_this_rank": ev.n_events,
+                   "pixels_per_event": ev.n_pixels / ev.n_events,
                    "schedule": {"autotuned": tuned, "autotune_best_ms": tuned_ms, "cuda_graph": True},
                    "l2": "flushed between steps (256 MiB device write, untimed); inputs 190 MB > L2",
-                   "parallelism": f"events sharded over {ws} GPU(s), no collective",
+                   "parallelism": f"events sharded over {ws} GPU(s) ({args.scaling} scaling), no collective",
                    "launch": desc, "status": rc},
         "roofline": {"bound": "hbm",
                      "kernel": "tracking: track_ring_kernel (module-window class) and track_kernel (whole-event "
@@ -642,7 +660,7 @@ def run_ours(args):
     return 0
 
 
-def _e2e(V, rec, ev, dev, args, dist, ws, sptr) -> dict:
+def _e2e(V, rec, ev, dev, args, dist, job_events, sptr) -> dict:
     import torch
     ns = ev.n_sensors
     so = torch.from_numpy(ev.sensor_off.view(np.int32)).pin_memory()
@@ -666,11 +684,11 @@ def _e2e(V, rec, ev, dev, args, dist, ws, sptr) -> dict:
     nt, nh = int(tot[0]), int(tot[1])
     h2d = int(so.numel() * 4 + col.numel() * 2 + row.numel() * 2)
     d2h = 4 * (ev.n_events + 1) + 4 * (nt + 1) + 4 * nh + 52 * nt + nt + 4 * ev.n_events + 16
-    return {"value": ws * ev.n_events * n / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    return {"value": job_events * n / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "status": rc, "api": "velo_reconstruct_host (pinned host buffers)"}
 
 
-def _e2e_server(geom, ev, args, dist, ws, n_tracks: int, n_hits: int) -> dict:
+def _e2e_server(geom, ev, args, dist, job_events, n_tracks: int, n_hits: int) -> dict:
     """End to end through the serving API: the batch cut into equal requests
     of at most 6,250 events (four at least), all arriving at once, on a
     server of four slots (``velo_server_replay``).  Every step copies each
@@ -700,7 +718,7 @@ def _e2e_server(geom, ev, args, dist, ws, n_tracks: int, n_hits: int) -> dict:
     r = len(sizes)
     h2d = 4 * (E * ev.n_sensors + r) + 4 * int(ev.n_pixels)
     d2h = 4 * (E + r) + 4 * (n_tracks + r) + 4 * n_hits + 52 * n_tracks + n_tracks + 4 * E + 16 * r
-    return {"value": ws * E * n / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+    return {"value": job_events * n / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "api": f"velo_server_replay: the batch as {r} requests of {chunk} events on 4 slots "
                    "(pinned host inputs, results in pinned host buffers)"}
 
@@ -715,6 +733,8 @@ def main():
                     help="nominal: the 10,000-event throughput batch; uneven: 50,000 events of mixed pileup")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="duration of the Poisson arrival stream at 1.2x the server's capacity")
+    ap.add_argument("--scaling", choices=("strong", "weak"), default="strong",
+                    help="strong: one batch split over the GPUs by pixel count; weak: a batch per GPU")
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the PV, uneven-batch and classifier legs (the headline line only)")
     args = ap.parse_args()
