@@ -183,7 +183,7 @@ FixedPlan plan_fixed() {
 }
 
 struct WorkPlan {
-  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, hits, clx, cly, clk, total;
+  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, tev, hits, clx, cly, clk, total;
 };
 
 WorkPlan plan_work(const velo_config& c) {
@@ -197,6 +197,7 @@ WorkPlan plan_work(const velo_config& c) {
   a.lg = o; o = align256(o + 4ull * c.max_tracks);
   a.nh = o; o = align256(o + 2ull * c.max_tracks);
   a.ho = o; o = align256(o + 4ull * c.max_tracks);
+  a.tev = o; o = align256(o + 4ull * c.max_tracks);
   a.hits = o; o = align256(o + 4ull * c.max_track_hits);
   if (c.flags & VELO_CFG_CLUSTERS) {
     a.clx = o; o = align256(o + 4ull * c.max_pixels);
@@ -220,6 +221,7 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
   w.tr_logit = (float*)(base + a.lg);
   w.tr_nhits = (uint16_t*)(base + a.nh);
   w.tr_hitoff = (uint32_t*)(base + a.ho);
+  w.tr_event = (uint32_t*)(base + a.tev);
   w.tr_hits = (uint32_t*)(base + a.hits);
   w.cap_tracks = (uint32_t)c.max_tracks;
   w.cap_hits = (uint32_t)c.max_track_hits;

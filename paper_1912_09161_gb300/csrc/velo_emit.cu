@@ -82,63 +82,26 @@ cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output
 }
 
 // ---------------------------------------------------------------------------
-// emit: one block per event (grid-stride), one thread per track
+// emit: two kernels.
+//   emit_event_kernel -- one block per event (grid-stride): event status,
+//     hit ids and (on request) the cluster list;
+//   emit_fit_kernel   -- one thread per kept track over the whole batch
+//     (grid-stride over the scratch tracks, whose events are recorded by the
+//     tracking kernels): gathers the track's hits from the clustering output
+//     at every pass of the fit (no per-thread hit arrays) and writes its state.
 // ---------------------------------------------------------------------------
 constexpr int kEmitThreads = 128;
 
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
-                                                            DevParams par, EventsView ev, WorkView wk,
-                                                            velo_output out) {
-  __shared__ float s_z[kMaxModules];
-  __shared__ uint16_t s_cb[kMaxSensors + 1];  // canonical id of each sensor's first hit
-  __shared__ uint32_t s_so[kMaxSensors + 1];  // each sensor's first hit in the clustering output
-  const int ns = geo->n_sensors;
-  for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
-  const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
-  const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
-  const float kms = fit_kms(par);
+__device__ __forceinline__ bool event_fits(const EventRec& r, uint32_t o0, const velo_output& out) {
+  return (uint64_t)o0 + r.n_tracks <= out.cap_tracks && (uint64_t)r.out_hit_base + r.n_hits <= out.cap_hits;
+}
+
+__global__ void __launch_bounds__(kEmitThreads) emit_event_kernel(uint32_t n_events, WorkView wk, velo_output out) {
   for (uint32_t e = blockIdx.x; e < n_events; e += gridDim.x) {
-    __syncthreads();
-    for (int s = threadIdx.x; s <= ns; s += blockDim.x) {
-      s_cb[s] = wk.ev_cbase[(size_t)e * (kMaxSensors + 1) + s];
-      s_so[s] = ev.sensor_off[(size_t)e * ns + s];
-    }
-    __syncthreads();
     const EventRec r = wk.rec[e];
     const uint32_t o0 = out.track_off[e], h0 = r.out_hit_base;
     uint32_t status = r.status;
-    const bool fits = (uint64_t)o0 + r.n_tracks <= out.cap_tracks && (uint64_t)h0 + r.n_hits <= out.cap_hits;
-    if (fits) {
-      const size_t ocap = out.cap_tracks;
-      for (uint32_t k = threadIdx.x; k < r.n_tracks; k += blockDim.x) {
-        const uint32_t t = r.track_base + k;
-        const uint32_t nh = wk.tr_nhits[t];
-        const uint32_t hoff = wk.tr_hitoff[t];
-        // the track's hits from the clustering output, by canonical id
-        float2 xy[kMaxModules];
-        uint8_t md[kMaxModules];
-        for (uint32_t j = 0; j < nh; ++j) {
-          const uint32_t h = wk.tr_hits[r.hit_base + hoff + j];
-          const uint32_t id = h & 0xFFFFu, m = h >> 16, s0 = kSPM * m;
-          const uint32_t s = s0 + (id >= s_cb[s0 + 1]) + (id >= s_cb[s0 + 2]) + (id >= s_cb[s0 + 3]);
-          xy[j] = wk.prov[s_so[s] + (id - s_cb[s])];
-          md[j] = (uint8_t)m;
-        }
-        float st[12];
-        fit_track(
-            nh,
-            [&](uint32_t j, float& x, float& y, int& m) {
-              x = xy[j].x;
-              y = xy[j].y;
-              m = md[j];
-            },
-            s_z, sig2, kms, st);
-#pragma unroll
-        for (int q = 0; q < 12; ++q) out.states[q * ocap + o0 + k] = st[q];
-        out.states[12 * ocap + o0 + k] = use_mlp ? 1.0f / (1.0f + expf(-wk.tr_logit[t])) : 0.0f;
-        out.ndof[o0 + k] = (uint8_t)(2 * nh - 4);
-        out.hit_off[o0 + k] = h0 + hoff;
-      }
+    if (event_fits(r, o0, out)) {
       for (uint32_t k = threadIdx.x; k < r.n_hits; k += blockDim.x)
         out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k] & 0xFFFFu;
     } else if (r.n_tracks) {
@@ -160,14 +123,64 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(uint32_t n_events, c
   }
 }
 
+__global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
+                                                                DevParams par, EventsView ev, WorkView wk,
+                                                                velo_output out) {
+  __shared__ float s_z[kMaxModules];
+  const int ns = geo->n_sensors;
+  for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
+  __syncthreads();
+  const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
+  const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
+  const float kms = fit_kms(par);
+  const uint32_t total = *(volatile uint32_t*)&wk.cnt->track_cursor;
+  const size_t ocap = out.cap_tracks;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total && t < wk.cap_tracks;
+       t += gridDim.x * blockDim.x) {
+    const uint32_t e = __ldg(&wk.tr_event[t]);
+    if (e >= n_events) continue;  // a slot of an event that ran out of scratch storage
+    const EventRec r = wk.rec[e];
+    const uint32_t o0 = out.track_off[e];
+    if (!event_fits(r, o0, out)) continue;
+    const uint32_t k = t - r.track_base;
+    const uint32_t nh = __ldg(&wk.tr_nhits[t]);
+    const uint32_t hoff = __ldg(&wk.tr_hitoff[t]);
+    const uint32_t* th = wk.tr_hits + r.hit_base + hoff;
+    const uint16_t* cb = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
+    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
+    float st[12];
+    fit_track(
+        nh,
+        [&](uint32_t j, float& x, float& y, int& m) {
+          // hit j from the clustering output, by module and canonical id
+          const uint32_t h = __ldg(&th[j]);
+          const uint32_t id = h & 0xFFFFu, mm = h >> 16, s0 = kSPM * mm;
+          const uint32_t s = s0 + (id >= __ldg(&cb[s0 + 1])) + (id >= __ldg(&cb[s0 + 2])) + (id >= __ldg(&cb[s0 + 3]));
+          const float2 v = __ldg(&wk.prov[__ldg(&so[s]) + (id - __ldg(&cb[s]))]);
+          x = v.x;
+          y = v.y;
+          m = (int)mm;
+        },
+        s_z, sig2, kms, st);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) out.states[q * ocap + o0 + k] = st[q];
+    out.states[12 * ocap + o0 + k] = use_mlp ? 1.0f / (1.0f + expf(-__ldg(&wk.tr_logit[t]))) : 0.0f;
+    out.ndof[o0 + k] = (uint8_t)(2 * nh - 4);
+    out.hit_off[o0 + k] = r.out_hit_base + hoff;
+  }
+}
+
 cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
                         const WorkView& wk, const velo_output& out, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;
-  // up to 2048 threads' worth of blocks per SM on a 152-SM part (a grid-stride
-  // loop covers any larger batch)
+  // up to 2048 threads' worth of blocks per SM on a 152-SM part (grid-stride
+  // loops cover any larger batch)
   constexpr uint32_t kMaxBlocks = 152u * (2048u / kEmitThreads);
   const int blocks = (int)(n_events < kMaxBlocks ? n_events : kMaxBlocks);
-  emit_kernel<<<blocks, kEmitThreads, 0, st>>>(n_events, geo, par, ev, wk, out);
+  emit_event_kernel<<<blocks, kEmitThreads, 0, st>>>(n_events, wk, out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  emit_fit_kernel<<<kMaxBlocks, kEmitThreads, 0, st>>>(n_events, geo, par, ev, wk, out);
   return cudaGetLastError();
 }
 

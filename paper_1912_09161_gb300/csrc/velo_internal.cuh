@@ -136,6 +136,7 @@ struct WorkView {
   float* tr_logit;               // [cap_tracks] classifier logit (0 without the classifier)
   uint16_t* tr_nhits;            // [cap_tracks]
   uint32_t* tr_hitoff;           // [cap_tracks] first hit, relative to the event's hit base
+  uint32_t* tr_event;            // [cap_tracks] event of the track
   uint32_t* tr_hits;             // [cap_hits] module << 16 | event-local canonical id
   // tracking-kernel hit slots per class: kMaxModules positions per candidate,
   // max_tracks candidates per CTA, one region per CTA of the class

@@ -523,7 +523,13 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
       atomicAdd(&wk.cnt->cls_pixels[cls], (unsigned long long)(ev.sensor_off[(size_t)(e + 1) * ns] - gbase));
     }
     __syncthreads();
-    if (s_misc[M_SKIP]) continue;
+    if (s_misc[M_SKIP]) {
+      // the event's scratch slots that exist stay unwritten: mark them, so
+      // that the fit kernel passes over them
+      for (uint32_t k = tid; k < K; k += NT)
+        if ((uint64_t)s_misc[M_TBASE] + k < wk.cap_tracks) wk.tr_event[s_misc[M_TBASE] + k] = kInv;
+      continue;
+    }
     const uint32_t tb = s_misc[M_TBASE], hb = s_misc[M_HBASE];
 
     // kept tracks to scratch in canonical order: their hits as module << 16 |
@@ -543,6 +549,7 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
       wk.tr_logit[o] = use_mlp ? t_seed[t] : 0.0f;
       wk.tr_nhits[o] = (uint16_t)n;
       wk.tr_hitoff[o] = t_hoff[r];
+      wk.tr_event[o] = e;
     }
   }
 }

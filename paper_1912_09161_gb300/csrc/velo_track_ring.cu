@@ -586,7 +586,13 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     atomicAdd(&wk.cnt->cls_pixels[cls], (unsigned long long)(ev.sensor_off[(size_t)(e + 1) * ns] - gbase));
   }
   __syncthreads();
-  if (s_misc[R_SKIP]) return;
+  if (s_misc[R_SKIP]) {
+    // the event's scratch slots that exist stay unwritten: mark them, so that
+    // the fit kernel passes over them
+    for (uint32_t k = tid; k < K; k += NT)
+      if ((uint64_t)s_misc[R_TBASE] + k < wk.cap_tracks) wk.tr_event[s_misc[R_TBASE] + k] = kInv;
+    return;
+  }
   const uint32_t tb = s_misc[R_TBASE], hb = s_misc[R_HBASE];
 
   // kept tracks to scratch in canonical order: their hits' canonical ids
@@ -601,6 +607,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     wk.tr_logit[o] = use_mlp ? mseed[t] : 0.0f;
     wk.tr_nhits[o] = (uint16_t)n;
     wk.tr_hitoff[o] = t_hoff[r];
+    wk.tr_event[o] = e;
   }
 }
 

@@ -330,3 +330,51 @@ def test_global_event_cut(V, geom):
     assert np.all(res.event_status[over] == V.velo.EV_GEC) and np.all(res.event_status[~over] == 0)
     assert int(res.totals[3]) == 0
     assert_parity(res, orc)
+
+
+def test_capacity_truncation(V, geom, cfg0_events, cfg0_oracle):
+    """Storage that runs out: (1) the handle's track scratch (max_tracks 600
+    for about 1,400 tracks) -- events that got no room are marked
+    VELO_EV_TRUNCATED with no tracks, the status is VELO_ERR_CAPACITY, every
+    other event equals the oracle; (2) the caller's output arrays (room for
+    500 tracks) -- totals give the sizes needed, events beyond the room are
+    marked VELO_EV_TRUNCATED, the ones before it equal the oracle."""
+    ev = cfg0_events
+    orc = cfg0_oracle
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, max_tracks=600,
+                          max_track_hits=600 * 16, clusters=True)
+    try:
+        d = V.upload_events(ev)
+        ct, ch, cc = V.suggested_caps(ev.n_events, ev.n_pixels)
+        out = V.alloc_output(ev.n_events, ct, ch, cc)
+        rec.reconstruct(d, out)
+        rc = rec.sync_status()
+        res = out.to_host(ev.n_events)
+    finally:
+        rec.close()
+    assert rc == V.velo.VELO_ERR_CAPACITY
+    trunc = (res.event_status & V.velo.EV_TRUNCATED) != 0
+    assert trunc.any() and not trunc.all()
+    for e in range(ev.n_events):
+        if trunc[e]:
+            assert res.track_off[e + 1] == res.track_off[e]
+        else:
+            assert res.event_tracks(e) == orc.event_tracks(e)
+            g0, g1 = int(res.track_off[e]), int(res.track_off[e + 1])
+            o0 = int(orc.track_off[e])
+            assert np.array_equal(res.states[g0:g1, :12].view(np.uint32), orc.states[o0:o0 + g1 - g0, :12].view(np.uint32))
+    # the caller's output too small
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
+    try:
+        out = V.alloc_output(ev.n_events, 500, 500 * 16, 0)
+        rec.reconstruct(V.upload_events(ev), out)
+        rc = rec.sync_status()
+        res = out.to_host(ev.n_events)
+    finally:
+        rec.close()
+    assert rc == V.velo.VELO_ERR_CAPACITY
+    assert int(res.totals[0]) == orc.n_tracks and int(res.totals[1]) == int(orc.hit_off[-1])
+    fits = res.track_off[1:].astype(np.int64) <= 500
+    assert np.all(((res.event_status & V.velo.EV_TRUNCATED) != 0) == ~fits)
+    for e in np.nonzero(fits)[0]:
+        assert res.event_tracks(int(e)) == orc.event_tracks(int(e))
