@@ -325,6 +325,23 @@ int velo_get_stats(velo_handle *h, velo_stats *out);
 int velo_describe(const velo_handle *h, char *buf, size_t n);
 
 /*
+ * Velo-only Kalman filter with a momentum per track (paper section 2.3.5: the
+ * Velo segment refitted with the momentum of the full track, which the
+ * downstream detectors measure; here the caller supplies it).  Refits the
+ * tracks of a velo_reconstruct output: `tracks` must hold hit offsets, hit
+ * ids and the cluster list (a handle created with VELO_CFG_CLUSTERS and
+ * cluster output requested); p_gev [n_tracks] (device) is each track's
+ * momentum in GeV.  The filter is the one of section 2.3.1 with the slope
+ * kick per module crossed set to ms_coeff * 1e-3 / p instead of the
+ * constant-pT value; a track with p <= 0 keeps the constant-pT fit.  Writes
+ * states [VELO_NSTATE][states_pitch] (device, states_pitch >= cap_tracks):
+ * rows 0-11 as velo_output.states, row 12 the momentum used (0 for the
+ * constant-pT fit).  Enqueued on `stream`.  Errors: VELO_ERR_INPUT.
+ */
+int velo_refit_momentum(velo_handle *h, uint32_t n_events, const velo_output *tracks, const float *p_gev,
+                        float *states, uint32_t states_pitch, void *stream);
+
+/*
  * Primary-vertex finding (paper section 2.3.1, last step: vertices from a
  * histogram of the tracks' closest approach to the beamline; every track is
  * weighted to every vertex, so all candidates are fitted in parallel).  It

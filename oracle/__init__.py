@@ -126,6 +126,8 @@ def _load():
         lib.oracle_fit.argtypes = [_P(_Geo), _P(_Params), ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
                                    ctypes.c_void_p]
+        lib.oracle_refit_momentum.argtypes = [_P(_Geo), _P(_Params), ctypes.c_uint32] + [ctypes.c_void_p] * 9
+        lib.oracle_refit_momentum.restype = None
         lib.oracle_pv.argtypes = [_P(_PVParams), ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_pv.restype = ctypes.c_int
@@ -315,3 +317,24 @@ def find_pvs(track_off, states, params: PVParams | None = None) -> PVResult:
     if rc != 0:
         raise ValueError("oracle_pv: bad parameters")
     return PVResult(n_events, pv_off, pv[:int(pv_off[-1])].copy(), status[:n_events].copy())
+
+
+def refit_momentum(geom, result, p_track, params: Params | None = None) -> np.ndarray:
+    """States [n_tracks, 13] of a reconstruction's tracks refitted with a
+    momentum per track (GeV; <= 0 keeps the constant-pT noise): the Velo-only
+    Kalman filter with the full track's momentum (section 2.3.5).  ``result``
+    needs cluster_off, cl_x, cl_y, cl_key, track_off, hit_off, hit_ids."""
+    lib = _load()
+    params = params or Params()
+    gc, keep = _geo_c(geom)
+    arrs = [np.ascontiguousarray(getattr(result, k), dt) for k, dt in
+            (("cluster_off", np.uint32), ("cl_x", np.float32), ("cl_y", np.float32), ("cl_key", np.uint32),
+             ("track_off", np.uint32), ("hit_off", np.uint32), ("hit_ids", np.uint32))]
+    pt = np.ascontiguousarray(p_track, np.float32)
+    n_tracks = int(arrs[4][-1])
+    assert len(pt) >= n_tracks
+    st = np.zeros((max(n_tracks, 1), NSTATE), np.float32)
+    lib.oracle_refit_momentum(ctypes.byref(gc), ctypes.byref(params._c()), len(arrs[4]) - 1,
+                              *[a.ctypes.data for a in arrs], pt.ctypes.data, st.ctypes.data)
+    del keep
+    return st[:n_tracks]

@@ -472,8 +472,12 @@ static void propagate(proj_t *s, float dz) {
 }
 
 /* Fits one track; hits given in stored (decreasing module) order. */
+/* p_track > 0: the track's own momentum (GeV) sets the scattering noise,
+ * ms_coeff * 1e-3 / p_track per module crossed (the Velo-only Kalman filter
+ * with the momentum of the full track, section 2.3.5); otherwise the
+ * constant transverse momentum of section 2.3.1. */
 static void fit_track(const or_geometry *g, const or_params *p, const evwork *w, const int32_t *hits,
-                      uint32_t n, float *st, uint32_t *ndof) {
+                      uint32_t n, float p_track, float *st, uint32_t *ndof) {
   float xs[OR_MAX_MODULES], ys[OR_MAX_MODULES], zs[OR_MAX_MODULES], dm[OR_MAX_MODULES];
   for (uint32_t k = 0; k < n; ++k) {
     xs[k] = w->x[hits[k]];
@@ -499,6 +503,7 @@ static void fit_track(const or_geometry *g, const or_params *p, const evwork *w,
   float sin_t = sqrtf(t2 / (1.0f + t2));
   float kms = p->ms_coeff * 0.001f / p->pt_nominal;
   float sig_ms = kms * sin_t;
+  if (p_track > 0.0f) sig_ms = (p->ms_coeff * 0.001f) / p_track;
   float q = sig_ms * sig_ms;
   float sig2 = p->sigma_meas * p->sigma_meas;
   proj_t fx = kalman_1d(xs, zs, dm, n, sig2, q);
@@ -588,7 +593,7 @@ static void run_event(const job_t *j, uint32_t e, evwork *w) {
     uint32_t t = w->out_idx[k];
     o->tn[k] = w->n[t];
     for (uint32_t h = 0; h < w->n[t]; ++h) o->th[hp++] = (uint32_t)w->hits[t][h];
-    fit_track(j->g, j->p, w, w->hits[t], w->n[t], o->ts + (size_t)k * OR_NSTATE, &o->tndof[k]);
+    fit_track(j->g, j->p, w, w->hits[t], w->n[t], -1.0f, o->ts + (size_t)k * OR_NSTATE, &o->tndof[k]);
     w->work[6] += w->n[t];
     w->work[7]++;
     o->tflags[k] = (w->keep[t] ? 1u : 0u) | (w->n[t] == 3 ? 2u : 0u);
@@ -703,5 +708,37 @@ void oracle_fit(const or_geometry *g, const or_params *p, const float *x, const 
   int32_t hits[OR_MAX_MODULES];
   w.x = (float *)x; w.y = (float *)y; w.module = (uint32_t *)module;
   for (uint32_t k = 0; k < n && k < OR_MAX_MODULES; ++k) hits[k] = (int32_t)k;
-  fit_track(g, p, &w, hits, n, state, ndof);
+  fit_track(g, p, &w, hits, n, -1.0f, state, ndof);
+}
+
+/* Refits reconstructed tracks with a momentum per track (p_track[t] > 0; a
+ * track with p_track[t] <= 0 keeps the constant-pT noise): hits by event-local
+ * id from the cluster list (cluster_off, cl_x, cl_y, cl_key), tracks as
+ * track_off / hit_off / hit_ids.  Writes states [n_tracks][13] (row 12 = the
+ * momentum used, 0 for the constant-pT fit). */
+void oracle_refit_momentum(const or_geometry *g, const or_params *p, uint32_t n_events, const uint32_t *cluster_off,
+                           const float *cl_x, const float *cl_y, const uint32_t *cl_key, const uint32_t *track_off,
+                           const uint32_t *hit_off, const uint32_t *hit_ids, const float *p_track, float *states) {
+  float xs[OR_MAX_MODULES], ys[OR_MAX_MODULES];
+  uint32_t ms[OR_MAX_MODULES];
+  int32_t hits[OR_MAX_MODULES];
+  for (uint32_t k = 0; k < OR_MAX_MODULES; ++k) hits[k] = (int32_t)k;
+  evwork w;
+  memset(&w, 0, sizeof(w));
+  w.x = xs; w.y = ys; w.module = ms;
+  for (uint32_t e = 0; e < n_events; ++e) {
+    for (uint32_t t = track_off[e]; t < track_off[e + 1]; ++t) {
+      uint32_t n = hit_off[t + 1] - hit_off[t];
+      if (n > OR_MAX_MODULES) n = OR_MAX_MODULES;
+      for (uint32_t k = 0; k < n; ++k) {
+        uint32_t c = cluster_off[e] + hit_ids[hit_off[t] + k];
+        xs[k] = cl_x[c];
+        ys[k] = cl_y[c];
+        ms[k] = (cl_key[c] >> 16) / g->sensors_per_module;
+      }
+      uint32_t ndof = 0;
+      fit_track(g, p, &w, hits, n, p_track[t], states + (size_t)t * OR_NSTATE, &ndof);
+      states[(size_t)t * OR_NSTATE + 12] = p_track[t] > 0.0f ? p_track[t] : 0.0f;
+    }
+  }
 }

@@ -801,6 +801,19 @@ int velo_reconstruct(velo_handle* h, const velo_events* events, const velo_outpu
   return enqueue(h, ev, wk, *out, st, false);
 }
 
+int velo_refit_momentum(velo_handle* h, uint32_t n_events, const velo_output* tracks, const float* p_gev,
+                        float* states, uint32_t states_pitch, void* stream) {
+  if (!h || !tracks || !p_gev || !states) return fail(VELO_ERR_INPUT, "velo_refit_momentum: null argument");
+  if (!tracks->track_off || !tracks->hit_off || !tracks->hit_ids || !tracks->cluster_off || !tracks->cl_x ||
+      !tracks->cl_y || !tracks->cl_key)
+    return fail(VELO_ERR_INPUT, "velo_refit_momentum: the tracks need hit and cluster arrays");
+  if (states_pitch < tracks->cap_tracks)
+    return fail(VELO_ERR_INPUT, "velo_refit_momentum: states pitch %u below cap_tracks %u", states_pitch,
+                tracks->cap_tracks);
+  CUDA_TRY(launch_refit(n_events, h->d_geo, h->par, *tracks, p_gev, states, states_pitch, (cudaStream_t)stream));
+  return VELO_OK;
+}
+
 void velo_pv_default_params(velo_pv_params* p) {
   if (!p) return;
   p->z_min = -300.0f;

@@ -170,6 +170,58 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
   }
 }
 
+// Refit of reconstructed tracks with a momentum per track: one thread per
+// track; hits by event-local id from the cluster list of the output.
+__global__ void __launch_bounds__(kEmitThreads) refit_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
+                                                             DevParams par, velo_output tr, const float* __restrict__ p_gev,
+                                                             float* __restrict__ states, uint32_t pitch) {
+  __shared__ float s_z[kMaxModules];
+  for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
+  __syncthreads();
+  const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
+  const float kms = fit_kms(par);
+  const float ms = fmul(par.ms_coeff, 0.001f);
+  const uint32_t total = tr.track_off[n_events];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total && t < tr.cap_tracks;
+       t += gridDim.x * blockDim.x) {
+    // the track's event: the last e with track_off[e] <= t
+    uint32_t lo = 0, hi = n_events - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(&tr.track_off[mid]) <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t c0 = __ldg(&tr.cluster_off[lo]), c1 = __ldg(&tr.cluster_off[lo + 1]);
+    const uint32_t h0 = __ldg(&tr.hit_off[t]), nh = __ldg(&tr.hit_off[t + 1]) - h0;
+    // tracks of an event whose outputs were truncated were never written
+    if ((__ldg(&tr.event_status[lo]) & VELO_EV_TRUNCATED) || nh < 3 || nh > (uint32_t)kMaxModules ||
+        (uint64_t)h0 + nh > tr.cap_hits || c1 > tr.cap_clusters || c1 <= c0)
+      continue;
+    const float p = __ldg(&p_gev[t]);
+    float st[12];
+    fit_track(
+        nh,
+        [&](uint32_t j, float& x, float& y, int& m) {
+          const uint32_t c = min(c0 + __ldg(&tr.hit_ids[h0 + j]), c1 - 1);
+          x = __ldg(&tr.cl_x[c]);
+          y = __ldg(&tr.cl_y[c]);
+          m = (int)((__ldg(&tr.cl_key[c]) >> 16) / kSPM);
+        },
+        s_z, sig2, kms, st, p > 0.0f ? fdiv(ms, p) : -1.0f);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) states[(size_t)q * pitch + t] = st[q];
+    states[(size_t)12 * pitch + t] = p > 0.0f ? p : 0.0f;
+  }
+}
+
+cudaError_t launch_refit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const velo_output& tracks,
+                         const float* p_gev, float* states, uint32_t pitch, cudaStream_t st) {
+  if (n_events == 0) return cudaSuccess;
+  refit_kernel<<<152u * (2048u / kEmitThreads), kEmitThreads, 0, st>>>(n_events, geo, par, tracks, p_gev, states,
+                                                                       pitch);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
                         const WorkView& wk, const velo_output& out, cudaStream_t st) {
   if (n_events == 0) return cudaSuccess;

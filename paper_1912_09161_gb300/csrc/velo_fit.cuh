@@ -14,9 +14,12 @@ namespace velo {
 // momentum; the final state goes to the closest approach to the beam axis.
 // hit(k, x, y, m) gives hit k (0 = highest z) of the n >= 3 hits; z_of[m] is
 // the z of module m.  out: x, y, z, tx, ty, c00, c20, c22, c11, c31, c33, chi2.
+// sig_ms_track > 0 replaces the constant-pT slope kick per module crossed by
+// a kick of the track's own (the Velo-only Kalman filter with the momentum of
+// the full track, section 2.3.5).
 template <class HitFn>
 __device__ __forceinline__ void fit_track(uint32_t n, HitFn hit, const float* z_of, float sig2, float kms,
-                                          float* out) {
+                                          float* out, float sig_ms_track = -1.0f) {
   float sz = 0.0f, sx = 0.0f, sy = 0.0f;
   for (uint32_t k = 0; k < n; ++k) {
     float x, y;
@@ -41,7 +44,7 @@ __device__ __forceinline__ void fit_track(uint32_t n, HitFn hit, const float* z_
   const float tx0 = fdiv(szx, szz), ty0 = fdiv(szy, szz);
   const float t2 = fadd(fmul(tx0, tx0), fmul(ty0, ty0));
   const float sin_t = __fsqrt_rn(fdiv(t2, fadd(1.0f, t2)));
-  const float sig_ms = fmul(kms, sin_t);
+  const float sig_ms = sig_ms_track > 0.0f ? sig_ms_track : fmul(kms, sin_t);
   const float qn = fmul(sig_ms, sig_ms);
   float u[2], tu[2], c00[2], c10[2], c11[2], chi2[2];
   float h0[2], h1[2];

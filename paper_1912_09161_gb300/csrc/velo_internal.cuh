@@ -189,6 +189,9 @@ cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, cons
 
 // Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
+// Refit with a momentum per track (velo_emit.cu).
+cudaError_t launch_refit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const velo_output& tracks,
+                         const float* p_gev, float* states, uint32_t pitch, cudaStream_t st);
 cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
                         const WorkView& wk, const velo_output& out, cudaStream_t st);
 

@@ -31,7 +31,7 @@ EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_required
             "velo_mlp_get_state", "velo_mlp_set_state", "velo_server_create", "velo_server_destroy",
             "velo_server_request_bytes", "velo_server_set_mlp", "velo_server_submit", "velo_server_poll",
             "velo_server_result", "velo_server_release", "velo_server_status", "velo_server_replay",
-            "velo_pv_default_params", "velo_find_pvs", "velo_last_error", "velo_version")
+            "velo_pv_default_params", "velo_find_pvs", "velo_refit_momentum", "velo_last_error", "velo_version")
 PV_NOUT = 10
 PV_NAMES = ("x", "y", "z", "cxx", "cyy", "czz", "cxy", "cxz", "cyz", "weight")
 PV_CAPACITY, PV_SKIPPED = 1, 2
@@ -194,6 +194,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
                  "velo_server_poll", "velo_server_result", "velo_server_release", "velo_server_status",
                  "velo_server_replay"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.velo_refit_momentum.argtypes = [vp, ctypes.c_uint32, P(velo_output), vp, vp, ctypes.c_uint32, vp]
+    lib.velo_refit_momentum.restype = ctypes.c_int
     lib.velo_pv_default_params.argtypes = [P(velo_pv_params)]
     lib.velo_pv_default_params.restype = None
     lib.velo_find_pvs.argtypes = [vp, ctypes.c_uint32, P(velo_output), P(velo_pv_params), P(velo_pv_output), vp]
@@ -575,6 +577,18 @@ def velo_find_pvs(h, n_events: int, tracks: "DeviceOutput", params: PVParams, ou
     tc, pc, oc = tracks.to_c(), params.to_c(), out.to_c()
     _check(load_library(False).velo_find_pvs(h, n_events, ctypes.byref(tc), ctypes.byref(pc), ctypes.byref(oc),
                                              ctypes.c_void_p(stream)), "velo_find_pvs")
+
+
+def velo_refit_momentum(h, n_events: int, tracks: "DeviceOutput", p_gev, stream: int = 0):
+    """States [13, cap_tracks] (torch, on the tracks' device) of the tracks
+    refitted with a momentum per track (``p_gev``: device float32 [>= n_tracks])."""
+    import torch
+    st = torch.zeros((NSTATE, max(tracks.cap_tracks, 1)), dtype=torch.float32, device=tracks.track_off.device)
+    tc = tracks.to_c()
+    _check(load_library(False).velo_refit_momentum(h, n_events, ctypes.byref(tc), _ptr(p_gev), _ptr(st),
+                                                   max(tracks.cap_tracks, 1), ctypes.c_void_p(stream)),
+           "velo_refit_momentum")
+    return st
 
 
 def velo_version() -> str:

@@ -55,6 +55,8 @@ MUTANTS = [
      "float kms = p->ms_coeff * 0.001f * p->pt_nominal;"),
     ("covariance update order", "    s.c10 = s.c10 - k1 * s.c00;\n    s.c00 = s.c00 - k0 * s.c00;",
      "    s.c00 = s.c00 - k0 * s.c00;\n    s.c10 = s.c10 - k1 * s.c00;"),
+    ("per-track momentum ignored", "  if (p_track > 0.0f) sig_ms = (p->ms_coeff * 0.001f) / p_track;\n", ""),
+    ("per-track kick grows with p", "sig_ms = (p->ms_coeff * 0.001f) / p_track;", "sig_ms = (p->ms_coeff * 0.001f) * p_track;"),
     ("prediction covariance", "s.c00 = s.c00 + dz * s.c10 + dz * c10n;\n    s.c10 = c10n;\n    s.c11 = s.c11 + dm[k]",
      "s.c00 = s.c00 + dz * c10n;\n    s.c10 = c10n;\n    s.c11 = s.c11 + dm[k]"),
 ]

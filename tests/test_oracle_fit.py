@@ -170,3 +170,68 @@ def test_pulls_unit_width():
         assert abs(np.mean(pull)) < 0.1
     chi2ndof = np.mean(r.states[ok, 11] / r.ndof[ok])
     assert abs(chi2ndof - 1.0) < 0.05
+
+
+def _refit_inputs(n_events=100):
+    import oracle.metrics as MET
+    geom = velo_synth.geometry()
+    ev = velo_synth.generate(velo_synth.config(0, n_events=n_events))
+    r = oracle.reconstruct(geom, ev, n_threads=4)
+    match = MET.track_match(ev, r)
+    return geom, ev, r, match
+
+
+def test_refit_momentum_limits():
+    """The Velo-only filter with a momentum per track (section 2.3.5): no
+    momentum gives the constant-pT fit bit for bit; an infinite momentum
+    (no scattering) gives the fit without scattering noise bit for bit; the
+    momentum the constant-pT assumption implies, pT / sin(theta) with theta
+    from the least-squares line, gives that fit up to rounding."""
+    geom, ev, r, match = _refit_inputs(20)
+    st0 = oracle.refit_momentum(geom, r, np.zeros(r.n_tracks))
+    assert np.array_equal(st0[:, :12].view(np.uint32), r.states[:, :12].view(np.uint32))
+    assert np.all(st0[:, 12] == 0)
+    stinf = oracle.refit_momentum(geom, r, np.full(r.n_tracks, 1e30))
+    r0 = oracle.reconstruct(geom, ev, oracle.Params(ms_coeff=0.0))
+    assert np.array_equal(r0.track_off, r.track_off)
+    assert np.array_equal(stinf[:, :12].view(np.uint32), r0.states[:, :12].view(np.uint32))
+    # pT / sin(theta) of every track's unweighted least-squares line
+    cl_z = geom.module_z[(r.cl_key >> 16) // geom.sensors_per_module].astype(np.float64)
+    p_eq = np.zeros(r.n_tracks)
+    for t in range(r.n_tracks):
+        e = int(np.searchsorted(r.track_off, t, side="right")) - 1
+        c = r.cluster_off[e] + r.hit_ids[r.hit_off[t]:r.hit_off[t + 1]]
+        z, x, y = cl_z[c], r.cl_x[c].astype(np.float64), r.cl_y[c].astype(np.float64)
+        tx, ty = np.polyfit(z, x, 1)[0], np.polyfit(z, y, 1)[0]
+        p_eq[t] = 0.4 / np.sqrt((tx * tx + ty * ty) / (1 + tx * tx + ty * ty))
+    steq = oracle.refit_momentum(geom, r, p_eq)
+    # the two noise values differ by float rounding (1e-6 relative); x and y
+    # at the beamline sit 100-300 mm from the hits, so their absolute scale
+    assert np.allclose(steq[:, 2:12], r.states[:, 2:12], rtol=1e-4, atol=1e-12)
+    assert np.allclose(steq[:, :2], r.states[:, :2], rtol=0, atol=1e-4)
+
+
+def test_refit_momentum_pulls():
+    """With the generator's momentum (its slope kicks are 1 mrad GeV / p per
+    sensor crossed) the impact-parameter pulls at the true vertex have about
+    unit width in every momentum range; with the constant pT of 400 MeV the
+    errors of low-momentum tracks are far too small."""
+    geom, ev, r, match = _refit_inputs(100)
+    ok = match >= 0
+    p_true = np.where(ok, ev.part_p[np.maximum(match, 0)], 0.0)
+    st = oracle.refit_momentum(geom, r, p_true)
+    v = ev.part_vertex[match[ok]]
+
+    def pulls(s):
+        s = s[ok].astype(np.float64)
+        dz = ev.vtx_z[v] - s[:, 2]
+        x = s[:, 0] + s[:, 3] * dz - ev.vtx_x[v]
+        cxx = s[:, 5] + 2 * dz * s[:, 6] + dz * dz * s[:, 7]
+        return x / np.sqrt(cxx)
+
+    p = p_true[ok]
+    for lo, hi in ((0, 2), (2, 5), (5, 10), (10, 1e9)):
+        sel = (p >= lo) & (p < hi)
+        w = np.std(pulls(st)[sel])
+        assert 0.9 < w < 1.4, (lo, hi, w)
+    assert np.std(pulls(r.states)[p < 2]) > 5.0
