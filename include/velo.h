@@ -240,6 +240,35 @@ int velo_set_params(velo_handle *h, const velo_params *params);
 int velo_reconstruct(velo_handle *h, const velo_events *events, const velo_output *out, void *stream);
 
 /*
+ * Super-pixel raw input (paper section 2.3.1: the VELO clustering works on bit
+ * masks of small regions; the detector packs its hits per 2-column x 4-row
+ * region of a sensor).  One 32-bit word per fired region: bits 0-7 the hit
+ * map (bit dc * 4 + dr is pixel (2 spc + dc, 4 spr + dr)), bits 8-13 spr,
+ * bits 14-20 spc (bits 21-31 ignored).  Words of event e, sensor s occupy
+ * [sensor_off[e*n_sensors + s], sensor_off[e*n_sensors + s + 1]) of sp, in
+ * any order; a pixel set by several words counts once.  Device pointers.
+ */
+typedef struct velo_sp_events {
+  uint32_t n_events;
+  const uint32_t *sensor_off;  /* [n_events * n_sensors + 1] into sp */
+  const uint32_t *sp;
+} velo_sp_events;
+
+/*
+ * velo_reconstruct on super-pixel input: the words are expanded into pixels
+ * on the device with bit operations (population counts, a scan, the set bits
+ * of each hit map) into the handle's decode storage (allocated by the first
+ * call: 8 bytes per event and sensor plus 4 bytes per pixel at the handle's
+ * capacities), then reconstructed as velo_reconstruct does; results are those
+ * of velo_reconstruct on the same pixels.  A batch that expands beyond the
+ * handle's max_pixels marks the events past the limit VELO_EV_BAD_OFFSETS;
+ * a sensor whose word offsets decrease counts as empty and makes
+ * velo_sync_status return VELO_ERR_INPUT.  Enqueued on `stream` (not captured
+ * in the handle's CUDA graphs).  Errors as velo_reconstruct.
+ */
+int velo_reconstruct_sp(velo_handle *h, const velo_sp_events *events, const velo_output *out, void *stream);
+
+/*
  * Waits for the stream and reads the handle's device error word for the last
  * call: VELO_OK, VELO_ERR_INPUT (some event had bad pixels or offsets),
  * VELO_ERR_CAPACITY (some output or event did not fit), VELO_ERR_TIMEOUT.

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
 SOURCES = ["velo_api.cu", "velo_cluster.cu", "velo_track.cu", "velo_track_ring.cu", "velo_emit.cu", "velo_static.cu", "velo_mlp.cu",
-           "velo_serve.cu", "velo_pv.cu"]
+           "velo_serve.cu", "velo_pv.cu", "velo_sp.cu"]
 
 _lock = threading.Lock()
 

@@ -69,6 +69,8 @@ struct velo_handle {
   // global regions of the slow paths: second clustering pass and the
   // global-memory tracking pass
   void* slow_buf = nullptr;
+  // super-pixel decode storage (allocated by the first velo_reconstruct_sp)
+  void* sp_work = nullptr;
   // primary-vertex working storage (allocated by velo_find_pvs when needed)
   void* pv_work = nullptr;
   uint32_t pv_events = 0;
@@ -386,11 +388,11 @@ cudaError_t launch_class(velo_handle* h, const EventsView& ev, const WorkView& w
 // external events, so that the graph records them too; outside a capture
 // that flag is not allowed and they are recorded plainly.
 int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo_output& out, cudaStream_t st,
-            bool capture) {
+            bool capture, bool clear_counters = true) {
   const unsigned mark = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
   const uint32_t E = ev.n_events;
   const bool tm = h->timing;
-  CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
+  if (clear_counters) CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[0], st, mark));
   CUDA_TRY(launch_cluster(h->d_geo, ev, wk, h->cl_threads, h->par.gec_max_pixels, st));
   CUDA_TRY(launch_cluster_big(h->d_geo, ev, wk, h->par.gec_max_pixels, st));
@@ -624,6 +626,7 @@ void velo_destroy(velo_handle* h) {
   if (h->ring_buf) cudaFree(h->ring_buf);
   if (h->slow_buf) cudaFree(h->slow_buf);
   if (h->pv_work) cudaFree(h->pv_work);
+  if (h->sp_work) cudaFree(h->sp_work);
   if (h->h_totals) cudaFreeHost(h->h_totals);
   delete h;
 }
@@ -858,6 +861,43 @@ int velo_find_pvs(velo_handle* h, uint32_t n_events, const velo_output* tracks, 
   }
   CUDA_TRY(launch_pv(h->pv_work, h->pv_events, h->pv_tracks, n_events, *params, *tracks, *out, (cudaStream_t)stream));
   return VELO_OK;
+}
+
+int velo_reconstruct_sp(velo_handle* h, const velo_sp_events* events, const velo_output* out, void* stream) {
+  if (!h || !events || !out) return fail(VELO_ERR_INPUT, "velo_reconstruct_sp: null argument");
+  const uint32_t E = events->n_events;
+  if (E > h->cfg.max_events)
+    return fail(VELO_ERR_NOMEM, "velo_reconstruct_sp: %u events exceed the handle's max_events %u", E,
+                h->cfg.max_events);
+  if (!events->sensor_off || (E && !events->sp)) return fail(VELO_ERR_INPUT, "velo_reconstruct_sp: null event arrays");
+  if (!out->track_off || !out->hit_off || !out->hit_ids || !out->states || !out->ndof || !out->event_status ||
+      !out->totals)
+    return fail(VELO_ERR_INPUT, "velo_reconstruct_sp: null output arrays");
+  const bool want_clusters = out->cluster_off != nullptr;
+  if (want_clusters && (!out->cl_x || !out->cl_y || !out->cl_key))
+    return fail(VELO_ERR_INPUT, "velo_reconstruct_sp: incomplete cluster outputs");
+  if (want_clusters && !(h->cfg.flags & VELO_CFG_CLUSTERS))
+    return fail(VELO_ERR_STATE, "velo_reconstruct_sp: handle created without VELO_CFG_CLUSTERS");
+  if (!h->sp_work) {
+    const size_t bytes = sp_work_bytes(h->cfg.max_events, (uint32_t)h->geo.n_sensors, h->cfg.max_pixels);
+    cudaError_t e = cudaMalloc(&h->sp_work, bytes);
+    if (e != cudaSuccess) {
+      h->sp_work = nullptr;
+      return fail(VELO_ERR_NOMEM, "velo_reconstruct_sp: cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(Counters), st));
+  EventsView ev{};
+  CUDA_TRY(launch_sp_decode(h->sp_work, h->cfg.max_events, (uint32_t)h->geo.n_sensors, h->cfg.max_pixels, E,
+                            events->sensor_off, events->sp, &h->d_cnt->error, &ev, st));
+  WorkView wk = h->wk;
+  if (!want_clusters) {
+    wk.cl_x = nullptr;
+    wk.cl_y = nullptr;
+    wk.cl_key = nullptr;
+  }
+  return enqueue(h, ev, wk, *out, st, false, false);
 }
 
 int velo_sync_status(velo_handle* h, void* stream) {

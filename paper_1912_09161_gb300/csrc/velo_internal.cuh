@@ -189,6 +189,14 @@ cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, cons
 
 // Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);
+// Super-pixel input (velo_sp.cu): working bytes for a batch of up to
+// max_events events / max_pixels pixels, and the decode into the pixel
+// layout (decoded: the event view of the result, in `work`).
+size_t sp_work_bytes(uint32_t max_events, uint32_t n_sensors, uint64_t max_pixels);
+cudaError_t launch_sp_decode(void* work, uint32_t max_events, uint32_t n_sensors, uint64_t max_pixels,
+                             uint32_t n_events, const uint32_t* sp_off, const uint32_t* sp, uint32_t* error,
+                             EventsView* decoded, cudaStream_t st);
+
 // Refit with a momentum per track (velo_emit.cu).
 cudaError_t launch_refit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const velo_output& tracks,
                          const float* p_gev, float* states, uint32_t pitch, cudaStream_t st);

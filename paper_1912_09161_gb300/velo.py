@@ -31,7 +31,8 @@ EXPORTED = ("velo_create", "velo_destroy", "velo_required_bytes", "velo_required
             "velo_mlp_get_state", "velo_mlp_set_state", "velo_server_create", "velo_server_destroy",
             "velo_server_request_bytes", "velo_server_set_mlp", "velo_server_submit", "velo_server_poll",
             "velo_server_result", "velo_server_release", "velo_server_status", "velo_server_replay",
-            "velo_pv_default_params", "velo_find_pvs", "velo_refit_momentum", "velo_last_error", "velo_version")
+            "velo_pv_default_params", "velo_find_pvs", "velo_refit_momentum", "velo_reconstruct_sp",
+            "velo_last_error", "velo_version")
 PV_NOUT = 10
 PV_NAMES = ("x", "y", "z", "cxx", "cyy", "czz", "cxy", "cxz", "cyz", "weight")
 PV_CAPACITY, PV_SKIPPED = 1, 2
@@ -88,6 +89,10 @@ class velo_cluster_output(ctypes.Structure):
 class velo_events(ctypes.Structure):
     _fields_ = [("n_events", ctypes.c_uint32), ("sensor_off", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("row", ctypes.c_void_p)]
+
+
+class velo_sp_events(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_uint32), ("sensor_off", ctypes.c_void_p), ("sp", ctypes.c_void_p)]
 
 
 class velo_output(ctypes.Structure):
@@ -194,6 +199,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
                  "velo_server_poll", "velo_server_result", "velo_server_release", "velo_server_status",
                  "velo_server_replay"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.velo_reconstruct_sp.argtypes = [vp, P(velo_sp_events), P(velo_output), vp]
+    lib.velo_reconstruct_sp.restype = ctypes.c_int
     lib.velo_refit_momentum.argtypes = [vp, ctypes.c_uint32, P(velo_output), vp, vp, ctypes.c_uint32, vp]
     lib.velo_refit_momentum.restype = ctypes.c_int
     lib.velo_pv_default_params.argtypes = [P(velo_pv_params)]
@@ -577,6 +584,14 @@ def velo_find_pvs(h, n_events: int, tracks: "DeviceOutput", params: PVParams, ou
     tc, pc, oc = tracks.to_c(), params.to_c(), out.to_c()
     _check(load_library(False).velo_find_pvs(h, n_events, ctypes.byref(tc), ctypes.byref(pc), ctypes.byref(oc),
                                              ctypes.c_void_p(stream)), "velo_find_pvs")
+
+
+def velo_reconstruct_sp(h, n_events: int, sensor_off, sp, out: "DeviceOutput", stream: int = 0):
+    """Reconstructs a super-pixel batch (device int32 views of the uint32
+    word offsets and words)."""
+    ec, oc = velo_sp_events(n_events, _ptr(sensor_off), _ptr(sp)), out.to_c()
+    _check(load_library(False).velo_reconstruct_sp(h, ctypes.byref(ec), ctypes.byref(oc), ctypes.c_void_p(stream)),
+           "velo_reconstruct_sp")
 
 
 def velo_refit_momentum(h, n_events: int, tracks: "DeviceOutput", p_gev, stream: int = 0):

@@ -158,3 +158,34 @@ def test_global_event_cut():
     # a cut at the largest event keeps everything
     r2 = oracle.reconstruct(geom, ev, oracle.Params(gec_max_pixels=int(ppe.max())))
     assert np.array_equal(r2.track_off, plain.track_off)
+
+
+def test_superpixel_unpack_hand_words():
+    """Hand-packed words: a full region, single bits at its corners, and a
+    region at the far corner of the sensor."""
+    import oracle.sp as SP
+    words = [(1 << 14) | (2 << 8) | 0xFF,             # spc 1, spr 2: cols 2-3, rows 8-11
+             (0 << 14) | (0 << 8) | 0x01,              # pixel (0, 0)
+             (0 << 14) | (0 << 8) | 0x80,              # bit 7: dc 1, dr 3 -> (1, 3)
+             (127 << 14) | (63 << 8) | 0x08]           # bit 3: dc 0, dr 3 -> (254, 255)
+    off, col, row = SP.unpack(np.array([0, 1, 4]), np.array(words), 2)
+    assert list(off) == [0, 8, 11]
+    assert sorted(zip(col[:8].tolist(), row[:8].tolist())) == [(c, r) for c in (2, 3) for r in range(8, 12)]
+    assert list(zip(col[8:].tolist(), row[8:].tolist())) == [(0, 0), (1, 3), (254, 255)]
+
+
+def test_superpixel_round_trip():
+    """Packing (the input generator's) then unpacking (the oracle's) gives
+    every sensor's set of valid pixels back."""
+    import oracle.sp as SP
+    import velo_synth
+    ev = velo_synth.generate(velo_synth.config(0, n_events=5))
+    off, words = velo_synth.to_superpixels(ev)
+    ns = ev.n_sensors
+    uoff, ucol, urow = SP.unpack(off, words, ns)
+    for s in range(5 * ns):
+        a = {(int(c), int(r)) for c, r in zip(ev.col[ev.sensor_off[s]:ev.sensor_off[s + 1]],
+                                              ev.row[ev.sensor_off[s]:ev.sensor_off[s + 1]]) if c < 256 and r < 256}
+        b = set(zip(ucol[uoff[s]:uoff[s + 1]].tolist(), urow[uoff[s]:uoff[s + 1]].tolist()))
+        assert a == b
+        assert len(b) == uoff[s + 1] - uoff[s]     # each pixel once

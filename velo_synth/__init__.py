@@ -318,3 +318,33 @@ def make_events(sensor_lists, n_sensors: int) -> SynthEvents:
         vtx_event=z(np.uint32), vtx_x=z(np.float64), vtx_y=z(np.float64), vtx_z=z(np.float64),
         mc_particle=z(np.int32), mc_module=z(np.uint8), mc_sensor=z(np.uint8),
         mc_x=z(np.float64), mc_y=z(np.float64), mc_z=z(np.float64))
+
+
+def to_superpixels(events) -> tuple[np.ndarray, np.ndarray]:
+    """The batch in the detector's super-pixel packing (input format only):
+    per sensor, one 32-bit word per fired 2-column x 4-row region -- bits 0-7
+    its hit map (bit dc * 4 + dr is pixel (2 spc + dc, 4 spr + dr)), bits 8-13
+    spr = row // 4, bits 14-20 spc = col // 2 -- in order of first appearance
+    in the sensor's pixel list.  Pixels outside 256 x 256 cannot be packed and
+    are dropped; repeated pixels set their bit once.  Returns (sensor_off over
+    the words [n_events * n_sensors + 1], words)."""
+    so = np.asarray(events.sensor_off, np.int64)
+    col = np.asarray(events.col, np.int64)
+    row = np.asarray(events.row, np.int64)
+    n_s = len(so) - 1
+    sensor_of = np.repeat(np.arange(n_s), np.diff(so))
+    ok = (col < 256) & (row < 256)
+    sensor_of, col, row = sensor_of[ok], col[ok], row[ok]
+    addr = ((col >> 1) << 6) | (row >> 2)
+    bit = ((col & 1) << 2) | (row & 3)
+    key = sensor_of * 8192 + addr
+    uniq, first, inv = np.unique(key, return_index=True, return_inverse=True)
+    masks = np.zeros(len(uniq), np.int64)
+    np.bitwise_or.at(masks, inv, np.int64(1) << bit)
+    # words per sensor in order of first appearance
+    order = np.lexsort((first, uniq // 8192))
+    uniq, masks = uniq[order], masks[order]
+    words = (((uniq % 8192) >> 6) << 14) | ((uniq % 64) << 8) | masks
+    counts = np.bincount(uniq // 8192, minlength=n_s)
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint32)
+    return off, words.astype(np.uint32)
