@@ -30,7 +30,7 @@ MUTANTS = [
      "if (w->skip[t] >= p->max_skipped) w->active[t] = 0;"),
     ("forwarded hits not marked used", "if (append[t] >= 0) used[append[t]] = 1;",
      "if (append[t] >= 0) used[append[t]] = 0;"),
-    ("used middle hit allowed", "      if (used[b]) continue;\n      int32_t ba = -1", "      int32_t ba = -1"),
+    ("used middle hit allowed", "      if (used[b]) continue;\n      w->work[2]++;", "      w->work[2]++;"),
     ("used a allowed", "        if (used[a]) continue;", ""),
     ("used c allowed", "          if (used[c]) continue;", ""),
     ("seed extrapolation sign", "float dzc = Z[i] - Z[i + 1];", "float dzc = Z[i + 1] - Z[i];"),
