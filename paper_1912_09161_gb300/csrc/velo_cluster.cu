@@ -56,12 +56,20 @@ struct HitOut {
   uint16_t* key;       // smallest pixel key per hit, or null
 };
 
+// a / cnt in IEEE single precision: for a power-of-two count the quotient is
+// the product with the exact reciprocal (a power of two scales exactly), so
+// the common one- and two-pixel clusters skip the division.
+__device__ __forceinline__ float div_count(float a, uint32_t cnt) {
+  if ((cnt & (cnt - 1u)) == 0u) return fmul(a, __int_as_float((127 - (__ffs(cnt) - 1)) << 23));
+  return fdiv(a, (float)cnt);
+}
+
 // Centroid of the pixel centres, mapped to the global frame (evaluated left
 // to right, no contraction); written at provisional position p.
 __device__ __forceinline__ void store_cluster(const HitOut& out, const SensorGeo& g, uint32_t p, uint32_t key16,
                                               uint32_t cnt, uint32_t sc, uint32_t sr) {
-  const float lx = fmul(fadd(fdiv((float)sc, (float)cnt), 0.5f), g.pitch);
-  const float ly = fmul(fadd(fdiv((float)sr, (float)cnt), 0.5f), g.pitch);
+  const float lx = fmul(fadd(div_count((float)sc, cnt), 0.5f), g.pitch);
+  const float ly = fmul(fadd(div_count((float)sr, cnt), 0.5f), g.pitch);
   const float x = fadd(fadd(g.ox, fmul(g.cdx, lx)), fmul(g.rdx, ly));
   const float y = fadd(fadd(g.oy, fmul(g.cdy, lx)), fmul(g.rdy, ly));
   out.prov[p] = make_float2(x, y);

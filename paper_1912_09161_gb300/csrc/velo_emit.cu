@@ -104,6 +104,9 @@ __global__ void __launch_bounds__(kEmitThreads) emit_event_kernel(uint32_t n_eve
     if (event_fits(r, o0, out)) {
       for (uint32_t k = threadIdx.x; k < r.n_hits; k += blockDim.x)
         out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k] & 0xFFFFu;
+      // the end of the event's last hit list (the next event's first track
+      // may lie past the caller's capacity and write no start of its own)
+      if (threadIdx.x == 0) out.hit_off[o0 + r.n_tracks] = h0 + r.n_hits;
     } else if (r.n_tracks) {
       status |= VELO_EV_TRUNCATED;
     }

@@ -396,6 +396,8 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       const int g = tid / GB, gl = tid % GB;
       const uint32_t nbl = s_misc[R_NB];
       for (uint32_t b0 = 0; b0 < nbl; b0 += NG) {
+        // a warp whose groups all lie past the list has nothing to do
+        if (b0 + (uint32_t)warp * (32u / GB) >= nbl) continue;
         const bool has = b0 + g < nbl;
         const uint32_t qb = has ? blist[b0 + g] : 0u;
         unsigned long long best = ~0ull;
