@@ -164,7 +164,9 @@ int velo_create(const velo_geometry *geometry, const velo_params *params,
 void velo_destroy(velo_handle *h);
 
 /* Bytes of the arena a handle with this configuration holds (the arena of
- * velo_create, without the per-CTA and slow-path regions).  Host only. */
+ * velo_create, without the per-CTA and slow-path regions; the fixed device
+ * memory per stream of section 3.2).  Host only; no device is touched.
+ * Errors: VELO_ERR_INPUT for a null pointer or an invalid geometry. */
 int velo_required_bytes(const velo_geometry *geometry, const velo_config *config, size_t *bytes);
 
 /*
@@ -270,8 +272,10 @@ int velo_reconstruct_sp(velo_handle *h, const velo_sp_events *events, const velo
 
 /*
  * Waits for the stream and reads the handle's device error word for the last
- * call: VELO_OK, VELO_ERR_INPUT (some event had bad pixels or offsets),
- * VELO_ERR_CAPACITY (some output or event did not fit), VELO_ERR_TIMEOUT.
+ * call (the one small device-to-host copy the flow of section 2.2 allows
+ * besides the results): VELO_OK, VELO_ERR_INPUT (some event had bad pixels
+ * or offsets), VELO_ERR_CAPACITY (some output or event did not fit),
+ * VELO_ERR_TIMEOUT (a bounded wait in a kernel gave up).
  */
 int velo_sync_status(velo_handle *h, void *stream);
 
@@ -329,12 +333,16 @@ int velo_get_schedule(const velo_handle *h, velo_schedule *schedule);
 /*
  * Times a fixed list of candidate schedules on this batch (a warm-up and two
  * timed runs each; the outputs are the caller's and are overwritten) and
- * keeps the fastest; returns it and its time in ms.  Synchronous.
+ * keeps the fastest; returns it and its time in ms.  Synchronous.  The paper
+ * fixes one launch shape per kernel (section 2.3); choosing among shapes
+ * that give identical results is this library's addition.
  */
 int velo_autotune(velo_handle *h, const velo_events *events, const velo_output *out, void *stream,
                   velo_schedule *best, float *best_ms);
 
 /*
+ * Launch overhead (section 3.2 runs each batch as a sequence of kernels on
+ * one stream; here the sequence is replayed as one graph).
  * Captures the launch sequence of velo_reconstruct into a CUDA graph per
  * (events, outputs, stream) descriptor and replays it on later calls with
  * the same descriptors (up to four are kept; a change of parameters,
@@ -343,14 +351,17 @@ int velo_autotune(velo_handle *h, const velo_events *events, const velo_output *
  */
 int velo_set_graphs(velo_handle *h, int on);
 
-/* Turns per-kernel timing (CUDA events on the call's stream) on or off. */
+/* Turns per-kernel timing (CUDA events on the call's stream) on or off; the
+ * per-algorithm device times behind the throughput study of section 3.2. */
 int velo_set_timing(velo_handle *h, int on);
 
-/* Waits for the last call and returns its statistics; timing must be on. */
+/* Waits for the last call and returns its statistics; timing must be on
+ * (VELO_ERR_INPUT otherwise). */
 int velo_get_stats(velo_handle *h, velo_stats *out);
 
 /* Writes a JSON description of the handle (per kernel class: threads, CTAs,
- * shared memory, per-event capacities; arena bytes) into buf[0, n). */
+ * shared memory, per-event capacities; arena bytes; slow paths) into
+ * buf[0, n), NUL-terminated and truncated to fit.  Host only. */
 int velo_describe(const velo_handle *h, char *buf, size_t n);
 
 /*
@@ -430,9 +441,11 @@ typedef struct velo_pv_output {
   uint32_t *totals;   /* [2] */
 } velo_pv_output;
 
-/* Default parameters (the frozen readings): z from -300 mm in 2400 bins of
- * 0.25 mm, window 2, min_peak 3, min_sep 4, max_r2 0.25 mm^2, chi2_cut 9,
- * 12 rounds, min_weight 3, merge_dz 1 mm, 64 vertices. */
+/* Default parameters of the PV finder of section 2.3.1 (the paper gives the
+ * method, not the numbers; these are this library's readings): z from
+ * -300 mm in 2400 bins of 0.25 mm, window 2, min_peak 3, min_sep 4,
+ * max_r2 0.25 mm^2, chi2_cut 9, 12 rounds, min_weight 3, merge_dz 1 mm,
+ * 64 vertices.  Host only. */
 void velo_pv_default_params(velo_pv_params *params);
 
 int velo_find_pvs(velo_handle *h, uint32_t n_events, const velo_output *tracks, const velo_pv_params *params,
