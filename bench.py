@@ -281,10 +281,12 @@ def serving(geom, seconds: float, n_slots: int = 8) -> dict:
     capacity = events/s of the continuous-batching server (n_slots slots, pool
     = 4 batches of the maximum size, so that memory decides admission for
     large batches) working through a backlog of such batches; the server then
-    serves Poisson arrivals at 1.2x its capacity for ``seconds`` (an overload:
-    the queue grows, and the latency is mostly queueing) and at 0.8x for a
-    quarter of it; latency is from a batch's arrival to its results in host
-    memory.  The rate of one slot working through the backlog batch after
+    serves Poisson arrivals at 1.2x its capacity for ``seconds`` (the
+    configured load, an overload: the queue grows for as long as the arrivals
+    last, the latency is mostly queueing, and the rate served shows that the
+    server keeps its capacity under a backlog) and at 0.8x for a quarter of
+    it (a load it sustains); latency is from a batch's arrival to its results
+    in host memory.  The rate of one slot working through the backlog batch after
     batch (a server without continuous batching) is kept beside them."""
     import velo_synth
     from paper_1912_09161_gb300 import serve
@@ -655,7 +657,8 @@ def run_ours(args):
             line["uneven"] = uneven_leg(V, geom, dev, stream, flush, max(3, args.steps // 2), 3)
             line["classifier"] = classifier_leg(V, geom, ev, d, dev, stream, flush, max(3, args.steps // 2), 3,
                                                 kept["oracle"])
-    line["p99_latency_ms"] = serve_res["load_1.2x"]["p99_ms"]
+    line["p99_latency_ms"] = serve_res["load_1.2x"]["p99_ms"]          # the configured overload
+    line["p99_latency_ms_at_0.8x"] = serve_res["load_0.8x"]["p99_ms"]   # a load the server sustains
     print(json.dumps(line), flush=True)
     return 0
 
@@ -732,7 +735,8 @@ def main():
     ap.add_argument("--workload", choices=tuple(WORKLOADS), default="nominal",
                     help="nominal: the 10,000-event throughput batch; uneven: 50,000 events of mixed pileup")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
-                    help="duration of the Poisson arrival stream at 1.2x the server's capacity")
+                    help="duration of the Poisson arrival stream at 1.2x the server's capacity "
+                         "(the 0.8x load runs for a quarter of it)")
     ap.add_argument("--scaling", choices=("strong", "weak"), default="strong",
                     help="strong: one batch split over the GPUs by pixel count; weak: a batch per GPU")
     ap.add_argument("--no-legs", action="store_true",

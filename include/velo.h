@@ -309,17 +309,20 @@ typedef struct velo_stats {
  * to one block; the schedule only decides how blocks share the GPU).  Events
  * run in the first class that holds their hits.  class_mask selects the
  * classes:
+ *   bit 7: the narrow module-window class (64 threads, thirteen CTAs per SM,
+ *          up to 8192 hits and modules of up to 160 hits; events that
+ *          outgrow it go to a pass of the wide class when bit 6 is set);
  *   bit 6: the module-window class (128 threads, nine CTAs per SM, up to
- *          8192 hits; it keeps only the three modules of a round and the
- *          next one in shared memory);
+ *          8192 hits and modules of up to 256 hits; it keeps only the three
+ *          modules of a round and the next one in shared memory);
  *   bits 0-5: whole-event classes by CTAs per SM: bit 0 = 8, 1 = 6, 2 = 4,
  *          3 = 3, 4 = 2, 5 = 1 (always present), track_threads each; a class
  *          that holds no more hits than the classes before it is skipped.
  * At most four classes.  Events that outgrow their class go to a retry pass
  * of the last (one-CTA-per-SM) class.  concurrent = 1 runs the classes on
  * their own streams at once, 0 one after another.  Results are identical
- * under every schedule.  Default: {256, 0x60, 1} (module-window class, then
- * one CTA per SM).
+ * under every schedule.  Default: {256, 0xE0, 1} (narrow module window, wide
+ * module window, then one CTA per SM, concurrent).
  */
 typedef struct velo_schedule {
   uint32_t track_threads;  /* 128 or 256 threads per tracking CTA */

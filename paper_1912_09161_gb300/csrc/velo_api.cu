@@ -56,16 +56,17 @@ struct velo_handle {
   // clustering kernel
   int cl_threads = 256;
   // tracking-kernel classes (increasing shared-memory plans), each on its stream
-  velo_schedule sched{256, 0x60u, 1};  // module-window class, then 1 CTA per SM (bits over kPerSm), concurrent
+  velo_schedule sched{256, 0xE0u, 1};  // narrow and wide module windows, then 1 CTA per SM (bits over kPerSm), concurrent
   int n_classes = 0;
   Caps caps[kMaxClasses]{};
   int per_sm[kMaxClasses]{};
   int threads = 256;
   int ctas[kMaxClasses]{};
-  bool ring_cls[kMaxClasses]{};  // class k runs the module-window kernel
-  // module-window kernel: CTAs per SM and its per-CTA global regions
-  int ring_per_sm = 0;
-  void* ring_buf = nullptr;
+  int ring_cls[kMaxClasses]{};   // shape of the module-window kernel class k runs, or -1 (whole-event kernel)
+  int wide_cls = -1;             // class of the wide module window (the narrow shape's overflow pass), or -1
+  // module-window kernel, per shape: CTAs per SM and the per-CTA global regions
+  int ring_per_sm[2] = {0, 0};
+  void* ring_buf[2] = {nullptr, nullptr};
   // global regions of the slow paths: second clustering pass and the
   // global-memory tracking pass
   void* slow_buf = nullptr;
@@ -185,7 +186,7 @@ FixedPlan plan_fixed() {
 }
 
 struct WorkPlan {
-  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, tev, hits, clx, cly, clk, total;
+  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, tev, hits, hpos, clx, cly, clk, total;
 };
 
 WorkPlan plan_work(const velo_config& c) {
@@ -201,6 +202,7 @@ WorkPlan plan_work(const velo_config& c) {
   a.ho = o; o = align256(o + 4ull * c.max_tracks);
   a.tev = o; o = align256(o + 4ull * c.max_tracks);
   a.hits = o; o = align256(o + 4ull * c.max_track_hits);
+  a.hpos = o; o = align256(o + 8ull * c.max_track_hits);
   if (c.flags & VELO_CFG_CLUSTERS) {
     a.clx = o; o = align256(o + 4ull * c.max_pixels);
     a.cly = o; o = align256(o + 4ull * c.max_pixels);
@@ -225,6 +227,7 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
   w.tr_hitoff = (uint32_t*)(base + a.ho);
   w.tr_event = (uint32_t*)(base + a.tev);
   w.tr_hits = (uint32_t*)(base + a.hits);
+  w.tr_pos = (float2*)(base + a.hpos);
   w.cap_tracks = (uint32_t)c.max_tracks;
   w.cap_hits = (uint32_t)c.max_track_hits;
   w.cl_x = (c.flags & VELO_CFG_CLUSTERS) ? (float*)(base + a.clx) : nullptr;
@@ -242,8 +245,10 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
 // CTAs per SM of the candidate classes; a schedule's class_mask selects
 // from this list (at most kMaxClasses; one CTA per SM is always included).
 constexpr int kPerSm[6] = {8, 6, 4, 3, 2, 1};
-// class_mask bit of the module-window class (128 threads, kRingCtasPerSm CTAs per SM).
+// class_mask bits of the module-window classes: bit 6 the wide shape (128
+// threads, nine CTAs per SM), bit 7 the narrow one (64 threads, thirteen).
 constexpr uint32_t kRingClassBit = 1u << 6;
+constexpr uint32_t kRingNarrowBit = 1u << 7;
 
 // Hit-slot bytes of a class plan: kMaxModules u16 per candidate, max_tracks
 // candidates per CTA.
@@ -269,30 +274,37 @@ size_t trk_bytes_bound(const velo_handle* h) {
   return best;
 }
 
-// The module-window kernel's CTAs per SM and the global regions of all its
-// CTAs (array by array, each 256-byte aligned).  Without room for one CTA
-// per SM the class is left out of every schedule.
-int setup_ring(velo_handle* h) {
-  cudaError_t e = ring_set_smem_limit();
+// A module-window shape's CTAs per SM and the global regions of all its CTAs
+// (array by array, each 256-byte aligned; room for one hit per module per
+// candidate).  Without room for one CTA per SM the shape is left out of every
+// schedule.
+int setup_ring(velo_handle* h, int shape) {
+  const RingShape& sh = kRingShapes[shape];
+  cudaError_t e = ring_set_smem_limit(shape);
   if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(ring): %s", cudaGetErrorString(e));
   int occ = 0;
-  e = ring_occupancy(&occ);
+  e = ring_occupancy(shape, &occ);
   if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "occupancy query (ring): %s", cudaGetErrorString(e));
   if (occ < 1) return VELO_OK;
-  h->ring_per_sm = occ > kRingCtasPerSm ? kRingCtasPerSm : occ;
-  const size_t n = (size_t)h->ring_per_sm * h->n_sm;
+  h->ring_per_sm[shape] = occ > sh.ctas_per_sm ? sh.ctas_per_sm : occ;
+  const size_t n = (size_t)h->ring_per_sm[shape] * h->n_sm;
+  const size_t stride = kRingTrackHits;
+  const size_t mt = sh.max_t;
   size_t o = 0;
-  const size_t o_trk = o; o = align256(o + n * kRingMaxT * kRingTrackHits * sizeof(uint32_t));
-  const size_t o_sh = o; o = align256(o + n * 3 * kRingMaxT * sizeof(uint16_t));
-  const size_t o_n = o; o = align256(o + n * kRingMaxT);
-  const size_t o_seed = o; o = align256(o + n * kRingMaxT * sizeof(float));
-  e = cudaMalloc(&h->ring_buf, o);
+  const size_t o_trk = o; o = align256(o + n * mt * stride * sizeof(uint32_t));
+  const size_t o_pos = o; o = align256(o + n * mt * stride * sizeof(float2));
+  const size_t o_sh = o; o = align256(o + n * 3 * mt * sizeof(uint16_t));
+  const size_t o_n = o; o = align256(o + n * mt);
+  const size_t o_seed = o; o = align256(o + n * mt * sizeof(float));
+  e = cudaMalloc(&h->ring_buf[shape], o);
   if (e != cudaSuccess) {
-    h->ring_buf = nullptr;
+    h->ring_buf[shape] = nullptr;
+    h->ring_per_sm[shape] = 0;
     return fail(VELO_ERR_NOMEM, "cudaMalloc(%zu) (ring): %s", o, cudaGetErrorString(e));
   }
-  char* b = (char*)h->ring_buf;
-  h->wk.ring = RingScratch{(uint32_t*)(b + o_trk), (uint16_t*)(b + o_sh), (uint8_t*)(b + o_n), (float*)(b + o_seed)};
+  char* b = (char*)h->ring_buf[shape];
+  h->wk.ring[shape] = RingScratch{(uint32_t*)(b + o_trk), (float2*)(b + o_pos), (uint16_t*)(b + o_sh),
+                                  (uint8_t*)(b + o_n), (float*)(b + o_seed)};
   return VELO_OK;
 }
 
@@ -319,16 +331,22 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
   const int threads = (int)sc.track_threads;
   Caps caps[kMaxClasses]{};
   int per_sm[kMaxClasses]{}, n = 0;
-  bool ring[kMaxClasses]{};
+  int ring[kMaxClasses] = {-1, -1, -1, -1};
+  uint32_t maxmod[kMaxClasses]{};
   uint32_t prev_maxh = 0;
   const uint32_t mask = sc.class_mask | (1u << 5);
-  if ((mask & kRingClassBit) && h->ring_per_sm > 0) {
-    // module-window class first: every event of up to kRingMaxH hits
-    caps[0] = Caps{kRingMaxH, kRingMaxT, ring_smem_bytes()};
-    per_sm[0] = h->ring_per_sm;
-    ring[0] = true;
-    n = 1;
-    prev_maxh = kRingMaxH;
+  // module-window classes first, narrow then wide: every event of up to
+  // kRingMaxH hits whose busiest module fits the shape
+  for (int shape : {kRingNarrow, kRingWide}) {
+    const uint32_t bit = shape == kRingNarrow ? kRingNarrowBit : kRingClassBit;
+    if (!(mask & bit) || h->ring_per_sm[shape] <= 0) continue;
+    const RingShape& sh = kRingShapes[shape];
+    caps[n] = Caps{sh.max_h, sh.max_t, ring_smem_bytes(shape)};
+    per_sm[n] = h->ring_per_sm[shape];
+    ring[n] = shape;
+    maxmod[n] = sh.mod_hits;
+    ++n;
+    prev_maxh = sh.max_h;
   }
   for (int i = 0; i < 6; ++i) {
     if (!((mask >> i) & 1u)) continue;
@@ -344,14 +362,15 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     if (n == kMaxClasses) return fail(VELO_ERR_INPUT, "schedule: at most %d classes", kMaxClasses);
     caps[n] = c;
     per_sm[n] = occ < kPerSm[i] ? occ : kPerSm[i];
+    maxmod[n] = 0xFFFFFFFFu;
     ++n;
     prev_maxh = c.maxh;
   }
   if (n == 0) return fail(VELO_ERR_INPUT, "schedule: no class");
-  if (ring[n - 1]) return fail(VELO_ERR_INPUT, "schedule: no whole-event class for the retry pass");
+  if (ring[n - 1] >= 0) return fail(VELO_ERR_INPUT, "schedule: no whole-event class for the retry pass");
   size_t need = 0;
   for (int k = 0; k < n; ++k)
-    if (!ring[k]) need += class_trk_bytes(caps[k], per_sm[k] * h->n_sm);
+    if (ring[k] < 0) need += class_trk_bytes(caps[k], per_sm[k] * h->n_sm);
   if (need > h->trk_bytes) return fail(VELO_ERR_NOMEM, "schedule: hit slots need %zu bytes, have %zu", need, h->trk_bytes);
   cudaError_t e = track_set_smem_limit(threads, (int)caps[n - 1].smem);
   if (e != cudaSuccess) return fail(VELO_ERR_CUDA, "cudaFuncSetAttribute(track): %s", cudaGetErrorString(e));
@@ -363,13 +382,21 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
     h->per_sm[k] = k < n ? per_sm[k] : 0;
     h->ctas[k] = k < n ? per_sm[k] * h->n_sm : 0;
     h->wk.class_maxh[k] = k < n ? caps[k].maxh : 0;
-    h->ring_cls[k] = k < n && ring[k];
+    h->wk.class_maxmod[k] = k < n ? maxmod[k] : 0;
+    h->ring_cls[k] = k < n ? ring[k] : -1;
   }
   h->wk.n_classes = n;
+  h->wide_cls = -1;
+  bool narrow = false;
+  for (int k = 0; k < n; ++k) {
+    if (ring[k] == kRingWide) h->wide_cls = k;
+    if (ring[k] == kRingNarrow) narrow = true;
+  }
+  h->wk.ring_retry = narrow && h->wide_cls >= 0 ? 1 : 0;
   size_t off = 0;
   for (int k = 0; k < kMaxClasses; ++k) {
-    h->wk.trk_hits[k] = k < n && !ring[k] ? h->trk + off : nullptr;
-    if (k < n && !ring[k]) off += (size_t)h->ctas[k] * caps[k].maxt * kMaxModules;
+    h->wk.trk_hits[k] = k < n && ring[k] < 0 ? h->trk + off : nullptr;
+    if (k < n && ring[k] < 0) off += (size_t)h->ctas[k] * caps[k].maxt * kMaxModules;
   }
   h->version++;
   return VELO_OK;
@@ -377,7 +404,7 @@ int build_classes(velo_handle* h, const velo_schedule& sc) {
 
 // Tracking kernel of class k on its own queue.
 cudaError_t launch_class(velo_handle* h, const EventsView& ev, const WorkView& wk, int k, cudaStream_t st) {
-  if (h->ring_cls[k]) return launch_track_ring(h->d_geo, h->par, ev, wk, k, k, h->ctas[k], st);
+  if (h->ring_cls[k] >= 0) return launch_track_ring(h->ring_cls[k], h->d_geo, h->par, ev, wk, k, k, h->ctas[k], st);
   return launch_track(h->d_geo, h->par, ev, wk, h->caps[k], k, k, h->threads, h->ctas[k], st);
 }
 
@@ -410,6 +437,10 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
       for (int k = h->n_classes - 1; k >= 0; --k)
         CUDA_TRY(launch_class(h, ev, wk, k, st));
     }
+    // events that outgrew the narrow module window: the wide one
+    if (h->wk.ring_retry)
+      CUDA_TRY(launch_track_ring(kRingWide, h->d_geo, h->par, ev, wk, h->wide_cls, kRingRetryQueue,
+                                 h->ctas[h->wide_cls], st));
     // events that ran out of track storage in their class: largest plan
     const int big = h->n_classes - 1;
     CUDA_TRY(launch_track(h->d_geo, h->par, ev, wk, h->caps[big], big, kRetryQueue, h->threads, h->ctas[big], st));
@@ -580,7 +611,9 @@ int velo_create(const velo_geometry* geometry, const velo_params* params, const 
     h->wk.cnt = h->d_cnt;
     h->d_mlp = base + fx.mlp;
     carve_work(h, base + fx.total, h->cfg);
-    rc = setup_ring(h);
+    rc = setup_ring(h, kRingWide);
+    if (rc) break;
+    rc = setup_ring(h, kRingNarrow);
     if (rc) break;
     rc = setup_slow(h);
     if (rc) break;
@@ -623,7 +656,8 @@ void velo_destroy(velo_handle* h) {
   if (h->arena) cudaFree(h->arena);
   if (h->stage) cudaFree(h->stage);
   if (h->trk) cudaFree(h->trk);
-  if (h->ring_buf) cudaFree(h->ring_buf);
+  for (void* b : h->ring_buf)
+    if (b) cudaFree(b);
   if (h->slow_buf) cudaFree(h->slow_buf);
   if (h->pv_work) cudaFree(h->pv_work);
   if (h->sp_work) cudaFree(h->sp_work);
@@ -641,9 +675,11 @@ int velo_describe(const velo_handle* h, char* buf, size_t n) {
   for (int k = 0; k < h->n_classes && w > 0 && (size_t)w < n; ++k)
     w += snprintf(buf + w, n - w,
                   "%s{\"kernel\": \"%s\", \"threads\": %d, \"ctas_per_sm\": %d, \"ctas\": %d, \"smem\": %u, "
-                  "\"max_hits\": %u, \"max_tracks\": %u}",
-                  k ? ", " : "", h->ring_cls[k] ? "window" : "event", h->ring_cls[k] ? kRingThreads : h->threads,
-                  h->per_sm[k], h->ctas[k], h->caps[k].smem, h->caps[k].maxh, h->caps[k].maxt);
+                  "\"max_hits\": %u, \"max_tracks\": %u, \"max_module_hits\": %u}",
+                  k ? ", " : "",
+                  h->ring_cls[k] == kRingNarrow ? "window_narrow" : h->ring_cls[k] == kRingWide ? "window" : "event",
+                  h->ring_cls[k] >= 0 ? kRingShapes[h->ring_cls[k]].threads : h->threads, h->per_sm[k], h->ctas[k],
+                  h->caps[k].smem, h->caps[k].maxh, h->caps[k].maxt, h->wk.class_maxmod[k]);
   if (w > 0 && (size_t)w < n)
     w += snprintf(buf + w, n - w,
                   "], \"slow_paths\": {\"cluster_ctas\": %d, \"cluster_region_bytes\": %zu, \"track_ctas\": %d, "
@@ -699,14 +735,16 @@ int velo_get_schedule(const velo_handle* h, velo_schedule* sc) {
 int velo_autotune(velo_handle* h, const velo_events* events, const velo_output* out, void* stream,
                   velo_schedule* best_out, float* best_ms) {
   if (!h || !events || !out) return fail(VELO_ERR_INPUT, "velo_autotune: null argument");
-  // threads per whole-event CTA, classes (bit 6: module window; bits over 8,
-  // 6, 4, 3, 2, 1 CTAs per SM), concurrency
-  //   window + 1, concurrent and in sequence; window + {2,1}
+  // threads per whole-event CTA, classes (bit 7: narrow module window, bit 6:
+  // wide module window; bits over 8, 6, 4, 3, 2, 1 CTAs per SM), concurrency
+  //   narrow + wide + 1, concurrent and in sequence; narrow + 1
+  //   wide + 1, concurrent and in sequence; wide + {2,1}
   //   256 threads: {4,3,2,1} concurrent and in sequence, {4,2,1}, {3,2,1}, {2,1}
   //   128 threads: {8,4,2,1}, {6,4,2,1}
   static const velo_schedule cand[] = {
-      {256, 0x60u, 1}, {256, 0x60u, 0}, {256, 0x70u, 1}, {256, 0x1Cu, 1}, {256, 0x1Cu, 0}, {256, 0x14u, 1},
-      {256, 0x18u, 1}, {256, 0x10u, 1}, {128, 0x15u, 1}, {128, 0x16u, 1},
+      {256, 0xE0u, 1}, {256, 0xE0u, 0}, {256, 0xA0u, 1}, {256, 0x60u, 1}, {256, 0x60u, 0}, {256, 0x70u, 1},
+      {256, 0x1Cu, 1}, {256, 0x1Cu, 0}, {256, 0x14u, 1}, {256, 0x18u, 1}, {256, 0x10u, 1}, {128, 0x15u, 1},
+      {128, 0x16u, 1},
   };
   cudaStream_t st = (cudaStream_t)stream;
   const bool graphs = h->use_graphs, timing = h->timing;

@@ -691,7 +691,7 @@ struct ClusterSmem {
 template <int NT, bool BIG>
 __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsView& ev, const WorkView& wk,
                               uint32_t e, const ClusterSmem& S, uint32_t& H_out, uint32_t& status_out,
-                              unsigned char* gscr, uint32_t gec_max_pixels) {
+                              uint32_t& maxmod_out, unsigned char* gscr, uint32_t gec_max_pixels) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = geo->n_sensors, ncols = geo->n_cols, nrows = geo->n_rows;
   unsigned char* slice = S.warps + (warp == 0 ? 0u : kBigSlice + (uint32_t)(warp - 1) * kSmallSlice);
@@ -729,6 +729,15 @@ __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsV
   const uint16_t* row = ev.row + gbase;
   const HitOut out{wk.prov + gbase, wk.prov_key ? wk.prov_key + gbase : nullptr};
   bool bad = false;
+  // the event's raw pixels into L2 while the sensors are classified: one
+  // prefetch per 128-byte line, each at an address the sensors' loads read
+  {
+    const uint32_t bytes = 2u * (so[ns] - gbase), lines = (bytes + 127u) / 128u;
+    for (uint32_t k = tid; k < 2u * lines; k += NT) {
+      const char* base = (const char*)(k < lines ? col : row);
+      asm volatile("prefetch.global.L2 [%0];\n" ::"l"(base + (k % lines) * 128u));
+    }
+  }
   // sensors by size class
   for (int s = tid; s < ns; s += NT) {
     const uint32_t n = s_soff[s + 1] - s_soff[s];
@@ -823,6 +832,13 @@ __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsV
   }
   uint16_t* cb = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
   for (int s = tid; s <= ns; s += NT) cb[s] = (uint16_t)s_cnt[s];
+  // hits of the busiest module (warp 0; the tracking classes' windows hold
+  // modules of bounded size)
+  if (warp == 0) {
+    uint32_t mx = 0;
+    for (int m = lane; m < geo->n_modules; m += 32) mx = max(mx, s_cnt[kSPM * (m + 1)] - s_cnt[kSPM * m]);
+    maxmod_out = __reduce_max_sync(kFull, mx);
+  }
   H_out = H;
   status_out = st;
   return true;
@@ -852,10 +868,12 @@ __host__ __device__ inline ClusterLayout cluster_layout(int n_threads) {
 uint32_t cluster_smem_bytes(int n_threads) { return cluster_layout(n_threads).total; }
 
 // Queues a clustered event for the first tracking class that holds its H
-// hits; beyond every class, for the global-memory pass if there is one.
-__device__ inline void queue_event(const WorkView& wk, uint32_t e, uint32_t gbase, uint32_t H, uint32_t st) {
+// hits and its busiest module's maxmod hits; beyond every class, for the
+// global-memory pass if there is one.
+__device__ inline void queue_event(const WorkView& wk, uint32_t e, uint32_t gbase, uint32_t H, uint32_t maxmod,
+                                   uint32_t st) {
   int cls = 0;
-  while (cls < wk.n_classes && H > wk.class_maxh[cls]) ++cls;
+  while (cls < wk.n_classes && (H > wk.class_maxh[cls] || maxmod > wk.class_maxmod[cls])) ++cls;
   int q = cls;
   if (cls >= wk.n_classes) q = (wk.huge_scratch && H <= kHugeMaxH) ? kHugeQueue : -1;
   if (q < 0) {
@@ -876,9 +894,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) cluster_kernel(const DevGeometr
   const ClusterSmem S{(uint32_t*)(smem + L.soff), (uint32_t*)(smem + L.ccnt), (uint32_t*)(smem + L.misc),
                       (uint32_t*)(smem + L.scan), (uint8_t*)(smem + L.lists), smem + L.warps};
   for (uint32_t e = blockIdx.x; e < ev.n_events; e += gridDim.x) {
-    uint32_t H = 0, st = 0;
-    if (!cluster_event<NT, false>(geo, ev, wk, e, S, H, st, nullptr, gec)) continue;
-    if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, st);
+    uint32_t H = 0, st = 0, mx = 0;
+    if (!cluster_event<NT, false>(geo, ev, wk, e, S, H, st, mx, nullptr, gec)) continue;
+    if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, mx, st);
   }
 }
 
@@ -901,9 +919,9 @@ __global__ void __launch_bounds__(NT, 1) cluster_big_kernel(const DevGeometry* _
     const uint32_t q = s_ticket;
     if (q >= *(volatile uint32_t*)&wk.cnt->queue_len[kBigSensorQueue]) break;
     const uint32_t e = wk.queue[kBigSensorQueue][q];
-    uint32_t H = 0, st = 0;
-    if (!cluster_event<NT, true>(geo, ev, wk, e, S, H, st, gscr, gec)) continue;
-    if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, st);
+    uint32_t H = 0, st = 0, mx = 0;
+    if (!cluster_event<NT, true>(geo, ev, wk, e, S, H, st, mx, gscr, gec)) continue;
+    if (threadIdx.x == 0) queue_event(wk, e, ev.sensor_off[(size_t)e * geo->n_sensors], H, mx, st);
   }
 }
 

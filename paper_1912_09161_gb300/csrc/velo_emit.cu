@@ -84,11 +84,12 @@ cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output
 // ---------------------------------------------------------------------------
 // emit: two kernels.
 //   emit_event_kernel -- one block per event (grid-stride): event status,
-//     hit ids and (on request) the cluster list;
+//     the end of its last hit list and (on request) the cluster list;
 //   emit_fit_kernel   -- one thread per kept track over the whole batch
 //     (grid-stride over the scratch tracks, whose events are recorded by the
-//     tracking kernels): gathers the track's hits from the clustering output
-//     at every pass of the fit (no per-thread hit arrays) and writes its state.
+//     tracking kernels): reads the track's hit positions, which the tracking
+//     kernels wrote contiguously, at every pass of the fit (no per-thread hit
+//     arrays) and writes its state, hit offset and hit ids.
 // ---------------------------------------------------------------------------
 constexpr int kEmitThreads = 128;
 
@@ -102,8 +103,6 @@ __global__ void __launch_bounds__(kEmitThreads) emit_event_kernel(uint32_t n_eve
     const uint32_t o0 = out.track_off[e], h0 = r.out_hit_base;
     uint32_t status = r.status;
     if (event_fits(r, o0, out)) {
-      for (uint32_t k = threadIdx.x; k < r.n_hits; k += blockDim.x)
-        out.hit_ids[h0 + k] = wk.tr_hits[r.hit_base + k] & 0xFFFFu;
       // the end of the event's last hit list (the next event's first track
       // may lie past the caller's capacity and write no start of its own)
       if (threadIdx.x == 0) out.hit_off[o0 + r.n_tracks] = h0 + r.n_hits;
@@ -130,7 +129,6 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
                                                                 DevParams par, EventsView ev, WorkView wk,
                                                                 velo_output out) {
   __shared__ float s_z[kMaxModules];
-  const int ns = geo->n_sensors;
   for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
   __syncthreads();
   const bool use_mlp = par.use_mlp && wk.mlp_w != nullptr;
@@ -149,20 +147,15 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
     const uint32_t nh = __ldg(&wk.tr_nhits[t]);
     const uint32_t hoff = __ldg(&wk.tr_hitoff[t]);
     const uint32_t* th = wk.tr_hits + r.hit_base + hoff;
-    const uint16_t* cb = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
-    const uint32_t* so = ev.sensor_off + (size_t)e * ns;
+    const float2* tp = wk.tr_pos + r.hit_base + hoff;
     float st[12];
     fit_track(
         nh,
         [&](uint32_t j, float& x, float& y, int& m) {
-          // hit j from the clustering output, by module and canonical id
-          const uint32_t h = __ldg(&th[j]);
-          const uint32_t id = h & 0xFFFFu, mm = h >> 16, s0 = kSPM * mm;
-          const uint32_t s = s0 + (id >= __ldg(&cb[s0 + 1])) + (id >= __ldg(&cb[s0 + 2])) + (id >= __ldg(&cb[s0 + 3]));
-          const float2 v = __ldg(&wk.prov[__ldg(&so[s]) + (id - __ldg(&cb[s]))]);
+          const float2 v = __ldg(&tp[j]);
           x = v.x;
           y = v.y;
-          m = (int)mm;
+          m = (int)(__ldg(&th[j]) >> 16);
         },
         s_z, sig2, kms, st);
 #pragma unroll
@@ -170,6 +163,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
     out.states[12 * ocap + o0 + k] = use_mlp ? 1.0f / (1.0f + expf(-__ldg(&wk.tr_logit[t]))) : 0.0f;
     out.ndof[o0 + k] = (uint8_t)(2 * nh - 4);
     out.hit_off[o0 + k] = r.out_hit_base + hoff;
+    for (uint32_t j = 0; j < nh; ++j) out.hit_ids[r.out_hit_base + hoff + j] = __ldg(&th[j]) & 0xFFFFu;
   }
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "velo.h"
@@ -17,21 +18,31 @@ constexpr int kMaxClasses = 4;                   // shared-memory classes of the
 constexpr int kRetryQueue = kMaxClasses;         // events that ran out of storage in their class
 constexpr int kHugeQueue = kMaxClasses + 1;      // events beyond every shared-memory class (global-memory pass)
 constexpr int kBigSensorQueue = kMaxClasses + 2; // events with a sensor beyond the warp paths (second clustering pass)
-constexpr int kQueues = kMaxClasses + 3;
+constexpr int kRingRetryQueue = kMaxClasses + 3; // events that outgrew the narrow window class (wide window, after)
+constexpr int kQueues = kMaxClasses + 4;
 constexpr int kMlpIn = 10, kMlpH = 32;
 constexpr int kMlpParams = kMlpIn * kMlpH + kMlpH + kMlpH * kMlpH + kMlpH + kMlpH + 1;  // 1441
 constexpr int kMlpNormOffset = (2 * kMlpParams + 15) & ~15;  // byte offset of the float normalisation
 
-// Module-window tracking kernel (velo_track_ring.cu): CTA size and the
-// capacities of its shared-memory window and global region; an event beyond
-// any of them goes to the retry queue.
-constexpr int kRingThreads = 128;
-constexpr int kRingCtasPerSm = 9;         // register budget: 65536 / (128 * 9) -> 56 per thread
-constexpr uint32_t kRingModHits = 256;    // hits of one module
-constexpr uint32_t kRingMaxH = 8192;      // hits of one event
-constexpr uint32_t kRingMaxAct = 160;     // active tracks in one round
-constexpr uint32_t kRingMaxT = 512;       // track candidates of one event
-constexpr uint32_t kRingTrackHits = 32;   // hits of one candidate
+// Module-window tracking kernel (velo_track_ring.cu), in two shapes: CTA
+// size, CTAs per SM and the capacities of the shared-memory window and the
+// global region; an event beyond any of them goes on to a larger plan.
+//   wide   (variant 0): 128 threads, nine CTAs per SM (register budget:
+//           65536 / (128 * 9) -> 56 per thread);
+//   narrow (variant 1): 64 threads and a smaller window (modules of up to 160
+//           hits, 136 active tracks, 384 candidates), thirteen CTAs per SM
+//           (shared memory: 13 x 17.9 KB of the SM's 228 KB).
+// A round of the search offers about 30 active tracks and 30 middle hits
+// (nominal events), which two warps cover; the narrow shape trades the idle
+// warps of the wide one for more events in flight.
+struct RingShape {
+  int threads, ctas_per_sm;
+  uint32_t mod_hits, max_h, max_act, max_t;
+};
+constexpr RingShape kRingShapes[2] = {{128, 9, 256, 8192, 160, 512}, {64, 13, 160, 8192, 136, 384}};
+constexpr int kRingWide = 0, kRingNarrow = 1;
+constexpr uint32_t kRingMaxH = 8192;      // hits of one event, both shapes
+constexpr uint32_t kRingTrackHits = kMaxModules;  // hits of one candidate: one per module at most
 
 // Device copy of the geometry (in the handle's arena).
 struct DevGeometry {
@@ -92,8 +103,8 @@ enum : uint32_t {
 struct Counters {
   uint32_t ticket[kQueues];         // persistent-kernel tickets per queue
   uint32_t queue_len[kQueues];      // events queued per class, and for retry
-  uint32_t track_cursor;            // scratch bump allocators
-  uint32_t hit_cursor;
+  uint32_t track_cursor;            // scratch bump allocators (adjacent, 8-byte aligned:
+  uint32_t hit_cursor;              // the module-window kernel bumps both in one 64-bit atomic)
   uint32_t error;                   // kErr* bits
   uint32_t pad0;
   uint32_t cls_events[kMaxClasses];  // events completed per class
@@ -102,14 +113,18 @@ struct Counters {
   uint32_t cls_clusters[kMaxClasses];  // hits (clusters) read per class
   unsigned long long cls_pixels[kMaxClasses];  // raw pixels of the completed events
 };
+static_assert(offsetof(Counters, track_cursor) % 8 == 0 && offsetof(Counters, hit_cursor) == offsetof(Counters, track_cursor) + 4,
+              "the scratch cursors form one aligned 64-bit word");
 
-// Global region of the module-window kernel, one per CTA (arrays of n_ctas
-// regions): each candidate's hit list and its seed (canonical ids).
+// Global region of a module-window kernel, one per CTA (arrays of n_ctas
+// regions): each candidate's hit list (ids and positions) and its seed
+// (canonical ids).
 struct RingScratch {
-  uint32_t* trk;      // [kRingMaxT * kRingTrackHits] hits per candidate: module << 16 | canonical id
-  uint16_t* seed_hit; // [3 * kRingMaxT] seed hits a, b, c
-  uint8_t* n_hits;    // [kRingMaxT]
-  float* seed;        // [kRingMaxT] seed scatter, then the classifier logit
+  uint32_t* trk;      // [max_t * kRingTrackHits] hits per candidate: module << 16 | canonical id
+  float2* trk_pos;    // [max_t * kRingTrackHits] their positions (x, y)
+  uint16_t* seed_hit; // [3 * max_t] seed hits a, b, c
+  uint8_t* n_hits;    // [max_t]
+  float* seed;        // [max_t] seed scatter, then the classifier logit
 };
 
 // Device views.
@@ -123,25 +138,28 @@ struct EventsView {
 struct WorkView {
   Counters* cnt;
   EventRec* rec;                 // [max_events]
-  uint32_t* queue[kQueues];      // [max_events] each: one per class, then the retry queue
+  uint32_t* queue[kQueues];      // [max_events] each: one per class, then the retry queues
   uint32_t class_maxh[kMaxClasses];
+  uint32_t class_maxmod[kMaxClasses];  // hits of an event's busiest module a class takes
   int n_classes;
+  int ring_retry;                // a wide-window pass follows the classes (narrow overflows go there)
   // hits from the clustering kernel, at provisional positions (event pixel
   // base + sensor pixel offset + rank in the sensor)
   float2* prov;                  // [cap_pixels]
   uint16_t* prov_key;            // [cap_pixels] smallest pixel key (cluster output only)
   uint16_t* ev_cbase;            // [max_events][kMaxSensors + 1] canonical id of each sensor's first hit
   // scratch tracks (SoA), bump-allocated per event, canonical order within
-  // the event; the emit kernel fits them from their hits' ids
+  // the event; the emit kernel fits them from their hits' positions
   float* tr_logit;               // [cap_tracks] classifier logit (0 without the classifier)
   uint16_t* tr_nhits;            // [cap_tracks]
   uint32_t* tr_hitoff;           // [cap_tracks] first hit, relative to the event's hit base
   uint32_t* tr_event;            // [cap_tracks] event of the track
   uint32_t* tr_hits;             // [cap_hits] module << 16 | event-local canonical id
+  float2* tr_pos;                // [cap_hits] position (x, y) of each of those hits
   // tracking-kernel hit slots per class: kMaxModules positions per candidate,
   // max_tracks candidates per CTA, one region per CTA of the class
   uint16_t* trk_hits[kMaxClasses];
-  RingScratch ring;
+  RingScratch ring[2];           // per shape (null trk: shape not set up)
   // slow paths (null: not available, such events are flagged VELO_EV_OVERFLOW)
   unsigned char* big_scratch;    // [kBigCtas][kBigScratchBytes]
   unsigned char* huge_scratch;   // [kHugeCtas][huge_bytes]: whole-event layout, then hit slots
@@ -180,12 +198,13 @@ size_t huge_region_bytes(uint32_t n_modules);
 cudaError_t launch_track_huge(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                               int cls, cudaStream_t st);
 
-// Module-window tracking kernel (velo_track_ring.cu).
-uint32_t ring_smem_bytes();
-cudaError_t ring_set_smem_limit();
-cudaError_t ring_occupancy(int* blocks_per_sm);
-cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
-                              int cls, int queue, int n_ctas, cudaStream_t st);
+// Module-window tracking kernel (velo_track_ring.cu), shape 0 (wide) or 1
+// (narrow).
+uint32_t ring_smem_bytes(int shape);
+cudaError_t ring_set_smem_limit(int shape);
+cudaError_t ring_occupancy(int shape, int* blocks_per_sm);
+cudaError_t launch_track_ring(int shape, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
+                              const WorkView& wk, int cls, int queue, int n_ctas, cudaStream_t st);
 
 // Output kernels (velo_emit.cu).
 cudaError_t launch_scan(uint32_t n_events, const WorkView& wk, const velo_output& out, cudaStream_t st);

@@ -224,6 +224,7 @@ extern "C" int velo_cluster_static(const velo_geometry* geometry, const velo_eve
   for (int k = 0; k < kQueues; ++k) wk.queue[k] = (uint32_t*)(b + kOffQueue) + (size_t)k * kStaticMaxEvents;
   wk.n_classes = 1;                 // every event is queued once; nothing consumes the queue here
   wk.class_maxh[0] = 0xFFFFu;
+  wk.class_maxmod[0] = 0xFFFFFFFFu;
   wk.prov = (float2*)(b + kOffProv);
   wk.prov_key = (uint16_t*)(b + kOffKey);
   wk.ev_cbase = (uint16_t*)(b + kOffCbase);

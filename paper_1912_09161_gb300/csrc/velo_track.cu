@@ -501,8 +501,11 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
     const uint32_t K = s_misc[M_KEPT];
     const uint32_t NH = block_exscan(t_hoff, K, s_scan);
     if (tid == 0) {
-      uint32_t tb = atomicAdd(&wk.cnt->track_cursor, K);
-      uint32_t hb = atomicAdd(&wk.cnt->hit_cursor, NH);
+      // both scratch cursors in one 64-bit atomic (tracks in the low word),
+      // as in the module-window kernel that may run at the same time
+      const unsigned long long old = atomicAdd((unsigned long long*)&wk.cnt->track_cursor,
+                                               ((unsigned long long)NH << 32) | K);
+      const uint32_t tb = (uint32_t)old, hb = (uint32_t)(old >> 32);
       uint32_t st = status;
       uint32_t nk = K, nh = NH;
       if ((uint64_t)tb + K > wk.cap_tracks || (uint64_t)hb + NH > wk.cap_hits) {
@@ -533,7 +536,7 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
     const uint32_t tb = s_misc[M_TBASE], hb = s_misc[M_HBASE];
 
     // kept tracks to scratch in canonical order: their hits as module << 16 |
-    // canonical id (the emit kernel fits them from the clustering output)
+    // canonical id, and their positions (the emit kernel fits them)
     for (uint32_t t = tid; t < ntr; t += NT) {
       if (t_key[t] == 0xFFFFFFFFu) continue;
       const uint32_t r = t_rank[t], n = t_n[t];
@@ -544,6 +547,7 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
         const uint32_t p = th[k];
         while (s_cb[kSPM * m] > p) --m;
         wk.tr_hits[h0 + k] = ((uint32_t)m << 16) | pid[p];
+        wk.tr_pos[h0 + k] = pos[p];
       }
       const size_t o = (size_t)tb + r;
       wk.tr_logit[o] = use_mlp ? t_seed[t] : 0.0f;

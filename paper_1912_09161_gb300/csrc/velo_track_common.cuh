@@ -36,13 +36,15 @@ __device__ __forceinline__ float phi_halfwidth(float x, float y, float w) {
 }
 
 // Candidate positions of module m in the phi window around pa: one or two
-// contiguous ranges (bins[k] = end position of bin k of the event).
+// contiguous ranges (bins[k] = end position of bin k of the event; 8- or
+// 16-bit entries).
 struct Cand {
   uint32_t s0, n0, s1, n1;
   __device__ __forceinline__ uint32_t n() const { return n0 + n1; }
   __device__ __forceinline__ uint32_t at(uint32_t k) const { return k < n0 ? s0 + k : s1 + (k - n0); }
 };
-__device__ __forceinline__ Cand window_cands(const uint16_t* bins, int m, float pa, float w) {
+template <typename BinT>
+__device__ __forceinline__ Cand window_cands(const BinT* bins, int m, float pa, float w) {
   const BinWindow bw = bin_window(pa, w);
   const int base = m * kNB;
   const int last = bw.first + bw.count - 1;
@@ -86,10 +88,14 @@ __device__ __forceinline__ void list_append(bool pred, uint16_t val, uint16_t* l
 // An event that runs out of storage in its class goes to the retry queue,
 // which the largest shared-memory class drains after all classes finish;
 // running out there sends it to the global-memory pass (when the handle has
-// one), and running out in that pass marks the event.
-__device__ inline void defer_or_fail(const WorkView& wk, int queue, uint32_t e, uint32_t gbase, uint32_t H, uint32_t status) {
+// one), and running out in that pass marks the event.  An event that
+// outgrows the narrow module window goes first to a pass of the wide one
+// (when the schedule has it), and from there to the retry queue.
+__device__ inline void defer_or_fail(const WorkView& wk, int queue, uint32_t e, uint32_t gbase, uint32_t H, uint32_t status,
+                                     bool narrow = false) {
   int next = -1;
-  if (queue < kRetryQueue) next = kRetryQueue;
+  if (narrow && queue < kRetryQueue && wk.ring_retry) next = kRingRetryQueue;
+  else if (queue < kRetryQueue || queue == kRingRetryQueue) next = kRetryQueue;
   else if (queue == kRetryQueue && wk.huge_scratch && H <= kHugeMaxH) next = kHugeQueue;
   if (next >= 0) {
     const uint32_t pos = atomicAdd(&wk.cnt->queue_len[next], 1u);

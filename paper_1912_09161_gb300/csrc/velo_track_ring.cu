@@ -1,5 +1,6 @@
 // Tracking kernel with a rolling module window: hits -> track candidates, one
-// event per CTA of 128 threads, nine CTAs per SM.
+// event per CTA, in two shapes (RingShape): 128 threads and nine CTAs per SM
+// (wide), or 64 threads, a smaller window and thirteen CTAs per SM (narrow).
 //
 // The search by triplet (paper section 2.3.1) only ever looks at three
 // consecutive modules: round i extends the active tracks into module i
@@ -8,26 +9,32 @@
 // slots (each: the module's hits ordered by phi bin, their canonical ids, the
 // bin ends, a used bitmap and a bitmap of the running round's seed hits), the
 // active tracks (double-buffered records), the list of the round's unused
-// middle hits and the next module's raw hits -- about 23 KB per event; nine
-// events share an SM (the register budget sets the nine).  The hits come straight from the clustering output:
+// middle hits and the next module's raw hits -- about 23 KB per event in the
+// wide shape (nine events share an SM; the register budget sets the nine),
+// 17 KB in the narrow one (thirteen).  The hits come straight from the
+// clustering output:
 //   - round i copies module i - 2's hits into a staging buffer with cp.async
 //     during its phase B;
 //   - round i - 1 bins them by phi into the free slot during its phase A, on
 //     a warp that phase A leaves idle;
 // so every hit is read from global memory once.  After the rounds the kernel
 // applies the plain cuts (or the classifier), ranks the kept candidates
-// canonically and writes their hits (module, canonical id) to scratch for the
-// emit kernel, which fits them.  Candidate hit lists (module << 16 |
-// canonical id, up to kRingTrackHits) and seed records live in the CTA's
-// global region.
-// Events beyond the window's capacities (a module of more than kRingModHits
-// hits, more than kRingMaxAct active tracks, kRingMaxT candidates, kRingMaxH
-// hits, or a candidate of kRingTrackHits hits) go to the retry queue, which a
-// whole-event class drains.  Decisions are the same IEEE single-precision
-// operations, in the same order, as in the whole-event kernel: results are
-// identical whichever kernel runs an event.
+// canonically and writes their hits (module, canonical id) and the hits'
+// positions to scratch for the emit kernel, which fits them.  Candidate hit
+// lists (module << 16 | canonical id, and the positions, which a hit has at
+// hand in shared memory when it joins a candidate; room for one hit per
+// module) and seed records live in the CTA's global region.
+// Events beyond the window's capacities (a module of more than mod_hits hits,
+// more than max_act active tracks, max_t candidates or max_h hits) go on: from
+// the narrow shape to a pass of the wide one (when the schedule has it), from
+// the wide one to the retry queue, which a whole-event class drains.
+// Decisions are the same IEEE single-precision operations, in the same order,
+// as in the whole-event kernel: results are identical whichever kernel and
+// shape run an event.
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "velo_device.cuh"
 #include "velo_fit.cuh"
@@ -40,42 +47,62 @@ namespace {
 
 constexpr int kRingSlots = 4;
 
-// ring slot: hits by phi bin, their canonical ids, bin ends (module-local),
-// bitmaps over the slot's positions: used, and hits of seeds of the running
-// round (merged into used at the next round's start)
-constexpr uint32_t kSlotPos = 0, kSlotPid = 8 * kRingModHits, kSlotBins = kSlotPid + 2 * kRingModHits;
-constexpr uint32_t kSlotUsed = kSlotBins + 2 * kNB, kSlotPend = kSlotUsed + kRingModHits / 8;
-constexpr uint32_t kSlotBytes = kSlotPend + kRingModHits / 8;
-// active-track records, per list: x, y, tx, ty (f32), track id (u16), module
-// of the last hit, hits, skips (u8)
-constexpr uint32_t kActBytes = kRingMaxAct * (4 * 4 + 2 + 1 + 1 + 1);
-static_assert(kActBytes % 16 == 0, "second list aligned");
-static_assert(2u * kActBytes >= 2u * 4u * kNB, "two warps' bin counters fit the active lists");
-static_assert(2 * kActBytes >= 3u * 4u * kRingMaxT, "ranking arrays fit the track lists");
-static_assert(kRingSlots * kSlotBytes >= 2u * (kRingMaxH / 8), "seen bitmaps fit the ring");
+__host__ __device__ constexpr uint32_t ralign16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // shared-memory plan
 struct RingLayout {
   uint32_t z, cb, misc, scan, wbin, blist, stage, slots, act, total;
 };
 
-__host__ __device__ constexpr uint32_t ralign16(uint32_t x) { return (x + 15u) & ~15u; }
+// Compile-time view of ring shape SH.
+//   ring slot: hits by phi bin, their canonical ids, bin ends (module-local;
+//   8-bit when a module holds fewer than 256 hits), bitmaps over the slot's
+//   positions: used, and hits of seeds of the running round (merged into
+//   used at the next round's start);
+//   active-track records, per list: x, y, tx, ty (f32), track id (u16),
+//   module of the last hit, hits, skips (u8).
+template <int SH>
+struct RS {
+  static constexpr RingShape shape = kRingShapes[SH];
+  static constexpr int NT = shape.threads, CPS = shape.ctas_per_sm, NW = NT / 32;
+  static constexpr uint32_t MOD = shape.mod_hits, MAXH = shape.max_h, ACT = shape.max_act, MAXT = shape.max_t;
+  using BinT = typename std::conditional<(MOD < 256), uint8_t, uint16_t>::type;
+  static constexpr uint32_t BW = (MOD + 31) / 32;        // bitmap words
+  static constexpr uint32_t BMB = ralign16(4 * BW);      // bitmap bytes, padded
+  static constexpr uint32_t kSlotPos = 0, kSlotPid = 8 * MOD;
+  static constexpr uint32_t kSlotBins = ralign16(kSlotPid + 2 * MOD);
+  static constexpr uint32_t kSlotUsed = ralign16(kSlotBins + (uint32_t)sizeof(BinT) * kNB);
+  static constexpr uint32_t kSlotPend = kSlotUsed + BMB;
+  static constexpr uint32_t kSlotBytes = kSlotPend + BMB;
+  static constexpr uint32_t kActBytes = ACT * (4 * 4 + 2 + 1 + 1 + 1);
+  static constexpr bool kNarrow = SH == kRingNarrow;
+  static_assert(NT == 64 || NT == 128, "two or four warps");
+  static_assert(MOD <= 256, "slot positions fit 8 bits");
+  static_assert(kActBytes % 4 == 0, "second list aligned");
+  static_assert(2u * kActBytes >= 2u * 4u * kNB, "two warps' bin counters fit the active lists");
+  static_assert(2u * kActBytes >= 13u * MAXT, "ranking arrays and hit counts fit the track lists");
+  static_assert(kRingSlots * kSlotBytes >= 2u * (MAXH / 8), "seen bitmaps fit the ring");
 
-__host__ __device__ inline RingLayout ring_layout() {
-  RingLayout L{};
-  uint32_t o = 0;
-  L.z = o; o = ralign16(o + 4 * kMaxModules);
-  L.cb = o; o = ralign16(o + 2 * (kMaxSensors + 1));
-  L.misc = o; o = ralign16(o + 4 * 32);
-  L.scan = o; o = ralign16(o + 4 * 32);
-  L.wbin = o; o = ralign16(o + 4 * kNB);                 // bin counters (the binning warp)
-  L.blist = o; o = ralign16(o + kRingModHits);            // unused middle hits of the round
-  L.stage = o; o = ralign16(o + 8 * kRingModHits);        // raw hits of the next module
-  L.slots = o; o = ralign16(o + kRingSlots * kSlotBytes);
-  L.act = o; o = ralign16(o + 2 * kActBytes);
-  L.total = o;
-  return L;
-}
+  __host__ __device__ static constexpr RingLayout layout() {
+    RingLayout L{};
+    uint32_t o = 0;
+    L.z = o; o = ralign16(o + 4 * kMaxModules);
+    L.cb = o; o = ralign16(o + 2 * (kMaxSensors + 1));
+    L.misc = o; o = ralign16(o + 4 * 32);
+    L.scan = o; o = ralign16(o + 4 * 32);
+    L.wbin = o; o = ralign16(o + 4 * kNB);     // bin counters (the binning warp)
+    L.blist = o; o = ralign16(o + MOD);         // unused middle hits of the round
+    L.stage = o; o = ralign16(o + 8 * MOD);     // raw hits of the next module
+    L.slots = o; o = ralign16(o + kRingSlots * kSlotBytes);
+    L.act = o; o = ralign16(o + 2 * kActBytes);
+    L.total = o;
+    return L;
+  }
+};
+// Each shape's CTAs per SM fit the SM's 228 KB of shared memory (1 KB per CTA
+// reserved by the hardware).
+static_assert(RS<kRingWide>::CPS * (RS<kRingWide>::layout().total + 1024u) <= 228u * 1024u, "wide shape fits");
+static_assert(RS<kRingNarrow>::CPS * (RS<kRingNarrow>::layout().total + 1024u) <= 228u * 1024u, "narrow shape fits");
 
 enum RMisc {
   R_EVENT = 0, R_NTR = 1, R_MAXMOD = 2, R_NB = 3, R_KEPT = 5, R_TBASE = 7, R_HBASE = 8, R_SKIP = 10, R_NACT = 12
@@ -87,16 +114,17 @@ struct ActList {
   uint8_t *m, *n, *skip;
 };
 
+template <uint32_t ACT>
 __device__ __forceinline__ ActList act_list(unsigned char* base) {
   ActList a;
   a.x = (float*)base;
-  a.y = a.x + kRingMaxAct;
-  a.tx = a.y + kRingMaxAct;
-  a.ty = a.tx + kRingMaxAct;
-  a.t = (uint16_t*)(a.ty + kRingMaxAct);
-  a.m = (uint8_t*)(a.t + kRingMaxAct);
-  a.n = a.m + kRingMaxAct;
-  a.skip = a.n + kRingMaxAct;
+  a.y = a.x + ACT;
+  a.tx = a.y + ACT;
+  a.ty = a.tx + ACT;
+  a.t = (uint16_t*)(a.ty + ACT);
+  a.m = (uint8_t*)(a.t + ACT);
+  a.n = a.m + ACT;
+  a.skip = a.n + ACT;
   return a;
 }
 
@@ -114,9 +142,17 @@ __device__ __forceinline__ int list_slot(bool pred, uint32_t* counter, uint32_t 
   return (pred && idx < cap) ? (int)idx : -1;
 }
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+// L2 policy for data read once (the clustering output): evicted before the
+// CTA's own global region, which each event rewrites and reads back.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src, uint64_t policy) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+  asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem_src), "l"(policy)
+               : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -130,31 +166,34 @@ __device__ __forceinline__ uint32_t module_src(const uint16_t* cb, const uint32_
   return __ldg(&so[s]) + (k - cb[s]);
 }
 
-// Copies module m's hits (canonical order) into the staging buffer, every
-// thread its share of 8-byte cp.async copies; committed as one group.
+// Copies module m's hits (canonical order) into the staging buffer: thread
+// `rank` of `nthreads` issues its share of 8-byte cp.async copies, committed
+// as one group.
 __device__ __forceinline__ void stage_module(int m, const uint16_t* cb, const uint32_t* so, const float2* prov,
-                                             float2* stage) {
+                                             float2* stage, uint32_t rank, uint32_t nthreads) {
   const uint32_t c0 = cb[kSPM * m], n = (uint32_t)cb[kSPM * (m + 1)] - c0;
-  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) cp_async8(stage + j, prov + module_src(cb, so, m, c0 + j));
+  const uint64_t pol = l2_evict_first();
+  for (uint32_t j = rank; j < n; j += nthreads) cp_async8(stage + j, prov + module_src(cb, so, m, c0 + j), pol);
   cp_async_commit();
 }
 
 // Bins module m into its ring slot (one warp, counters wc[kNB]): hits by phi
-// bin, their canonical ids, the module-local bin ends, a clear used bitmap.
-// src(j) gives hit j of the module in canonical order.
-template <class Src>
+// bin, their canonical ids, the module-local bin ends, clear used and pending
+// bitmaps.  src(j) gives hit j of the module in canonical order.
+template <int SH, class Src>
 __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned char* slots, uint32_t* wc, Src src) {
+  using C = RS<SH>;
   const int lane = threadIdx.x & 31;
   constexpr int BPL = kNB / 32;
-  unsigned char* slot = slots + (m & (kRingSlots - 1)) * kSlotBytes;
-  float2* pos = (float2*)(slot + kSlotPos);
-  uint16_t* pid = (uint16_t*)(slot + kSlotPid);
-  uint16_t* bins = (uint16_t*)(slot + kSlotBins);
-  uint32_t* ub = (uint32_t*)(slot + kSlotUsed);  // then the pending bitmap
+  unsigned char* slot = slots + (m & (kRingSlots - 1)) * C::kSlotBytes;
+  float2* pos = (float2*)(slot + C::kSlotPos);
+  uint16_t* pid = (uint16_t*)(slot + C::kSlotPid);
+  typename C::BinT* bins = (typename C::BinT*)(slot + C::kSlotBins);
+  uint32_t* ub = (uint32_t*)(slot + C::kSlotUsed);  // then the pending bitmap
   const uint32_t c0 = cb[kSPM * m], n = (uint32_t)cb[kSPM * (m + 1)] - c0;
 #pragma unroll
   for (int u = 0; u < BPL; ++u) wc[BPL * lane + u] = 0;
-  if (lane < (int)(2 * kRingModHits / 32)) ub[lane] = 0;
+  if (lane < (int)(2 * C::BMB / 4)) ub[lane] = 0;
   __syncwarp();
   for (uint32_t j = lane; j < n; j += 32) {
     const float2 v = src(j);
@@ -173,7 +212,7 @@ __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned c
   for (int u = 0; u < BPL; ++u) {
     wc[BPL * lane + u] = cur;
     cur += cnt[u];
-    bins[BPL * lane + u] = (uint16_t)cur;
+    bins[BPL * lane + u] = (typename C::BinT)cur;
   }
   __syncwarp();
   for (uint32_t j = lane; j < n; j += 32) {
@@ -185,28 +224,34 @@ __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned c
   __syncwarp();
 }
 
+template <typename BinT>
 struct Slot {
   const float2* pos;
   const uint16_t* pid;
-  const uint16_t* bins;
+  const BinT* bins;
   uint32_t* used;
   uint32_t* pend;
 };
 
-__device__ __forceinline__ Slot slot_of(unsigned char* slots, int m) {
-  unsigned char* s = slots + (m & (kRingSlots - 1)) * kSlotBytes;
-  return Slot{(const float2*)(s + kSlotPos), (const uint16_t*)(s + kSlotPid), (const uint16_t*)(s + kSlotBins),
-              (uint32_t*)(s + kSlotUsed), (uint32_t*)(s + kSlotPend)};
+template <int SH>
+__device__ __forceinline__ Slot<typename RS<SH>::BinT> slot_of(unsigned char* slots, int m) {
+  using C = RS<SH>;
+  unsigned char* s = slots + (m & (kRingSlots - 1)) * C::kSlotBytes;
+  return Slot<typename C::BinT>{(const float2*)(s + C::kSlotPos), (const uint16_t*)(s + C::kSlotPid),
+                                (const typename C::BinT*)(s + C::kSlotBins), (uint32_t*)(s + C::kSlotUsed),
+                                (uint32_t*)(s + C::kSlotPend)};
 }
 
 // MLP: the classifier keeps the candidates (a separate instantiation, so that
 // the plain kernel carries none of its code or registers).
-template <int GA, int GB, bool MLP>
+template <int SH, int GA, int GB, bool MLP>
 __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo, const DevParams& par,
                                              const EventsView& ev, const WorkView& wk, int cls, int qi, uint32_t e,
                                              uint32_t H, uint32_t gbase, uint32_t status, unsigned char* smem) {
-  constexpr int NT = kRingThreads, NW = NT / 32;
-  const RingLayout L = ring_layout();
+  using C = RS<SH>;
+  constexpr int NT = C::NT, NW = C::NW;
+  constexpr uint32_t MAXT = C::MAXT;
+  constexpr RingLayout L = C::layout();
   float* s_z = (float*)(smem + L.z);
   uint16_t* s_cb = (uint16_t*)(smem + L.cb);
   uint32_t* s_misc = (uint32_t*)(smem + L.misc);
@@ -216,10 +261,11 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   float2* stage = (float2*)(smem + L.stage);
   unsigned char* slots = smem + L.slots;
   uint32_t* t_key = (uint32_t*)(smem + L.act);  // after the rounds
-  uint32_t* t_rank = t_key + kRingMaxT;
-  uint32_t* t_hoff = t_rank + kRingMaxT;         // indexed by rank
+  uint32_t* t_rank = t_key + MAXT;
+  uint32_t* t_hoff = t_rank + MAXT;              // indexed by rank
+  uint8_t* t_n = (uint8_t*)(t_hoff + MAXT);      // hits per candidate
   uint32_t* seen1 = (uint32_t*)slots;            // after the rounds, over canonical ids
-  uint32_t* seen2 = seen1 + kRingMaxH / 32;
+  uint32_t* seen2 = seen1 + C::MAXH / 32;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ns = geo->n_sensors;
@@ -228,13 +274,15 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   constexpr bool use_mlp = MLP;
 
   // this CTA's global region
-  const RingScratch& R = wk.ring;
-  uint32_t* trk = R.trk + (size_t)blockIdx.x * kRingMaxT * kRingTrackHits;  // module << 16 | canonical id
-  uint16_t* mpa = R.seed_hit + (size_t)blockIdx.x * 3 * kRingMaxT;
-  uint16_t* mpb = mpa + kRingMaxT;
-  uint16_t* mpc = mpb + kRingMaxT;
-  uint8_t* mn = R.n_hits + (size_t)blockIdx.x * kRingMaxT;
-  float* mseed = R.seed + (size_t)blockIdx.x * kRingMaxT;
+  const RingScratch& R = wk.ring[SH];
+  constexpr uint32_t TH = kRingTrackHits;  // hits per candidate
+  uint32_t* trk = R.trk + (size_t)blockIdx.x * MAXT * TH;  // module << 16 | canonical id
+  float2* tpos = R.trk_pos + (size_t)blockIdx.x * MAXT * TH;
+  uint16_t* mpa = R.seed_hit + (size_t)blockIdx.x * 3 * MAXT;
+  uint16_t* mpb = mpa + MAXT;
+  uint16_t* mpc = mpb + MAXT;
+  uint8_t* mn = R.n_hits + (size_t)blockIdx.x * MAXT;
+  float* mseed = R.seed + (size_t)blockIdx.x * MAXT;
   const uint32_t* so = ev.sensor_off + (size_t)e * ns;
 
   // ---- 1. the last three modules into the ring, the next one staged -------
@@ -257,18 +305,20 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     }
   }
   __syncthreads();
-  if (s_misc[R_MAXMOD] > kRingModHits) {
-    if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
+  if (s_misc[R_MAXMOD] > C::MOD) {
+    if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status, C::kNarrow);
     return;
   }
-  if (nm >= 4) stage_module(nm - 4, s_cb, so, wk.prov, stage);
-  if (warp < 3 && nm - 1 - warp >= 0) {
-    const int m = nm - 1 - warp;
+  if (nm >= 4) stage_module(nm - 4, s_cb, so, wk.prov, stage, tid, NT);
+  // the last three modules, module nm - 1 - k by warp k % NW; bin counters:
+  // the binning warp's own for k = 0, the active lists (unused until the
+  // first round's seeds) for k = 1 and 2
+  for (int k = warp; k < 3; k += NW) {
+    const int m = nm - 1 - k;
+    if (m < 0) break;
     const uint32_t c0 = s_cb[kSPM * m];
-    // bin counters: the binning warp's own, and for warps 1 and 2 the active
-    // lists, unused until the first round's seeds
-    bin_module(m, s_cb, slots, warp == 0 ? s_wbin : (uint32_t*)(smem + L.act) + kNB * (warp - 1),
-               [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
+    bin_module<SH>(m, s_cb, slots, k == 0 ? s_wbin : (uint32_t*)(smem + L.act) + kNB * (k - 1),
+                   [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
   }
   cp_async_wait_all();
   __syncthreads();
@@ -278,18 +328,19 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   bool overflow = false;
   for (int i = nm - 3; i >= 0; --i) {
     const float zi = s_z[i];
-    const Slot Si = slot_of(slots, i), Sb = slot_of(slots, i + 1), Sa = slot_of(slots, i + 2);
+    const auto Si = slot_of<SH>(slots, i), Sb = slot_of<SH>(slots, i + 1), Sa = slot_of<SH>(slots, i + 2);
     bool ovf = false;
     // phase A: every active track is extended into module i by its best
     // hit (GA lanes per track).  Meanwhile warp NW - 2 makes the b and c
     // hits of the last round's seeds used (modules i + 2 and i + 1) and
     // lists the unused middle hits of module i + 1, and warp NW - 1 bins
-    // module i - 1 into the free slot.
+    // module i - 1 into the free slot, then stages module i - 2 (binned in
+    // the next round).
     const uint32_t nact = s_misc[R_NACT + cur];
     // this round's active list and the next round's (pointers formed per
     // round: an array of both indexed by cur would live in local memory)
-    const ActList A = act_list(smem + L.act + (cur ? kActBytes : 0u));
-    const ActList N = act_list(smem + L.act + (cur ? 0u : kActBytes));
+    const ActList A = act_list<C::ACT>(smem + L.act + (cur ? C::kActBytes : 0u));
+    const ActList N = act_list<C::ACT>(smem + L.act + (cur ? 0u : C::kActBytes));
     for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
       const uint32_t j = j0 + lane / GA;
       const int la = lane % GA;
@@ -331,10 +382,11 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
           const uint32_t p = (uint32_t)(best & 0xFFFFu);
           const float2 v = Si.pos[p];
           const float dzq = fsub(zl, zi);
-          if (n >= kRingTrackHits) {
+          if (n >= TH) {
             ovf = true;
           } else {
-            trk[(size_t)t * kRingTrackHits + n] = ((uint32_t)i << 16) | (uint32_t)((best >> 16) & 0xFFFFu);
+            trk[(size_t)t * TH + n] = ((uint32_t)i << 16) | (uint32_t)((best >> 16) & 0xFFFFu);
+            tpos[(size_t)t * TH + n] = v;
             mn[t] = (uint8_t)(n + 1);
             set_bit(Si.used, p);
             tx = fdiv(fsub(xl, v.x), dzq);
@@ -352,7 +404,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
           keep = sk <= par.max_skipped;
         }
       }
-      const int o = list_slot(keep, &s_misc[R_NACT + (cur ^ 1)], kRingMaxAct);
+      const int o = list_slot(keep, &s_misc[R_NACT + (cur ^ 1)], C::ACT);
       if (keep && o < 0) ovf = true;
       if (o >= 0) {
         N.x[o] = xl;
@@ -366,9 +418,9 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       }
     }
     if (warp == NW - 2) {
-      if (lane < (int)(2 * kRingModHits / 32)) {
-        const Slot& S = lane < (int)(kRingModHits / 32) ? Sa : Sb;
-        const int w = lane % (kRingModHits / 32);
+      if (lane < (int)(2 * C::BW)) {
+        const auto& S = lane < (int)C::BW ? Sa : Sb;
+        const int w = lane % C::BW;
         S.used[w] |= S.pend[w];
         S.pend[w] = 0;
       }
@@ -384,10 +436,12 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       }
       if (lane == 0) s_misc[R_NB] = cnt;
     }
-    if (warp == NW - 1 && i >= 1) bin_module(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
+    if (warp == NW - 1 && i >= 1) {
+      bin_module<SH>(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
+      if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage, lane, 32);  // after the warp's reads
+    }
     if (__syncthreads_or(ovf)) { overflow = true; break; }
     if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
-    if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage);  // binned in the next round
     // phase B: seeds with the middle hit b in module i + 1
     {
       const float za = s_z[i + 2], zb = s_z[i + 1];
@@ -401,7 +455,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         const bool has = b0 + g < nbl;
         const uint32_t qb = has ? blist[b0 + g] : 0u;
         unsigned long long best = ~0ull;
-        uint32_t bpos = 0;
+        uint32_t bpos = 0;  // slot positions of the best pair: c | a << 8
         float2 vb = make_float2(0.0f, 0.0f);
         if (has) {
           vb = Sb.pos[qb];
@@ -429,7 +483,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
               const unsigned long long key = ((unsigned long long)__float_as_uint(s2) << 32) | ida | Si.pid[qc];
               if (key < best) {
                 best = key;
-                bpos = qc;
+                bpos = qc | (qa << 8);
               }
             }
           }
@@ -448,27 +502,31 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         float2 vc = make_float2(0.0f, 0.0f);
         if (has && gl == 0 && best != ~0ull) {
           t = atomicAdd(&s_misc[R_NTR], 1u);
-          if (t >= kRingMaxT) {
+          if (t >= MAXT) {
             ovf = true;
           } else {
             const uint32_t ia = (uint32_t)(best >> 16) & 0xFFFFu, ic = (uint32_t)best & 0xFFFFu;
             const uint32_t ib = Sb.pid[qb];
-            uint32_t* th = trk + (size_t)t * kRingTrackHits;
+            uint32_t* th = trk + (size_t)t * TH;
             th[0] = ((uint32_t)(i + 2) << 16) | ia;
             th[1] = ((uint32_t)(i + 1) << 16) | ib;
             th[2] = ((uint32_t)i << 16) | ic;
+            vc = Si.pos[bpos & 0xFFu];
+            float2* tp = tpos + (size_t)t * TH;
+            tp[0] = Sa.pos[bpos >> 8];
+            tp[1] = vb;
+            tp[2] = vc;
             mpa[t] = (uint16_t)ia;
             mpb[t] = (uint16_t)ib;
             mpc[t] = (uint16_t)ic;
             mn[t] = 3;
             mseed[t] = __uint_as_float((uint32_t)(best >> 32));
             set_bit(Sb.pend, qb);
-            set_bit(Si.pend, bpos);
-            vc = Si.pos[bpos];
+            set_bit(Si.pend, bpos & 0xFFu);
             seeded = true;
           }
         }
-        const int o = list_slot(seeded, &s_misc[R_NACT + (cur ^ 1)], kRingMaxAct);
+        const int o = list_slot(seeded, &s_misc[R_NACT + (cur ^ 1)], C::ACT);
         if (seeded && o < 0) ovf = true;
         if (o >= 0) {
           N.x[o] = vc.x;
@@ -482,7 +540,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         }
       }
     }
-    cp_async_wait_all();  // module i - 2 is staged for the next round
+    cp_async_wait_all();  // module i - 2 is staged for the next round (warp NW - 1's copies)
     if (__syncthreads_or(ovf)) { overflow = true; break; }
     cur ^= 1;
   }
@@ -490,19 +548,15 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   if (overflow) {
     cp_async_wait_all();
     __syncthreads();
-    if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
+    if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status, C::kNarrow);
     return;
   }
 
   // ---- 3. plain cuts or classifier, canonical order -----------------------
   const uint32_t ntr = s_misc[R_NTR];
   const uint32_t nwords = (H + 31) / 32;
-  // position in the clustering output of a candidate hit (module << 16 |
-  // canonical id), and its module
-  auto hit_xy = [&](uint32_t h, int& m) -> float2 {
-    m = (int)(h >> 16);
-    return wk.prov[module_src(s_cb, so, m, h & 0xFFFFu)];
-  };
+  // the candidates' hit counts, read by every step below
+  for (uint32_t t = tid; t < ntr; t += NT) t_n[t] = mn[t];
   if (!use_mlp) {
     // plain cuts: >= 4 hits, or 3 hits with a small seed scatter and no hit
     // shared with another candidate
@@ -512,16 +566,24 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     }
     __syncthreads();
     for (uint32_t t = tid; t < ntr; t += NT) {
-      const uint32_t* th = trk + (size_t)t * kRingTrackHits;
-      const uint32_t n = mn[t];
-      for (uint32_t k = 0; k < n; ++k) {
-        const uint32_t h = th[k] & 0xFFFFu, b = 1u << (h & 31);
-        if (atomicOr(&seen1[h >> 5], b) & b) atomicOr(&seen2[h >> 5], b);
+      // the hit list in 16-byte loads, eight hits at a time (independent
+      // loads; entries past the list lie inside its slot and are ignored)
+      const uint4* th4 = (const uint4*)(trk + (size_t)t * TH);
+      const uint32_t n = t_n[t];
+      for (uint32_t k0 = 0; k0 < n; k0 += 8) {
+        const uint4 a = th4[k0 / 4], b = th4[k0 / 4 + 1];
+        const uint32_t hv[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (k0 + j >= n) break;
+          const uint32_t h = hv[j] & 0xFFFFu, bit1 = 1u << (h & 31);
+          if (atomicOr(&seen1[h >> 5], bit1) & bit1) atomicOr(&seen2[h >> 5], bit1);
+        }
       }
     }
     __syncthreads();
     for (uint32_t t = tid; t < ntr; t += NT) {
-      const uint32_t ha = mpa[t], hb = mpb[t], hc = mpc[t], n = mn[t];
+      const uint32_t ha = mpa[t], hb = mpb[t], hc = mpc[t], n = t_n[t];
       bool keep = n >= 4;
       if (n == 3 && mseed[t] < par.max_scatter_3hit)
         keep = !bit(seen2, ha) && !bit(seen2, hb) && !bit(seen2, hc);
@@ -531,13 +593,15 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
     const float kms = fit_kms(par);
     for (uint32_t t = tid; t < ntr; t += NT) {
-      const uint32_t* th = trk + (size_t)t * kRingTrackHits;
-      const uint32_t n = mn[t];
+      const uint32_t* th = trk + (size_t)t * TH;
+      const float2* tp = tpos + (size_t)t * TH;
+      const uint32_t n = t_n[t];
       float st[12];
       fit_track(
           n,
           [&](uint32_t k, float& x, float& y, int& m) {
-            const float2 v = hit_xy(th[k], m);
+            const float2 v = tp[k];
+            m = (int)(th[k] >> 16);
             x = v.x;
             y = v.y;
           },
@@ -557,7 +621,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     uint32_t r = 0;
     for (uint32_t u = 0; u < ntr; ++u) r += t_key[u] < key;
     t_rank[t] = r;
-    t_hoff[r] = mn[t];
+    t_hoff[r] = t_n[t];
     kept_local++;
   }
   kept_local = __reduce_add_sync(kFull, kept_local);
@@ -566,8 +630,10 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   const uint32_t K = s_misc[R_KEPT];
   const uint32_t NH = block_exscan(t_hoff, K, s_scan);
   if (tid == 0) {
-    uint32_t tb = atomicAdd(&wk.cnt->track_cursor, K);
-    uint32_t hb = atomicAdd(&wk.cnt->hit_cursor, NH);
+    // both scratch cursors in one 64-bit atomic (tracks in the low word)
+    const unsigned long long old = atomicAdd((unsigned long long*)&wk.cnt->track_cursor,
+                                             ((unsigned long long)NH << 32) | K);
+    const uint32_t tb = (uint32_t)old, hb = (uint32_t)(old >> 32);
     uint32_t st = status;
     uint32_t nk = K, nh = NH;
     if ((uint64_t)tb + K > wk.cap_tracks || (uint64_t)hb + NH > wk.cap_hits) {
@@ -597,31 +663,46 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   }
   const uint32_t tb = s_misc[R_TBASE], hb = s_misc[R_HBASE];
 
-  // kept tracks to scratch in canonical order: their hits' canonical ids
-  // (the emit kernel fits them from the clustering output)
+  // kept tracks to scratch in canonical order: their hits' canonical ids and
+  // positions (the emit kernel fits them)
   for (uint32_t t = tid; t < ntr; t += NT) {
     if (t_key[t] == 0xFFFFFFFFu) continue;
-    const uint32_t r = t_rank[t], n = mn[t];
-    const uint32_t* th = trk + (size_t)t * kRingTrackHits;
+    const uint32_t r = t_rank[t], n = t_n[t];
+    const uint4* th4 = (const uint4*)(trk + (size_t)t * TH);
+    const float4* tp4 = (const float4*)(tpos + (size_t)t * TH);
     const uint32_t h0 = hb + t_hoff[r];
-    for (uint32_t k = 0; k < n; ++k) wk.tr_hits[h0 + k] = th[k];  // module << 16 | canonical id
+    // outputs with streaming stores (the L2 keeps the CTA's region instead);
+    // the lists in 16-byte loads, four hits at a time
+    for (uint32_t k0 = 0; k0 < n; k0 += 4) {
+      const uint4 a = th4[k0 / 4];
+      const float4 p = tp4[k0 / 2], q = tp4[k0 / 2 + 1];
+      const uint32_t hv[4] = {a.x, a.y, a.z, a.w};
+      const float2 pv[4] = {make_float2(p.x, p.y), make_float2(p.z, p.w), make_float2(q.x, q.y), make_float2(q.z, q.w)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (k0 + j >= n) break;
+        __stcs(&wk.tr_hits[h0 + k0 + j], hv[j]);  // module << 16 | canonical id
+        __stcs(&wk.tr_pos[h0 + k0 + j], pv[j]);
+      }
+    }
     const size_t o = (size_t)tb + r;
-    wk.tr_logit[o] = use_mlp ? mseed[t] : 0.0f;
-    wk.tr_nhits[o] = (uint16_t)n;
-    wk.tr_hitoff[o] = t_hoff[r];
-    wk.tr_event[o] = e;
+    __stcs(&wk.tr_logit[o], use_mlp ? mseed[t] : 0.0f);
+    __stcs(&wk.tr_nhits[o], (unsigned short)n);
+    __stcs(&wk.tr_hitoff[o], t_hoff[r]);
+    __stcs(&wk.tr_event[o], e);
   }
 }
 
-// One event per CTA from queue qi (events of up to kRingMaxH hits, clustered
-// by the clustering kernel).
-template <int GA, int GB, bool MLP>
-__global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kernel(const DevGeometry* __restrict__ geo,
-                                                                     DevParams par, EventsView ev, WorkView wk,
-                                                                     int cls, int qi) {
+// One event per CTA from queue qi (events of up to the shape's hits,
+// clustered by the clustering kernel).
+template <int SH, int GA, int GB, bool MLP>
+__global__ void __launch_bounds__(RS<SH>::NT, RS<SH>::CPS) track_ring_kernel(const DevGeometry* __restrict__ geo,
+                                                                             DevParams par, EventsView ev, WorkView wk,
+                                                                             int cls, int qi) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NT = kRingThreads;
-  const RingLayout L = ring_layout();
+  using C = RS<SH>;
+  constexpr int NT = C::NT;
+  constexpr RingLayout L = C::layout();
   float* s_z = (float*)(smem + L.z);
   uint16_t* s_cb = (uint16_t*)(smem + L.cb);
   uint32_t* s_misc = (uint32_t*)(smem + L.misc);
@@ -639,13 +720,13 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
     const uint32_t e = wk.queue[qi][q];
     const EventRec rec0 = wk.rec[e];
     const uint32_t H = rec0.n_clusters, gbase = rec0.pix_base, status = rec0.status;
-    if (H > kRingMaxH) {
-      if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status);
+    if (H > C::MAXH) {
+      if (tid == 0) defer_or_fail(wk, qi, e, gbase, H, status, C::kNarrow);
       continue;
     }
     const uint16_t* cbg = wk.ev_cbase + (size_t)e * (kMaxSensors + 1);
     for (int s = tid; s <= ns; s += NT) s_cb[s] = cbg[s];
-    window_event<GA, GB, MLP>(geo, par, ev, wk, cls, qi, e, H, gbase, status, smem);
+    window_event<SH, GA, GB, MLP>(geo, par, ev, wk, cls, qi, e, H, gbase, status, smem);
   }
 }
 
@@ -653,39 +734,59 @@ __global__ void __launch_bounds__(kRingThreads, kRingCtasPerSm) track_ring_kerne
 constexpr int kRingGroupA = 1;
 constexpr int kRingGroupB = 2;
 
-}  // namespace
-
-uint32_t ring_smem_bytes() { return ring_layout().total; }
-
-cudaError_t ring_set_smem_limit() {
-  cudaError_t e = cudaFuncSetAttribute(track_ring_kernel<kRingGroupA, kRingGroupB, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_smem_bytes());
+template <int SH>
+cudaError_t set_limit() {
+  const int bytes = (int)RS<SH>::layout().total;
+  cudaError_t e = cudaFuncSetAttribute(track_ring_kernel<SH, kRingGroupA, kRingGroupB, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(track_ring_kernel<kRingGroupA, kRingGroupB, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring_smem_bytes());
+  return cudaFuncSetAttribute(track_ring_kernel<SH, kRingGroupA, kRingGroupB, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// CTAs per SM of the kernel: the smaller of its two instantiations.
-cudaError_t ring_occupancy(int* blocks_per_sm) {
+// CTAs per SM of a shape: the smaller of its two instantiations.
+template <int SH>
+cudaError_t occupancy(int* blocks_per_sm) {
+  const size_t bytes = RS<SH>::layout().total;
   int a = 0, b = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &a, track_ring_kernel<kRingGroupA, kRingGroupB, false>, kRingThreads, ring_smem_bytes());
+      &a, track_ring_kernel<SH, kRingGroupA, kRingGroupB, false>, RS<SH>::NT, bytes);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, track_ring_kernel<kRingGroupA, kRingGroupB, true>,
-                                                      kRingThreads, ring_smem_bytes());
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, track_ring_kernel<SH, kRingGroupA, kRingGroupB, true>,
+                                                      RS<SH>::NT, bytes);
   *blocks_per_sm = a < b ? a : b;
   return e;
 }
 
-cudaError_t launch_track_ring(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
-                              int cls, int queue, int n_ctas, cudaStream_t st) {
+template <int SH>
+cudaError_t launch(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk, int cls,
+                   int queue, int n_ctas, cudaStream_t st) {
+  const size_t bytes = RS<SH>::layout().total;
   if (par.use_mlp && wk.mlp_w != nullptr)
-    track_ring_kernel<kRingGroupA, kRingGroupB, true>
-        <<<n_ctas, kRingThreads, ring_smem_bytes(), st>>>(geo, par, ev, wk, cls, queue);
+    track_ring_kernel<SH, kRingGroupA, kRingGroupB, true><<<n_ctas, RS<SH>::NT, bytes, st>>>(geo, par, ev, wk, cls, queue);
   else
-    track_ring_kernel<kRingGroupA, kRingGroupB, false>
-        <<<n_ctas, kRingThreads, ring_smem_bytes(), st>>>(geo, par, ev, wk, cls, queue);
+    track_ring_kernel<SH, kRingGroupA, kRingGroupB, false><<<n_ctas, RS<SH>::NT, bytes, st>>>(geo, par, ev, wk, cls, queue);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+uint32_t ring_smem_bytes(int shape) {
+  return shape == kRingNarrow ? RS<kRingNarrow>::layout().total : RS<kRingWide>::layout().total;
+}
+
+cudaError_t ring_set_smem_limit(int shape) {
+  return shape == kRingNarrow ? set_limit<kRingNarrow>() : set_limit<kRingWide>();
+}
+
+cudaError_t ring_occupancy(int shape, int* blocks_per_sm) {
+  return shape == kRingNarrow ? occupancy<kRingNarrow>(blocks_per_sm) : occupancy<kRingWide>(blocks_per_sm);
+}
+
+cudaError_t launch_track_ring(int shape, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
+                              const WorkView& wk, int cls, int queue, int n_ctas, cudaStream_t st) {
+  return shape == kRingNarrow ? launch<kRingNarrow>(geo, par, ev, wk, cls, queue, n_ctas, st)
+                              : launch<kRingWide>(geo, par, ev, wk, cls, queue, n_ctas, st);
 }
 
 }  // namespace velo

@@ -12,9 +12,11 @@ from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
-# module-window class (bit 6) with whole-event classes, and whole-event classes alone
-SCHEDULES = [(256, 0x60, 1), (256, 0x60, 0), (128, 0x70, 1), (256, 0x1C, 1), (256, 0x1C, 0), (256, 0x10, 1),
-             (128, 0x15, 1), (128, 0x07, 0), (128, 0x0A, 1)]
+# module-window classes (bit 7 narrow, bit 6 wide) with whole-event classes,
+# and whole-event classes alone
+SCHEDULES = [(256, 0x60, 1), (256, 0x60, 0), (128, 0x70, 1), (256, 0xE0, 1), (256, 0xE0, 0), (256, 0xA0, 1),
+             (128, 0xB0, 0), (256, 0x1C, 1), (256, 0x1C, 0), (256, 0x10, 1), (128, 0x15, 1), (128, 0x07, 0),
+             (128, 0x0A, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -97,4 +99,27 @@ def test_kernel_timing_with_and_without_graphs(env):
             assert all(x > 0 for x in st["ms"][:2]) and st["ms"][4] >= st["ms"][1]
             assert sum(st["events"]) == ev.n_events
             assert sum(st["tracks"]) == int(out.totals.cpu()[0])
+    rec.close()
+
+
+def test_narrow_window_routes_and_passes_on(env):
+    """Under the narrow + wide window schedule the narrow class takes most
+    events; events with a busier module than it holds go to the wide class,
+    and so do events that outgrow it mid-search (a pass of the wide window
+    after the classes).  Every event is reconstructed exactly once."""
+    V, torch, geom, ev = env
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels)
+    stream = torch.cuda.Stream()
+    d = V.upload_events(ev)
+    ct, ch, _ = V.suggested_caps(ev.n_events, ev.n_pixels)
+    out = V.alloc_output(ev.n_events, ct, ch, 0)
+    rec.set_schedule(256, 0xE0, 1)
+    rec.set_timing(True)
+    rec.reconstruct(d, out, stream.cuda_stream)
+    assert rec.sync_status(stream.cuda_stream) == V.velo.VELO_OK
+    st = rec.stats()
+    kinds = [c["kernel"] for c in rec.describe()["classes"]]
+    assert kinds[:2] == ["window_narrow", "window"]
+    assert st["events"][0] > 0.5 * ev.n_events and st["events"][1] > 0
+    assert sum(st["events"]) == ev.n_events
     rec.close()

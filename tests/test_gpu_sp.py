@@ -73,17 +73,21 @@ def test_superpixel_repeated_and_bad_offsets(V, geom):
     ev = velo_synth.generate(velo_synth.config(0, n_events=6))
     off, words = velo_synth.to_superpixels(ev)
     ns = ev.n_sensors
-    # every word of event 2 twice
+    # every word of event 2 twice, each sensor's words followed by a copy
+    parts, off2 = [], [0]
+    for s in range(ev.n_events * ns):
+        seg = words[int(off[s]):int(off[s + 1])]
+        if 2 * ns <= s < 3 * ns:
+            seg = np.concatenate([seg, seg])
+        parts.append(seg)
+        off2.append(off2[-1] + len(seg))
+    dup = np.concatenate(parts)
     a, b = int(off[2 * ns]), int(off[3 * ns])
-    dup = np.concatenate([words[:b], words[a:b], words[b:]])
-    off2 = off.astype(np.int64).copy()
-    for s in range(2 * ns, 3 * ns):
-        off2[s + 1] = off2[s] + 2 * (int(off[s + 1]) - int(off[s]))
-    off2[3 * ns + 1:] += b - a
+    assert len(dup) == len(words) + (b - a)
     uoff, ucol, urow = SP.unpack(off, words, ns)
     unpacked = dataclasses.replace(ev, sensor_off=uoff, col=ucol, row=urow, pix_label=np.full(len(ucol), -1, np.int32))
     orc = oracle.reconstruct(geom, unpacked)
-    rc, res = _run_sp(V, geom, ev.n_events, off2, dup, 2 * ev.n_pixels)
+    rc, res = _run_sp(V, geom, ev.n_events, np.asarray(off2, np.int64), dup, 2 * ev.n_pixels)
     assert rc == V.velo.VELO_OK
     assert_parity(res, orc)
     bad = off.astype(np.int64).copy()
