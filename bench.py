@@ -56,7 +56,16 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "track_kernel_nominal_10k.md")
 # sources of the tracking kernels, in the order the profile summary hashes them
 TRACK_SOURCES = ("velo_track_ring.cu", "velo_track.cu", "velo_track_common.cuh", "velo_internal.cuh",
                  "velo_device.cuh", "velo_fit.cuh", "velo_mlp.cuh")
-KERNELS_BASE = 6            # clustering and its second pass, retry and global-memory tracking passes, scan, emit
+# per call: clustering and its second pass, the queue ordering, the retry and
+# global-memory tracking passes, scan, and the two emit kernels; then one
+# launch per tracking class, and the wide-window pass when both window shapes
+# are in the schedule
+KERNELS_BASE = 8
+
+
+def launches_per_call(desc: dict) -> int:
+    kinds = [c["kernel"] for c in desc["classes"]]
+    return KERNELS_BASE + len(kinds) + (1 if "window_narrow" in kinds and "window" in kinds else 0)
                             # (+ one per class)
 
 
@@ -639,7 +648,7 @@ def run_ours(args):
                      "step_frac": step_bytes / (total_s / args.steps) / 1e9 / peak,
                      "stage_ms": {"cluster": stage[0], "track": stage[1], "scan": stage[2], "emit": stage[3]}},
         "e2e": e2e,
-        "gpu_launches": (KERNELS_BASE + len(desc["classes"])) * args.steps,
+        "gpu_launches": launches_per_call(desc) * args.steps,
         "clocks": clocks.summary(),
     }
     line["serving"] = serve_res

@@ -425,6 +425,7 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
   CUDA_TRY(launch_cluster_big(h->d_geo, ev, wk, h->par.gec_max_pixels, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[1], st, mark));
   if (E) {
+    CUDA_TRY(launch_order(wk, h->n_classes, st));
     if (h->sched.concurrent) {
       CUDA_TRY(cudaEventRecord(h->fork, st));
       for (int k = h->n_classes - 1; k >= 0; --k) {

@@ -191,6 +191,8 @@ cudaError_t track_set_smem_limit(int n_threads, int bytes);
 cudaError_t track_occupancy(int n_threads, int smem, int* blocks_per_sm);
 cudaError_t launch_track(const DevGeometry* geo, const DevParams& par, const EventsView& ev, const WorkView& wk,
                          const Caps& caps, int cls, int queue, int n_threads, int n_ctas, cudaStream_t st);
+// Reorders each class queue by decreasing hit count (before the classes run).
+cudaError_t launch_order(const WorkView& wk, int n_classes, cudaStream_t st);
 // Global-memory pass of the whole-event kernel over the huge queue (capacities
 // huge_caps(n_modules); working memory in wk.huge_scratch).
 Caps huge_caps(uint32_t n_modules);

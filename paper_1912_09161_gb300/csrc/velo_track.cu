@@ -594,6 +594,47 @@ cudaError_t launch_track_huge(const DevGeometry* geo, const DevParams& par, cons
   return cudaGetLastError();
 }
 
+// Busiest events first: one block per class queue reorders it by decreasing
+// hit count (a counting sort over kOrderBuckets buckets of the class's range;
+// order within a bucket is arbitrary), so that the persistent CTAs finish on
+// small events and the SMs drain evenly.  Results do not depend on the order.
+// The storage of queue temp[k] (empty until the tracking kernels run) holds
+// class k's sorted copy.
+constexpr int kOrderThreads = 1024, kOrderBuckets = 128;
+
+__global__ void __launch_bounds__(kOrderThreads) order_kernel(WorkView wk, int n_classes) {
+  __shared__ uint32_t s_off[kOrderBuckets];
+  __shared__ uint32_t s_scan[32];
+  const int k = blockIdx.x;
+  if (k >= n_classes) return;
+  const int temps[kMaxClasses] = {kRetryQueue, kHugeQueue, kBigSensorQueue, kRingRetryQueue};
+  uint32_t* q = wk.queue[k];
+  uint32_t* tmp = wk.queue[temps[k]];
+  const uint32_t n = *(volatile uint32_t*)&wk.cnt->queue_len[k];
+  const uint32_t maxh = wk.class_maxh[k] ? wk.class_maxh[k] : 1u;
+  auto bucket = [&](uint32_t e) -> uint32_t {  // 0 = busiest
+    const uint64_t b = (uint64_t)wk.rec[e].n_clusters * kOrderBuckets / ((uint64_t)maxh + 1);
+    return (uint32_t)(kOrderBuckets - 1) - (uint32_t)(b < kOrderBuckets ? b : kOrderBuckets - 1);
+  };
+  for (int b = threadIdx.x; b < kOrderBuckets; b += kOrderThreads) s_off[b] = 0;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += kOrderThreads) atomicAdd(&s_off[bucket(q[i])], 1u);
+  __syncthreads();
+  block_exscan(s_off, kOrderBuckets, s_scan);
+  for (uint32_t i = threadIdx.x; i < n; i += kOrderThreads) {
+    const uint32_t e = q[i];
+    tmp[atomicAdd(&s_off[bucket(e)], 1u)] = e;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += kOrderThreads) q[i] = tmp[i];
+}
+
+cudaError_t launch_order(const WorkView& wk, int n_classes, cudaStream_t st) {
+  if (n_classes <= 0) return cudaSuccess;
+  order_kernel<<<n_classes, kOrderThreads, 0, st>>>(wk, n_classes);
+  return cudaGetLastError();
+}
+
 cudaError_t track_set_smem_limit(int n_threads, int bytes) {
   switch (n_threads) {
     case 128: return cudaFuncSetAttribute(track_kernel<128, kGroupA, kGroupB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
