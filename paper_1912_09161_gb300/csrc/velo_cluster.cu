@@ -236,25 +236,40 @@ __device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const u
     }
     if (!__any_sync(kFull, reach)) break;
   }
+  // component label = smallest position: start from the smallest of the
+  // pixel's own and its neighbours' positions, then take the smallest label
+  // among the neighbours and that label's own label, until no label changes
+  // (labels only ever name pixels of the component and only decrease; when
+  // stable, neighbours agree, so the label is the component's smallest)
   uint32_t lab[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     nb[r] &= vm;
-    lab[r] = lane + 32u * r;
+    const uint32_t e = lane + 32u * r;
+    lab[r] = nb[r] ? min(e, (uint32_t)(__ffsll((long long)nb[r]) - 1)) : e;
   }
-  // propagate the smallest position over the neighbour masks
   while (true) {
-    bool ch = false;
+    uint32_t m[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
+      m[r] = lab[r];
       uint64_t bits = nb[r];
       const uint32_t cnt = __reduce_max_sync(kFull, (uint32_t)__popcll(bits));
       for (uint32_t it = 0; it < cnt; ++it) {
         const uint32_t q = bits ? (uint32_t)(__ffsll((long long)bits) - 1) : (lane + 32u * r);
         bits &= bits - 1;
-        const uint32_t lq = warp_fetch<R>(lab, q);
-        if (lq < lab[r]) { lab[r] = lq; ch = true; }
+        m[r] = min(m[r], warp_fetch<R>(lab, q));
       }
+    }
+    uint32_t jm[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) jm[r] = warp_fetch<R>(m, m[r]);
+    bool ch = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t v = min(m[r], jm[r]);
+      ch |= v < lab[r];
+      lab[r] = v;
     }
     if (!__any_sync(kFull, ch)) break;
   }
@@ -340,21 +355,21 @@ __device__ void cluster_segments(const DevGeometry* __restrict__ geo, const uint
     if (!__any_sync(kFull, reach)) break;
   }
   nb &= vseg;
-  // propagate the smallest position over the neighbour masks
-  uint32_t lab = (uint32_t)sl;
+  // smallest position of the component, as in the one-sensor path: start
+  // from the smallest of the own and the neighbours' positions, then the
+  // smallest of the neighbours' labels and that label's label, until stable
+  uint32_t lab = nb ? min((uint32_t)sl, (uint32_t)(__ffs(nb) - 1)) : (uint32_t)sl;
   while (true) {
-    bool ch = false;
-    uint32_t bits = nb;
+    uint32_t m = lab, bits = nb;
     const uint32_t cnt = __reduce_max_sync(kFull, (uint32_t)__popc(bits));
     for (uint32_t it = 0; it < cnt; ++it) {
       const int q = bits ? __ffs(bits) - 1 : sl;
       bits &= bits - 1;
-      const uint32_t lq = __shfl_sync(kFull, lab, q, W);
-      if (lq < lab) {
-        lab = lq;
-        ch = true;
-      }
+      m = min(m, __shfl_sync(kFull, lab, q, W));
     }
+    m = min(m, __shfl_sync(kFull, m, (int)m, W));
+    const bool ch = m < lab;
+    lab = m;
     if (!__any_sync(kFull, ch)) break;
   }
   // member sums at the root: count << 56 | sum(col) << 28 | sum(row)
