@@ -198,41 +198,43 @@ __device__ uint32_t cluster_sensor_reg(const uint16_t* __restrict__ col, const u
   for (int r = 0; r < R; ++r) nb[r] = 0;
   for (uint32_t d = 1; d < NE; ++d) {
     bool reach = false;
-    // position e + d (e - d) of every register of this lane is held by lane
-    // (lane + d) mod 32 ((lane - d) mod 32), in the register shifted by the
-    // carry: one shuffle per register and direction
+    // position e + d of every register of this lane is held by lane
+    // (lane + d) mod 32, in the register shifted by the carry: one shuffle
+    // per register.  Adjacency is symmetric: the pixel d positions back
+    // learns of the pair from this lane's forward test (one more shuffle of
+    // the per-register flags).
     const uint32_t sf = (lane + d) & 31u, cf = ((uint32_t)lane + d) >> 5;
     const int tb = lane - (int)d;
     const uint32_t sb = (uint32_t)tb & 31u;
     const int cb = tb >> 5;  // 0 or negative
-    uint32_t xf[R], xb[R];
+    uint32_t xf[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      xf[j] = __shfl_sync(kFull, k[j], sf);
-      xb[j] = __shfl_sync(kFull, k[j], sb);
-    }
+    for (int j = 0; j < R; ++j) xf[j] = __shfl_sync(kFull, k[j], sf);
+    uint32_t fwd = 0;  // bit r: element lane + 32 r is adjacent to element lane + 32 r + d
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const uint32_t e = lane + 32u * r;
-      const uint32_t qf = e + d, qb = e - d;
-      const int rf = r + (int)cf, rb = r + cb;
-      uint32_t kf = kInv, kb = kInv;
+      const uint32_t qf = e + d;
+      const int rf = r + (int)cf;
+      uint32_t kf = kInv;
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
+      for (int j = 0; j < R; ++j)
         if (rf == j) kf = xf[j];
-        if (rb == j) kb = xb[j];
-      }
-      if (!valid[r]) continue;
-      if (qf < NE && kf != kInv && kf - k[r] <= 513u) {
+      if (valid[r] && qf < NE && kf != kInv && kf - k[r] <= 513u) {
         reach = true;
         const uint32_t dl = kf - k[r];
-        if (dl == 1u || dl - 511u <= 2u) nb[r] |= 1ull << qf;
+        if (dl == 1u || dl - 511u <= 2u) {
+          nb[r] |= 1ull << qf;
+          fwd |= 1u << r;
+        }
       }
-      if (e >= d && k[r] - kb <= 513u) {
-        reach = true;
-        const uint32_t dl = k[r] - kb;
-        if (dl == 1u || dl - 511u <= 2u) nb[r] |= 1ull << qb;
-      }
+    }
+    const uint32_t bwd = __shfl_sync(kFull, fwd, sb);  // flags of the lane holding positions e - d
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t e = lane + 32u * r;
+      const int rb = r + cb;
+      if (valid[r] && e >= d && rb >= 0 && ((bwd >> rb) & 1u)) nb[r] |= 1ull << (e - d);
     }
     if (!__any_sync(kFull, reach)) break;
   }
@@ -338,20 +340,15 @@ __device__ void cluster_segments(const DevGeometry* __restrict__ geo, const uint
   // neighbour masks over segment positions, scanning outward until out of reach
   uint32_t nb = 0;
   for (int d = 1; d < W; ++d) {
-    const uint32_t kf = __shfl_down_sync(kFull, k, d, W), kb = __shfl_up_sync(kFull, k, d, W);
-    bool reach = false;
-    if (valid) {
-      if (sl + d < W && kf != kInv && kf - k <= 513u) {
-        reach = true;
-        const uint32_t dl = kf - k;
-        if (dl == 1u || dl - 511u <= 2u) nb |= 1u << (sl + d);
-      }
-      if (sl >= d && k - kb <= 513u) {
-        reach = true;
-        const uint32_t dl = k - kb;
-        if (dl == 1u || dl - 511u <= 2u) nb |= 1u << (sl - d);
-      }
-    }
+    // forward test against the pixel d positions on; the pixel d positions
+    // back learns of an adjacent pair from this lane's flag
+    const uint32_t kf = __shfl_down_sync(kFull, k, d, W);
+    const bool reach = valid && sl + d < W && kf != kInv && kf - k <= 513u;
+    const uint32_t dl = kf - k;
+    const bool fwd = reach && (dl == 1u || dl - 511u <= 2u);
+    if (fwd) nb |= 1u << (sl + d);
+    const bool bwd = __shfl_up_sync(kFull, (uint32_t)fwd, d, W) != 0u;
+    if (valid && sl >= d && bwd) nb |= 1u << (sl - d);
     if (!__any_sync(kFull, reach)) break;
   }
   nb &= vseg;
@@ -753,12 +750,20 @@ __device__ bool cluster_event(const DevGeometry* __restrict__ geo, const EventsV
       asm volatile("prefetch.global.L2 [%0];\n" ::"l"(base + (k % lines) * 128u));
     }
   }
-  // sensors by size class
-  for (int s = tid; s < ns; s += NT) {
-    const uint32_t n = s_soff[s + 1] - s_soff[s];
-    const int c = n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : n <= 64 ? 3 : n <= kMidStage ? 4 : n <= kWarpStage ? 5 : 6;
-    const uint32_t p = atomicAdd(&s_misc[CM_CLASS + c], 1u);
-    S.list[c * kMaxSensors + p] = (uint8_t)s;
+  // sensors by size class (one shared-memory atomic per class and warp)
+  for (int s0 = warp * 32; s0 < ns; s0 += NT) {
+    const int s = s0 + lane;
+    int c = kSizeClasses;  // no sensor
+    if (s < ns) {
+      const uint32_t n = s_soff[s + 1] - s_soff[s];
+      c = n <= 8 ? 0 : n <= 16 ? 1 : n <= 32 ? 2 : n <= 64 ? 3 : n <= kMidStage ? 4 : n <= kWarpStage ? 5 : 6;
+    }
+    const uint32_t same = __match_any_sync(kFull, c);
+    const int leader = __ffs(same) - 1;
+    uint32_t base = 0;
+    if (lane == leader && c < kSizeClasses) base = atomicAdd(&s_misc[CM_CLASS + c], (uint32_t)__popc(same));
+    base = __shfl_sync(kFull, base, leader);
+    if (c < kSizeClasses) S.list[c * kMaxSensors + base + __popc(same & ((1u << lane) - 1u))] = (uint8_t)s;
   }
   __syncthreads();
   const bool big = s_misc[CM_CLASS + 6] != 0;
