@@ -159,11 +159,29 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Hits of module m in canonical order, from the clustering output: canonical
 // id k of sensor s sits at so[s] + (k - cb[s]) (so: the event's absolute
-// sensor offsets).
-__device__ __forceinline__ uint32_t module_src(const uint16_t* cb, const uint32_t* so, int m, uint32_t k) {
+// sensor offsets).  ModuleSrc holds, in every lane of the calling warp, the
+// module's four sensor offsets minus their canonical bases (one load by lanes
+// 0-3 and four shuffles), so that a hit's source costs no memory access.
+struct ModuleSrc {
+  uint32_t base[kSPM];  // so[s] - cb[s]
+  uint32_t cut1, cut2, cut3;  // cb of the module's second, third and fourth sensors
+  __device__ __forceinline__ uint32_t at(uint32_t k) const {
+    const uint32_t b = k >= cut3 ? base[3] : k >= cut2 ? base[2] : k >= cut1 ? base[1] : base[0];
+    return b + k;
+  }
+};
+__device__ __forceinline__ ModuleSrc module_src(const uint16_t* cb, const uint32_t* so, int m) {
+  const int lane = threadIdx.x & 31;
   const uint32_t s0 = kSPM * m;
-  const uint32_t s = s0 + (k >= cb[s0 + 1]) + (k >= cb[s0 + 2]) + (k >= cb[s0 + 3]);
-  return __ldg(&so[s]) + (k - cb[s]);
+  uint32_t v = 0;
+  if (lane < kSPM) v = __ldg(&so[s0 + lane]) - cb[s0 + lane];
+  ModuleSrc r;
+#pragma unroll
+  for (int q = 0; q < kSPM; ++q) r.base[q] = __shfl_sync(kFull, v, q);
+  r.cut1 = cb[s0 + 1];
+  r.cut2 = cb[s0 + 2];
+  r.cut3 = cb[s0 + 3];
+  return r;
 }
 
 // Copies module m's hits (canonical order) into the staging buffer: thread
@@ -173,13 +191,17 @@ __device__ __forceinline__ void stage_module(int m, const uint16_t* cb, const ui
                                              float2* stage, uint32_t rank, uint32_t nthreads) {
   const uint32_t c0 = cb[kSPM * m], n = (uint32_t)cb[kSPM * (m + 1)] - c0;
   const uint64_t pol = l2_evict_first();
-  for (uint32_t j = rank; j < n; j += nthreads) cp_async8(stage + j, prov + module_src(cb, so, m, c0 + j), pol);
+  const ModuleSrc src = module_src(cb, so, m);
+  for (uint32_t j = rank; j < n; j += nthreads) cp_async8(stage + j, prov + src.at(c0 + j), pol);
   cp_async_commit();
 }
 
 // Bins module m into its ring slot (one warp, counters wc[kNB]): hits by phi
 // bin, their canonical ids, the module-local bin ends, clear used and pending
-// bitmaps.  src(j) gives hit j of the module in canonical order.
+// bitmaps.  src(j) gives hit j of the module in canonical order (the module
+// holds at most MOD hits, checked at the event's start); each lane keeps its
+// hits' bins, packed four to a register, from the counting pass to the
+// scatter pass.
 template <int SH, class Src>
 __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned char* slots, uint32_t* wc, Src src) {
   using C = RS<SH>;
@@ -195,9 +217,19 @@ __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned c
   for (int u = 0; u < BPL; ++u) wc[BPL * lane + u] = 0;
   if (lane < (int)(2 * C::BMB / 4)) ub[lane] = 0;
   __syncwarp();
-  for (uint32_t j = lane; j < n; j += 32) {
-    const float2 v = src(j);
-    atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
+  constexpr int MPL = (int)((C::MOD + 31) / 32);  // hits per lane
+  uint32_t hb[(MPL + 3) / 4];
+#pragma unroll
+  for (int u = 0; u < (MPL + 3) / 4; ++u) hb[u] = 0;
+#pragma unroll
+  for (int u = 0; u < MPL; ++u) {
+    const uint32_t j = (uint32_t)lane + 32u * u;
+    if (j < n) {
+      const float2 v = src(j);
+      const uint32_t b = (uint32_t)phi_bin(pseudo_angle(v.x, v.y));
+      hb[u / 4] |= b << (8 * (u % 4));
+      atomicAdd(&wc[b], 1u);
+    }
   }
   __syncwarp();
   uint32_t cnt[BPL], sum = 0;
@@ -215,11 +247,15 @@ __device__ __forceinline__ void bin_module(int m, const uint16_t* cb, unsigned c
     bins[BPL * lane + u] = (typename C::BinT)cur;
   }
   __syncwarp();
-  for (uint32_t j = lane; j < n; j += 32) {
-    const float2 v = src(j);
-    const uint32_t p = atomicAdd(&wc[phi_bin(pseudo_angle(v.x, v.y))], 1u);
-    pos[p] = v;
-    pid[p] = (uint16_t)(c0 + j);
+#pragma unroll
+  for (int u = 0; u < MPL; ++u) {
+    const uint32_t j = (uint32_t)lane + 32u * u;
+    if (j < n) {
+      const float2 v = src(j);
+      const uint32_t p = atomicAdd(&wc[(hb[u / 4] >> (8 * (u % 4))) & 0xFFu], 1u);
+      pos[p] = v;
+      pid[p] = (uint16_t)(c0 + j);
+    }
   }
   __syncwarp();
 }
@@ -317,8 +353,9 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     const int m = nm - 1 - k;
     if (m < 0) break;
     const uint32_t c0 = s_cb[kSPM * m];
+    const ModuleSrc src = module_src(s_cb, so, m);
     bin_module<SH>(m, s_cb, slots, k == 0 ? s_wbin : (uint32_t*)(smem + L.act) + kNB * (k - 1),
-                   [&](uint32_t j) { return wk.prov[module_src(s_cb, so, m, c0 + j)]; });
+                   [&](uint32_t j) { return wk.prov[src.at(c0 + j)]; });
   }
   cp_async_wait_all();
   __syncthreads();
