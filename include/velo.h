@@ -309,8 +309,8 @@ typedef struct velo_stats {
  * to one block; the schedule only decides how blocks share the GPU).  Events
  * run in the first class that holds their hits.  class_mask selects the
  * classes:
- *   bit 7: the narrow module-window class (64 threads, thirteen CTAs per SM,
- *          up to 8192 hits and modules of up to 160 hits; events that
+ *   bit 7: the narrow module-window class (64 threads, fourteen CTAs per SM,
+ *          up to 8192 hits and modules of up to 144 hits; events that
  *          outgrow it go to a pass of the wide class when bit 6 is set);
  *   bit 6: the module-window class (128 threads, nine CTAs per SM, up to
  *          8192 hits and modules of up to 256 hits; it keeps only the three

@@ -246,7 +246,7 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
 // from this list (at most kMaxClasses; one CTA per SM is always included).
 constexpr int kPerSm[6] = {8, 6, 4, 3, 2, 1};
 // class_mask bits of the module-window classes: bit 6 the wide shape (128
-// threads, nine CTAs per SM), bit 7 the narrow one (64 threads, thirteen).
+// threads, nine CTAs per SM), bit 7 the narrow one (64 threads, fourteen).
 constexpr uint32_t kRingClassBit = 1u << 6;
 constexpr uint32_t kRingNarrowBit = 1u << 7;
 

@@ -29,9 +29,10 @@ constexpr int kMlpNormOffset = (2 * kMlpParams + 15) & ~15;  // byte offset of t
 // global region; an event beyond any of them goes on to a larger plan.
 //   wide   (variant 0): 128 threads, nine CTAs per SM (register budget:
 //           65536 / (128 * 9) -> 56 per thread);
-//   narrow (variant 1): 64 threads and a smaller window (modules of up to 160
-//           hits, 136 active tracks, 384 candidates), thirteen CTAs per SM
-//           (shared memory: 13 x 17.9 KB of the SM's 228 KB).
+//   narrow (variant 1): 64 threads and a smaller window (modules of up to 144
+//           hits, 120 active tracks, 384 candidates), fourteen CTAs per SM
+//           (shared memory: 14 x 16.1 KB of the SM's 228 KB; registers:
+//           65536 / (64 * 14) -> 72 per thread).
 // A round of the search offers about 30 active tracks and 30 middle hits
 // (nominal events), which two warps cover; the narrow shape trades the idle
 // warps of the wide one for more events in flight.
@@ -39,7 +40,7 @@ struct RingShape {
   int threads, ctas_per_sm;
   uint32_t mod_hits, max_h, max_act, max_t;
 };
-constexpr RingShape kRingShapes[2] = {{128, 9, 256, 8192, 160, 512}, {64, 13, 160, 8192, 136, 384}};
+constexpr RingShape kRingShapes[2] = {{128, 9, 256, 8192, 160, 512}, {64, 14, 144, 8192, 120, 384}};
 constexpr int kRingWide = 0, kRingNarrow = 1;
 constexpr uint32_t kRingMaxH = 8192;      // hits of one event, both shapes
 constexpr uint32_t kRingTrackHits = kMaxModules;  // hits of one candidate: one per module at most

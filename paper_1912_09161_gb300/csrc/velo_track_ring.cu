@@ -1,6 +1,6 @@
 // Tracking kernel with a rolling module window: hits -> track candidates, one
 // event per CTA, in two shapes (RingShape): 128 threads and nine CTAs per SM
-// (wide), or 64 threads, a smaller window and thirteen CTAs per SM (narrow).
+// (wide), or 64 threads, a smaller window and fourteen CTAs per SM (narrow).
 //
 // The search by triplet (paper section 2.3.1) only ever looks at three
 // consecutive modules: round i extends the active tracks into module i
@@ -11,7 +11,7 @@
 // active tracks (double-buffered records), the list of the round's unused
 // middle hits and the next module's raw hits -- about 23 KB per event in the
 // wide shape (nine events share an SM; the register budget sets the nine),
-// 17 KB in the narrow one (thirteen).  The hits come straight from the
+// 15 KB in the narrow one (fourteen).  The hits come straight from the
 // clustering output:
 //   - round i copies module i - 2's hits into a staging buffer with cp.async
 //     during its phase B;
@@ -767,17 +767,19 @@ __global__ void __launch_bounds__(RS<SH>::NT, RS<SH>::CPS) track_ring_kernel(con
   }
 }
 
-// Lanes per active track in phase A and per middle hit in phase B.
-constexpr int kRingGroupA = 1;
+// Lanes per active track in phase A (two in the narrow shape, whose 64
+// threads meet about 30 active tracks a round) and per middle hit in phase B.
+template <int SH>
+constexpr int kRingGroupA = SH == kRingNarrow ? 2 : 1;
 constexpr int kRingGroupB = 2;
 
 template <int SH>
 cudaError_t set_limit() {
   const int bytes = (int)RS<SH>::layout().total;
-  cudaError_t e = cudaFuncSetAttribute(track_ring_kernel<SH, kRingGroupA, kRingGroupB, false>,
+  cudaError_t e = cudaFuncSetAttribute(track_ring_kernel<SH, kRingGroupA<SH>, kRingGroupB, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(track_ring_kernel<SH, kRingGroupA, kRingGroupB, true>,
+  return cudaFuncSetAttribute(track_ring_kernel<SH, kRingGroupA<SH>, kRingGroupB, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
@@ -787,9 +789,9 @@ cudaError_t occupancy(int* blocks_per_sm) {
   const size_t bytes = RS<SH>::layout().total;
   int a = 0, b = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &a, track_ring_kernel<SH, kRingGroupA, kRingGroupB, false>, RS<SH>::NT, bytes);
+      &a, track_ring_kernel<SH, kRingGroupA<SH>, kRingGroupB, false>, RS<SH>::NT, bytes);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, track_ring_kernel<SH, kRingGroupA, kRingGroupB, true>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, track_ring_kernel<SH, kRingGroupA<SH>, kRingGroupB, true>,
                                                       RS<SH>::NT, bytes);
   *blocks_per_sm = a < b ? a : b;
   return e;
@@ -800,9 +802,9 @@ cudaError_t launch(const DevGeometry* geo, const DevParams& par, const EventsVie
                    int queue, int n_ctas, cudaStream_t st) {
   const size_t bytes = RS<SH>::layout().total;
   if (par.use_mlp && wk.mlp_w != nullptr)
-    track_ring_kernel<SH, kRingGroupA, kRingGroupB, true><<<n_ctas, RS<SH>::NT, bytes, st>>>(geo, par, ev, wk, cls, queue);
+    track_ring_kernel<SH, kRingGroupA<SH>, kRingGroupB, true><<<n_ctas, RS<SH>::NT, bytes, st>>>(geo, par, ev, wk, cls, queue);
   else
-    track_ring_kernel<SH, kRingGroupA, kRingGroupB, false><<<n_ctas, RS<SH>::NT, bytes, st>>>(geo, par, ev, wk, cls, queue);
+    track_ring_kernel<SH, kRingGroupA<SH>, kRingGroupB, false><<<n_ctas, RS<SH>::NT, bytes, st>>>(geo, par, ev, wk, cls, queue);
   return cudaGetLastError();
 }
 
