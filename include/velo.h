@@ -281,11 +281,16 @@ int velo_sync_status(velo_handle *h, void *stream);
 
 /*
  * End-to-end call with HOST buffers (paper section 2.2: raw data copied to the
- * GPU, only results copied back): copies the events from host memory (pinned
- * for asynchronous copies) into a staging buffer of the handle (allocated on
- * first use), reconstructs, and copies the outputs back into host buffers of
- * the same layout as velo_output.  Synchronous.  VELO_ERR_CAPACITY when the
- * caller's host buffers are too small (totals hold the needed sizes).
+ * GPU, only results copied back), outputs in host buffers of the same layout
+ * as velo_output.  Synchronous.  The sensor offsets are copied into a staging
+ * buffer of the handle (allocated on first use).  Pixel arrays in pinned,
+ * mapped host memory (cudaMallocHost, cudaHostAlloc, cudaHostRegister) are
+ * read in place by the clustering kernel over the host link (it reads each
+ * pixel once); pageable ones are copied to staging first.  The outputs go to
+ * staging and are copied back at their exact sizes (written in place by the
+ * kernels they were slower: their stores to host memory are scattered).
+ * VELO_ERR_CAPACITY when the caller's host buffers are too small (totals and
+ * event status hold the needed sizes; nothing else is written).
  */
 int velo_reconstruct_host(velo_handle *h, uint32_t n_events, const uint32_t *sensor_off_host,
                           const uint16_t *col_host, const uint16_t *row_host,
@@ -564,7 +569,8 @@ int velo_server_set_mlp(velo_server *s, const uint16_t *params_bf16, const float
 
 /*
  * Queues a request.  HOST pointers, owned by the caller, read until the
- * request is finished (pinned memory lets the copies overlap).  Pixels of
+ * request is finished (pinned memory lets the copies overlap; pinned pixel
+ * arrays are read in place by the clustering kernel).  Pixels of
  * event e, sensor s are [sensor_off[e*n_sensors+s], sensor_off[e*n_sensors+s+1])
  * of col/row; sensor_off[0] may be non-zero (a request cut from a larger
  * array).  VELO_ERR_NOMEM if the request exceeds max_events / max_pixels or

@@ -39,6 +39,23 @@ namespace velo {
 void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg); }
 }  // namespace velo
 
+namespace velo {
+
+// Device address of a host buffer the device can reach directly (pinned,
+// mapped memory: cudaMallocHost, cudaHostAlloc, cudaHostRegister), else null
+// (pageable memory, or a device pointer).
+void* host_mapped(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace velo
+
 struct velo_handle {
   int device = 0;
   int n_sm = 0;
@@ -992,12 +1009,24 @@ int velo_reconstruct_host(velo_handle* h, uint32_t n_events, const uint32_t* sen
   }
   char* b = (char*)h->stage;
   cudaStream_t st = (cudaStream_t)stream;
+  // the sensor offsets (read by every kernel) are copied; pinned pixel
+  // arrays are read in place by the clustering kernel, which reads each
+  // pixel once, over the host link; pageable ones are copied
   CUDA_TRY(cudaMemcpyAsync(b + s_off, sensor_off_host, 4 * n_off, cudaMemcpyHostToDevice, st));
+  const uint16_t* d_col = (const uint16_t*)(b + s_col);
+  const uint16_t* d_row = (const uint16_t*)(b + s_row);
   if (P) {
-    CUDA_TRY(cudaMemcpyAsync(b + s_col, col_host, 2 * P, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(b + s_row, row_host, 2 * P, cudaMemcpyHostToDevice, st));
+    const void* mc = host_mapped(col_host);
+    const void* mr = host_mapped(row_host);
+    if (mc && mr) {
+      d_col = (const uint16_t*)mc;
+      d_row = (const uint16_t*)mr;
+    } else {
+      CUDA_TRY(cudaMemcpyAsync(b + s_col, col_host, 2 * P, cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaMemcpyAsync(b + s_row, row_host, 2 * P, cudaMemcpyHostToDevice, st));
+    }
   }
-  velo_events ev{n_events, (const uint32_t*)(b + s_off), (const uint16_t*)(b + s_col), (const uint16_t*)(b + s_row)};
+  velo_events ev{n_events, (const uint32_t*)(b + s_off), d_col, d_row};
   velo_output od{};
   od.cap_tracks = (uint32_t)c.max_tracks;
   od.cap_hits = (uint32_t)c.max_track_hits;

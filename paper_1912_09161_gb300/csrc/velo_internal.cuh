@@ -241,5 +241,8 @@ velo_config work_config(uint32_t n_events, uint64_t n_pixels);
 size_t work_bytes(uint32_t n_events, uint64_t n_pixels);
 void bind_work(velo_handle* h, void* base, uint32_t n_events, uint64_t n_pixels);
 void set_last_error(const char* msg);
+// Device address of pinned, mapped host memory (cudaMallocHost, cudaHostAlloc,
+// cudaHostRegister), else null.
+void* host_mapped(const void* p);
 
 }  // namespace velo

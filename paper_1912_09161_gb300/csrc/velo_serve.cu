@@ -184,9 +184,20 @@ int start(velo_server* s, Slot& sl, const Request& r, uint64_t pool_off) {
     rebase_offsets_kernel<<<(unsigned)((n_off + 255) / 256), 256, 0, st>>>(d_off, n_off, r.p0);
     SRV_TRY(cudaGetLastError());
   }
+  // pinned pixel arrays are read in place by the clustering kernel (each
+  // pixel once, over the host link); pageable ones are copied into the range
+  const uint16_t* d_col = (const uint16_t*)(b + L.col);
+  const uint16_t* d_row = (const uint16_t*)(b + L.row);
   if (r.n_pixels) {
-    SRV_TRY(cudaMemcpyAsync(b + L.col, r.col + r.p0, 2 * r.n_pixels, cudaMemcpyHostToDevice, st));
-    SRV_TRY(cudaMemcpyAsync(b + L.row, r.row + r.p0, 2 * r.n_pixels, cudaMemcpyHostToDevice, st));
+    const uint16_t* mc = (const uint16_t*)host_mapped(r.col);
+    const uint16_t* mr = (const uint16_t*)host_mapped(r.row);
+    if (mc && mr) {
+      d_col = mc + r.p0;
+      d_row = mr + r.p0;
+    } else {
+      SRV_TRY(cudaMemcpyAsync(b + L.col, r.col + r.p0, 2 * r.n_pixels, cudaMemcpyHostToDevice, st));
+      SRV_TRY(cudaMemcpyAsync(b + L.row, r.row + r.p0, 2 * r.n_pixels, cudaMemcpyHostToDevice, st));
+    }
   }
   velo_output& d = sl.dout;
   d = velo_output{};
@@ -200,7 +211,7 @@ int start(velo_server* s, Slot& sl, const Request& r, uint64_t pool_off) {
   d.event_status = (uint32_t*)(b + L.evs);
   d.totals = (uint32_t*)(b + L.tot);
   bind_work(sl.h, b + L.work, r.n_events, r.n_pixels);
-  velo_events ev{r.n_events, d_off, (const uint16_t*)(b + L.col), (const uint16_t*)(b + L.row)};
+  velo_events ev{r.n_events, d_off, d_col, d_row};
   const int rc = velo_reconstruct(sl.h, &ev, &d, st);
   if (rc != VELO_OK) return rc;
   SRV_TRY(cudaMemcpyAsync(sl.h_tot, d.totals, 16, cudaMemcpyDeviceToHost, st));

@@ -211,6 +211,43 @@ def test_reconstruct_host_matches_oracle(V, geom, cfg0_events, cfg0_oracle):
     assert_parity(host.to_host(ev.n_events), cfg0_oracle)
 
 
+def test_reconstruct_host_pinned_in_place(V, geom, cfg0_events, cfg0_oracle):
+    """With pinned host buffers the host-buffer entry point reads the pixels in
+    place (no staging copy of them): the same clusters, tracks and states as
+    the oracle; host outputs too small for the batch give VELO_ERR_CAPACITY
+    with the needed totals and the event status."""
+    import torch
+    ev = cfg0_events
+    so = torch.from_numpy(np.ascontiguousarray(ev.sensor_off, np.uint32).view(np.int32)).pin_memory()
+    col = torch.from_numpy(np.ascontiguousarray(ev.col, np.uint16).view(np.int16)).pin_memory()
+    row = torch.from_numpy(np.ascontiguousarray(ev.row, np.uint16).view(np.int16)).pin_memory()
+    rec = V.Reconstructor(geom, V.Params(), max_events=ev.n_events, max_pixels=ev.n_pixels, clusters=True)
+    try:
+        ct, ch, cc = V.suggested_caps(ev.n_events, ev.n_pixels)
+        host = V.alloc_output(ev.n_events, ct, ch, cc, device="cpu")
+        for name in ("track_off", "hit_off", "hit_ids", "states", "ndof", "event_status", "totals", "cluster_off",
+                     "cl_x", "cl_y", "cl_key"):
+            setattr(host, name, getattr(host, name).pin_memory())
+        rc = V.velo.velo_reconstruct_host(rec.handle, ev.n_events, so.numpy().view(np.uint32),
+                                          col.numpy().view(np.uint16), row.numpy().view(np.uint16), host.to_c())
+        assert rc == V.velo.VELO_OK
+        assert_parity(host.to_host(ev.n_events), cfg0_oracle)
+        o = cfg0_oracle
+        t3 = int(o.track_off[3])  # the first three events fit
+        small = V.alloc_output(ev.n_events, t3, int(o.hit_off[t3]), cc, device="cpu")
+        for name in ("track_off", "hit_off", "hit_ids", "states", "ndof", "event_status", "totals", "cluster_off",
+                     "cl_x", "cl_y", "cl_key"):
+            setattr(small, name, getattr(small, name).pin_memory())
+        rc = V.velo.velo_reconstruct_host(rec.handle, ev.n_events, so.numpy().view(np.uint32),
+                                          col.numpy().view(np.uint16), row.numpy().view(np.uint16), small.to_c())
+    finally:
+        rec.close()
+    assert rc == V.velo.VELO_ERR_CAPACITY
+    res = small.to_host(ev.n_events)
+    assert int(res.totals[0]) == cfg0_oracle.n_tracks
+    assert int(res.totals[1]) == int(o.hit_off[-1])
+
+
 @pytest.mark.parametrize("schedule", [None, (256, 0x10, 1)])
 def test_exact_ties(V, schedule):
     """Exact ties of the scatter in seeding and in forwarding (exact-float
