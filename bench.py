@@ -188,10 +188,11 @@ def _measured_peak_hbm() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def _profile_traffic(kernel_srcs: list[str]) -> float | None:
+def _profile_traffic(kernel_srcs: list[str], class_mask: int | None = None) -> float | None:
     """DRAM bytes per call of the tracking kernels from the committed ncu
     summary, if it was taken on the current kernel sources (the sha256 prefix
-    of their concatenation is recorded in the summary)."""
+    of their concatenation is recorded in the summary) and, when the summary
+    names one, under the schedule's class mask."""
     try:
         text = open(PROFILE_SUMMARY).read()
         h = hashlib.sha256()
@@ -202,7 +203,10 @@ def _profile_traffic(kernel_srcs: list[str]) -> float | None:
         return None
     m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_cm = re.search(r"schedule_class_mask:\s*([0-9]+)", text)
     if not m_sha or not m_tr or m_sha.group(1) != sha:
+        return None
+    if m_cm and class_mask is not None and int(m_cm.group(1)) != class_mask:
         return None
     return float(m_tr.group(1))
 
@@ -623,7 +627,8 @@ def run_ours(args):
     desc = rec.describe()
     peak, peak_kind = _measured_peak_hbm()
     achieved = sum(reco_bytes) / (sum(reco_ms) / 1e3) / 1e9
-    traffic = _profile_traffic([os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", f) for f in TRACK_SOURCES])
+    traffic = _profile_traffic([os.path.join(ROOT, "paper_1912_09161_gb300", "csrc", f) for f in TRACK_SOURCES],
+                               int(desc["schedule"]["class_mask"]))
     tot = out.totals.cpu().numpy().view(np.uint32)
     step_bytes = _step_bytes(ev.n_pixels, ev.n_events, geom.n_sensors, int(tot[0]), int(tot[1]))
     stage = [statistics.mean(x[k] for x in stage_ms) for k in range(4)]
