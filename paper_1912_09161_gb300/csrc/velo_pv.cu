@@ -11,9 +11,11 @@
 //      unless a peak within min_sep bins has a larger count (or an equal one
 //      and a smaller bin); up to kPvMax seeds in increasing z;
 //   3. n_iter fit rounds: the threads split the tracks, and for each track sum
-//      its Tukey compatibility with every vertex in vertex order; then thread
-//      v accumulates vertex v's weighted normal equations over the tracks in
-//      track order and moves the vertex by its least-squares step;
+//      its Tukey compatibility with every vertex in vertex order; then, for
+//      chunks of 64 tracks and groups of 8 vertices, every thread computes
+//      one track's terms of the weighted normal equations for each vertex of
+//      the group (shared memory), and thread v adds vertex v's terms in track
+//      order; thread v then moves the vertex by its least-squares step;
 //   4. vertices with enough weight and a positive-definite normal matrix are
 //      kept unless a stronger kept vertex lies within merge_dz; they go to the
 //      event's slot, and a scan kernel compacts the slots into the caller's
@@ -33,6 +35,9 @@ constexpr int kPvThreads = 64;
 constexpr int kPvMax = 64;        // seeds per event (one thread each)
 constexpr int kPvMaxBins = 2560;  // histogram bins
 constexpr int kPvNOut = VELO_PV_NOUT;
+constexpr int kPvGroup = 8;       // vertices whose terms are staged at a time
+constexpr int kPvTerms = 9;       // terms of a (track, vertex) pair
+static_assert(kPvGroup * kPvThreads * kPvTerms <= 2 * kPvMaxBins, "terms fit the histogram arrays");
 
 struct PvTrack {
   float x, y, z, tx, ty, c00, c20, c22, c11, c31, c33;
@@ -97,8 +102,11 @@ struct PvWork {
 __global__ void __launch_bounds__(kPvThreads) pv_kernel(uint32_t n_events, velo_pv_params p, const uint32_t* track_off,
                                                         const float* __restrict__ states, uint32_t cap_tracks,
                                                         PvWork wk, uint32_t* status) {
-  __shared__ uint32_t s_hist[kPvMaxBins];  // histogram, then peak flags
-  __shared__ uint32_t s_win[kPvMaxBins];
+  // histogram (then peak flags) and window counts, one array, which the fit
+  // rounds reuse for the staged terms
+  __shared__ uint32_t s_buf[2 * kPvMaxBins];
+  uint32_t* s_hist = s_buf;
+  uint32_t* s_win = s_buf + kPvMaxBins;
   __shared__ float s_vx[kPvMax], s_vy[kPvMax], s_vz[kPvMax], s_sw[kPvMax];
   __shared__ int s_keep[kPvMax];
   __shared__ uint32_t s_seed[kPvMax];
@@ -174,6 +182,7 @@ __global__ void __launch_bounds__(kPvThreads) pv_kernel(uint32_t n_events, velo_
     }
     __syncthreads();
     // 3. fit rounds
+    float* s_terms = (float*)s_buf;  // [kPvGroup][kPvThreads][kPvTerms], over both histogram arrays
     float sxx = 0.0f, syy = 0.0f, sxt = 0.0f, syt = 0.0f, stt = 0.0f, bx = 0.0f, by = 0.0f, bt = 0.0f, sw = 0.0f;
     for (uint32_t it = 0; it < p.n_iter && V > 0; ++it) {
       for (uint32_t i = tid; i < T; i += kPvThreads) {
@@ -183,31 +192,68 @@ __global__ void __launch_bounds__(kPvThreads) pv_kernel(uint32_t n_events, velo_
         for (uint32_t v = 0; v < V; ++v) s = fadd(s, tukey(k, s_vx[v], s_vy[v], s_vz[v], p.chi2_cut));
         wk.tsum[t0 + i] = s;
       }
+      sxx = syy = sxt = syt = stt = bx = by = bt = sw = 0.0f;
       __syncthreads();
-      if (tid < V) {
-        const float x = s_vx[tid], y = s_vy[tid], z = s_vz[tid];
-        sxx = syy = sxt = syt = stt = bx = by = bt = sw = 0.0f;
-        for (uint32_t i = 0; i < T; ++i) {
-          const PvTrack k = pv_track(states, cap, t0 + i);
-          if (!near_axis(k, p.max_r2)) continue;
-          const float t = tukey(k, x, y, z, p.chi2_cut);
-          if (!(t > 0.0f)) continue;
-          const float w = fdiv(fmul(t, t), wk.tsum[t0 + i]);
-          const float dz = fsub(z, k.z);
-          const float rx = fsub(fadd(k.x, fmul(k.tx, dz)), x);
-          const float ry = fsub(fadd(k.y, fmul(k.ty, dz)), y);
-          const float wx = fdiv(w, pos_var(k.c00, k.c20, k.c22, dz));
-          const float wy = fdiv(w, pos_var(k.c11, k.c31, k.c33, dz));
-          const float a = fmul(wx, k.tx), c = fmul(wy, k.ty);
-          sxx = fadd(sxx, wx);
-          syy = fadd(syy, wy);
-          sxt = fadd(sxt, a);
-          syt = fadd(syt, c);
-          stt = fadd(stt, fadd(fmul(a, k.tx), fmul(c, k.ty)));
-          bx = fadd(bx, fmul(wx, rx));
-          by = fadd(by, fmul(wy, ry));
-          bt = fadd(bt, fadd(fmul(a, rx), fmul(c, ry)));
-          sw = fadd(sw, w);
+      for (uint32_t c0 = 0; c0 < T; c0 += kPvThreads) {
+        // this thread's track of the chunk
+        const uint32_t i = c0 + tid;
+        bool have = i < T;
+        PvTrack k{};
+        float ts = 0.0f;
+        if (have) {
+          k = pv_track(states, cap, t0 + i);
+          have = near_axis(k, p.max_r2);
+          if (have) ts = wk.tsum[t0 + i];
+        }
+        const uint32_t nc = min((uint32_t)kPvThreads, T - c0);
+        for (uint32_t g0 = 0; g0 < V; g0 += kPvGroup) {
+          // terms of (this track, vertex g0 + j); wx < 0 marks a pair that
+          // does not contribute
+#pragma unroll 1
+          for (uint32_t j = 0; j < (uint32_t)kPvGroup; ++j) {
+            float* tm = s_terms + ((size_t)j * kPvThreads + tid) * kPvTerms;
+            const uint32_t v = g0 + j;
+            tm[0] = -1.0f;
+            if (v >= V || !have) continue;
+            const float x = s_vx[v], y = s_vy[v], z = s_vz[v];
+            const float t = tukey(k, x, y, z, p.chi2_cut);
+            if (!(t > 0.0f)) continue;
+            const float w = fdiv(fmul(t, t), ts);
+            const float dz = fsub(z, k.z);
+            const float rx = fsub(fadd(k.x, fmul(k.tx, dz)), x);
+            const float ry = fsub(fadd(k.y, fmul(k.ty, dz)), y);
+            const float wx = fdiv(w, pos_var(k.c00, k.c20, k.c22, dz));
+            const float wy = fdiv(w, pos_var(k.c11, k.c31, k.c33, dz));
+            const float a = fmul(wx, k.tx), c = fmul(wy, k.ty);
+            tm[0] = wx;
+            tm[1] = wy;
+            tm[2] = a;
+            tm[3] = c;
+            tm[4] = fadd(fmul(a, k.tx), fmul(c, k.ty));
+            tm[5] = fmul(wx, rx);
+            tm[6] = fmul(wy, ry);
+            tm[7] = fadd(fmul(a, rx), fmul(c, ry));
+            tm[8] = w;
+          }
+          __syncthreads();
+          // vertex tid adds its terms over the chunk's tracks in track order
+          if (tid >= g0 && tid < V && tid < g0 + (uint32_t)kPvGroup) {
+            const float* col = s_terms + (size_t)(tid - g0) * kPvThreads * kPvTerms;
+            for (uint32_t ii = 0; ii < nc; ++ii) {
+              const float* tm = col + (size_t)ii * kPvTerms;
+              if (!(tm[0] >= 0.0f)) continue;
+              sxx = fadd(sxx, tm[0]);
+              syy = fadd(syy, tm[1]);
+              sxt = fadd(sxt, tm[2]);
+              syt = fadd(syt, tm[3]);
+              stt = fadd(stt, tm[4]);
+              bx = fadd(bx, tm[5]);
+              by = fadd(by, tm[6]);
+              bt = fadd(bt, tm[7]);
+              sw = fadd(sw, tm[8]);
+            }
+          }
+          __syncthreads();
         }
       }
       __syncthreads();  // every thread has read the positions of this round
