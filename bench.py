@@ -192,7 +192,7 @@ def _profile_traffic(kernel_srcs: list[str], class_mask: int | None = None) -> f
     """DRAM bytes per call of the tracking kernels from the committed ncu
     summary, if it was taken on the current kernel sources (the sha256 prefix
     of their concatenation is recorded in the summary) and, when the summary
-    names one, under the schedule's class mask."""
+    names them, under one of the schedules' class masks it was measured for."""
     try:
         text = open(PROFILE_SUMMARY).read()
         h = hashlib.sha256()
@@ -203,10 +203,10 @@ def _profile_traffic(kernel_srcs: list[str], class_mask: int | None = None) -> f
         return None
     m_sha = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    m_cm = re.search(r"schedule_class_mask:\s*([0-9]+)", text)
+    m_cm = re.search(r"schedule_class_mask:\s*([0-9 ]+)", text)
     if not m_sha or not m_tr or m_sha.group(1) != sha:
         return None
-    if m_cm and class_mask is not None and int(m_cm.group(1)) != class_mask:
+    if m_cm and class_mask is not None and class_mask not in [int(x) for x in m_cm.group(1).split()]:
         return None
     return float(m_tr.group(1))
 

@@ -202,11 +202,13 @@ class Server:
 
 
 def latency_summary(lat: np.ndarray, events: int, wall_s: float) -> dict:
+    """Request count, events/s and latency percentiles (None without requests:
+    a trace too short for any arrival)."""
+    lat = np.asarray(lat, np.float64)
+    pct = (lambda q: round(float(np.percentile(lat, q)) * 1e3, 3)) if len(lat) else (lambda q: None)
     return dict(requests=int(len(lat)), events=int(events), wall_s=round(wall_s, 3),
                 events_per_s=round(events / wall_s, 1) if wall_s > 0 else None,
-                p50_ms=round(float(np.percentile(lat, 50)) * 1e3, 3),
-                p99_ms=round(float(np.percentile(lat, 99)) * 1e3, 3),
-                max_ms=round(float(lat.max()) * 1e3, 3))
+                p50_ms=pct(50), p99_ms=pct(99), max_ms=round(float(lat.max()) * 1e3, 3) if len(lat) else None)
 
 
 __all__ = ["EventPool", "Server", "Trace", "VeloError", "burst_trace", "latency_summary", "poisson_trace"]

@@ -61,9 +61,10 @@ def test_profile_traffic_needs_the_profiled_sources(tmp_path, monkeypatch):
     assert bench._profile_traffic(srcs[:2]) is None
     # a summary that names its schedule reports only for that schedule
     summary.write_text(f"kernel_source_sha256: {h.hexdigest()[:16]}\ntraffic_bytes_per_launch: 4.5e8\n"
-                       "schedule_class_mask: 224\n")
+                       "schedule_class_mask: 160 224\n")
     assert bench._profile_traffic(srcs, 224) == 4.5e8
-    assert bench._profile_traffic(srcs, 160) is None
+    assert bench._profile_traffic(srcs, 160) == 4.5e8
+    assert bench._profile_traffic(srcs, 96) is None
 
 
 def test_aggregate_rate_over_ranks():
