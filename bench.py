@@ -481,6 +481,7 @@ def classifier_leg(V, geom, ev, d, dev, stream, flush, steps: int, warmup: int, 
         rec.set_mlp(stt.params_bf16, stt.mean, stt.istd)
         ct, ch, _ = V.suggested_caps(E, ev.n_pixels)
         out = V.alloc_output(E, ct, ch, 0, device=dev)
+        tuned, _ = rec.autotune(d, out, sptr)  # untimed: the classifier path's own schedule
         rec.set_graphs(True)
         rec.set_timing(True)
         ms, st = timed_calls(rec, d, out, sptr, stream, flush, steps, warmup)
@@ -497,7 +498,7 @@ def classifier_leg(V, geom, ev, d, dev, stream, flush, steps: int, warmup: int, 
         s = MET.summarize(ev, orc.cluster_off, orc.pix_cluster, r.track_off, r.hit_off, r.hit_ids)
         q[name] = {k: s[k] for k in ("efficiency", "ghost_rate", "clone_rate", "n_tracks")}
     return {"training": {"candidates": int(len(y)), "epochs": 20, "seconds": round(train_s, 2)},
-            "logit_threshold": thr, "value": E / (statistics.mean(ms) / 1e3), "unit": UNIT,
+            "logit_threshold": thr, "schedule": tuned, "value": E / (statistics.mean(ms) / 1e3), "unit": UNIT,
             "ms_per_step": statistics.mean(ms), "stage_ms": _stage(st), "quality": q,
             "efficiency_change": q["classifier"]["efficiency"] - q["plain"]["efficiency"],
             "ghost_rate_change": q["classifier"]["ghost_rate"] - q["plain"]["ghost_rate"]}
