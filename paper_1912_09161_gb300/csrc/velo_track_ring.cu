@@ -13,10 +13,10 @@
 // wide shape (nine events share an SM; the register budget sets the nine),
 // 15 KB in the narrow one (fourteen).  The hits come straight from the
 // clustering output:
-//   - round i copies module i - 2's hits into a staging buffer with cp.async
-//     during its phase B;
-//   - round i - 1 bins them by phi into the free slot during its phase A, on
-//     a warp that phase A leaves idle;
+//   - during phase A of round i, one warp bins module i - 1 (staged a round
+//     earlier) by phi into the free slot, then issues the cp.async copies of
+//     module i - 2's hits into the staging buffer (waited for at the round's
+//     end);
 // so every hit is read from global memory once.  After the rounds the kernel
 // applies the plain cuts (or the classifier), ranks the kept candidates
 // canonically and writes their hits (module, canonical id) and the hits'
