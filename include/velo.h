@@ -302,8 +302,8 @@ int velo_reconstruct_host(velo_handle *h, uint32_t n_events, const uint32_t *sen
 typedef struct velo_stats {
   uint32_t n_classes;
   uint32_t events[4];   /* events reconstructed by each class */
-  uint32_t tracks[4];   /* tracks written by each class */
-  uint32_t hits[4];     /* track hits written by each class */
+  uint32_t tracks[4];   /* tracks written by each class (with the classifier: candidates scored) */
+  uint32_t hits[4];     /* track hits written by each class (likewise) */
   uint32_t clusters[4]; /* hits (clusters) read by each class */
   uint64_t pixels[4];   /* raw pixels of those events */
   float ms[5];          /* device time: clustering, tracking (all classes), scan, emit, whole call */

@@ -203,7 +203,7 @@ FixedPlan plan_fixed() {
 }
 
 struct WorkPlan {
-  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, tev, hits, hpos, clx, cly, clk, total;
+  size_t rec, q[kQueues], prov, pkey, cbase, lg, nh, ho, tev, ork, ohf, hits, hpos, clx, cly, clk, total;
 };
 
 WorkPlan plan_work(const velo_config& c) {
@@ -218,6 +218,8 @@ WorkPlan plan_work(const velo_config& c) {
   a.nh = o; o = align256(o + 2ull * c.max_tracks);
   a.ho = o; o = align256(o + 4ull * c.max_tracks);
   a.tev = o; o = align256(o + 4ull * c.max_tracks);
+  a.ork = o; o = align256(o + 4ull * c.max_tracks);
+  a.ohf = o; o = align256(o + 4ull * c.max_tracks);
   a.hits = o; o = align256(o + 4ull * c.max_track_hits);
   a.hpos = o; o = align256(o + 8ull * c.max_track_hits);
   if (c.flags & VELO_CFG_CLUSTERS) {
@@ -243,6 +245,8 @@ void carve_work(velo_handle* h, char* base, const velo_config& c) {
   w.tr_nhits = (uint16_t*)(base + a.nh);
   w.tr_hitoff = (uint32_t*)(base + a.ho);
   w.tr_event = (uint32_t*)(base + a.tev);
+  w.tr_orank = (uint32_t*)(base + a.ork);
+  w.tr_ohoff = (uint32_t*)(base + a.ohf);
   w.tr_hits = (uint32_t*)(base + a.hits);
   w.tr_pos = (float2*)(base + a.hpos);
   w.cap_tracks = (uint32_t)c.max_tracks;
@@ -465,6 +469,8 @@ int enqueue(velo_handle* h, const EventsView& ev, const WorkView& wk, const velo
     // events beyond every shared-memory class: global-memory pass
     CUDA_TRY(launch_track_huge(h->d_geo, h->par, ev, wk, big, st));
   }
+  // classifier: score every candidate, keep those at or above the threshold
+  if (E && h->par.use_mlp && wk.mlp_w) CUDA_TRY(launch_classify(E, h->d_geo, h->par, wk, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[2], st, mark));
   CUDA_TRY(launch_scan(E, wk, out, st));
   if (tm) CUDA_TRY(cudaEventRecordWithFlags(h->ev[3], st, mark));

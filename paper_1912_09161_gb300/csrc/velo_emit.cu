@@ -9,6 +9,7 @@
 
 #include "velo_fit.cuh"
 #include "velo_internal.cuh"
+#include "velo_mlp.cuh"
 
 namespace velo {
 
@@ -143,9 +144,15 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
     const EventRec r = wk.rec[e];
     const uint32_t o0 = out.track_off[e];
     if (!event_fits(r, o0, out)) continue;
-    const uint32_t k = t - r.track_base;
+    uint32_t k = t - r.track_base;
     const uint32_t nh = __ldg(&wk.tr_nhits[t]);
     const uint32_t hoff = __ldg(&wk.tr_hitoff[t]);
+    uint32_t ohoff = hoff;  // first hit among the event's output hits
+    if (use_mlp) {          // the scored candidates: only the kept ones, at their ranks
+      k = __ldg(&wk.tr_orank[t]);
+      if (k == kInv) continue;
+      ohoff = __ldg(&wk.tr_ohoff[t]);
+    }
     const uint32_t* th = wk.tr_hits + r.hit_base + hoff;
     const float2* tp = wk.tr_pos + r.hit_base + hoff;
     float st[12];
@@ -162,9 +169,94 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
     for (int q = 0; q < 12; ++q) out.states[q * ocap + o0 + k] = st[q];
     out.states[12 * ocap + o0 + k] = use_mlp ? 1.0f / (1.0f + expf(-__ldg(&wk.tr_logit[t]))) : 0.0f;
     out.ndof[o0 + k] = (uint8_t)(2 * nh - 4);
-    out.hit_off[o0 + k] = r.out_hit_base + hoff;
-    for (uint32_t j = 0; j < nh; ++j) out.hit_ids[r.out_hit_base + hoff + j] = __ldg(&th[j]) & 0xFFFFu;
+    out.hit_off[o0 + k] = r.out_hit_base + ohoff;
+    for (uint32_t j = 0; j < nh; ++j) out.hit_ids[r.out_hit_base + ohoff + j] = __ldg(&th[j]) & 0xFFFFu;
   }
+}
+
+// Classifier, step 1: one thread per scratch candidate over the whole batch
+// fits it (as the emit kernel fits a kept track), forms its features and
+// evaluates the network; the logit goes to tr_logit and the keep flag
+// (logit >= threshold) to tr_orank.
+__global__ void __launch_bounds__(kEmitThreads) classify_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
+                                                                DevParams par, WorkView wk) {
+  __shared__ float s_z[kMaxModules];
+  for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
+  __syncthreads();
+  const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
+  const float kms = fit_kms(par);
+  const uint32_t total = *(volatile uint32_t*)&wk.cnt->track_cursor;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total && t < wk.cap_tracks;
+       t += gridDim.x * blockDim.x) {
+    const uint32_t e = __ldg(&wk.tr_event[t]);
+    if (e >= n_events) continue;  // a slot of an event that ran out of scratch storage
+    const uint32_t hb = wk.rec[e].hit_base;
+    const uint32_t n = __ldg(&wk.tr_nhits[t]);
+    const uint32_t hoff = __ldg(&wk.tr_hitoff[t]);
+    const uint32_t* th = wk.tr_hits + hb + hoff;
+    const float2* tp = wk.tr_pos + hb + hoff;
+    float st[12];
+    fit_track(
+        n,
+        [&](uint32_t j, float& x, float& y, int& m) {
+          const float2 v = __ldg(&tp[j]);
+          x = v.x;
+          y = v.y;
+          m = (int)(__ldg(&th[j]) >> 16);
+        },
+        s_z, sig2, kms, st);
+    float f[kMlpIn];
+    mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, (int)(__ldg(&th[0]) >> 16),
+                 (int)(__ldg(&th[n - 1]) >> 16), f);
+    const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
+    wk.tr_logit[t] = logit;
+    wk.tr_orank[t] = logit >= par.mlp_logit_threshold ? 1u : 0u;
+  }
+}
+
+// Classifier, step 2: one warp per event walks its candidates in canonical
+// order and gives each kept one its rank and first output hit among the kept
+// ones (kInv for the others); the event's record then counts the kept tracks
+// and hits, which the scan and emit kernels use.
+constexpr int kCompactThreads = 128;
+__global__ void __launch_bounds__(kCompactThreads) compact_kernel(uint32_t n_events, WorkView wk) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (kCompactThreads / 32);
+  for (uint32_t e = blockIdx.x * (kCompactThreads / 32) + (threadIdx.x >> 5); e < n_events; e += warps) {
+    const EventRec r = wk.rec[e];
+    if (r.n_tracks == 0) continue;
+    uint32_t K = 0, NH = 0;
+    for (uint32_t c0 = 0; c0 < r.n_tracks; c0 += 32) {
+      const uint32_t t = r.track_base + c0 + lane;
+      const bool have = c0 + lane < r.n_tracks;
+      const bool keep = have && wk.tr_orank[t] == 1u;
+      const uint32_t nh = keep ? (uint32_t)wk.tr_nhits[t] : 0u;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
+      const uint32_t incl = warp_incl_scan(nh);
+      if (have) {
+        wk.tr_orank[t] = keep ? K + (uint32_t)__popc(m & ((1u << lane) - 1u)) : kInv;
+        wk.tr_ohoff[t] = NH + incl - nh;
+      }
+      K += (uint32_t)__popc(m);
+      NH += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    if (lane == 0) {
+      wk.rec[e].n_tracks = K;
+      wk.rec[e].n_hits = NH;
+    }
+  }
+}
+
+cudaError_t launch_classify(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const WorkView& wk,
+                            cudaStream_t st) {
+  if (n_events == 0) return cudaSuccess;
+  classify_kernel<<<152u * (2048u / kEmitThreads), kEmitThreads, 0, st>>>(n_events, geo, par, wk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint32_t per = kCompactThreads / 32;
+  const uint32_t grid = (n_events + per - 1) / per < 152u * 16u ? (n_events + per - 1) / per : 152u * 16u;
+  compact_kernel<<<grid, kCompactThreads, 0, st>>>(n_events, wk);
+  return cudaGetLastError();
 }
 
 // Refit of reconstructed tracks with a momentum per track: one thread per

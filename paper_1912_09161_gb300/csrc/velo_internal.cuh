@@ -157,6 +157,10 @@ struct WorkView {
   uint32_t* tr_event;            // [cap_tracks] event of the track
   uint32_t* tr_hits;             // [cap_hits] module << 16 | event-local canonical id
   float2* tr_pos;                // [cap_hits] position (x, y) of each of those hits
+  // with the classifier, where the scored candidates go: rank among the
+  // event's kept tracks (kInv: not kept) and first hit among their hits
+  uint32_t* tr_orank;            // [cap_tracks]
+  uint32_t* tr_ohoff;            // [cap_tracks]
   // tracking-kernel hit slots per class: kMaxModules positions per candidate,
   // max_tracks candidates per CTA, one region per CTA of the class
   uint16_t* trk_hits[kMaxClasses];
@@ -224,6 +228,11 @@ cudaError_t launch_refit(uint32_t n_events, const DevGeometry* geo, const DevPar
                          const float* p_gev, float* states, uint32_t pitch, cudaStream_t st);
 cudaError_t launch_emit(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const EventsView& ev,
                         const WorkView& wk, const velo_output& out, cudaStream_t st);
+// Classifier (velo_emit.cu): every scratch candidate fitted and scored, then
+// per event the kept ones (logit >= threshold) ranked in canonical order and
+// the event's record set to their counts.
+cudaError_t launch_classify(uint32_t n_events, const DevGeometry* geo, const DevParams& par, const WorkView& wk,
+                            cudaStream_t st);
 
 // Primary-vertex finding (velo_pv.cu): working bytes for up to max_events
 // events and max_tracks tracks (per-track sums, per-event vertex slots and

@@ -458,31 +458,10 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
         t_key[t] = keep ? (((uint32_t)pid[pa] << 16) | pid[pb]) : 0xFFFFFFFFu;
       }
     } else {
-      // classifier: fit every candidate, keep it when its logit reaches the
-      // threshold; the logit is kept (in the seed-scatter slot) for the score
-      const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
-      const float kms = fit_kms(par);
-      for (uint32_t t = tid; t < ntr; t += NT) {
-        const uint16_t* th = trk + (size_t)t * kMaxModules;
-        const uint32_t n = t_n[t];
-        float st[12];
-        fit_track(
-            n,
-            [&](uint32_t k, float& x, float& y, int& m) {
-              const uint32_t p = th[k];
-              const float2 v = pos[p];
-              x = v.x;
-              y = v.y;
-              m = module_of(s_cb, (int)nm, p);
-            },
-            s_z, sig2, kms, st);
-        float f[kMlpIn];
-        mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, module_of(s_cb, (int)nm, th[0]),
-                     module_of(s_cb, (int)nm, th[n - 1]), f);
-        const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
-        t_seed[t] = logit;
-        t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)pid[t_pa[t]] << 16) | pid[t_pb[t]]) : 0xFFFFFFFFu;
-      }
+      // classifier: every candidate goes to scratch in canonical order; the
+      // batch's scoring kernel fits and scores it, and a per-event pass keeps
+      // those whose logit reaches the threshold
+      for (uint32_t t = tid; t < ntr; t += NT) t_key[t] = ((uint32_t)pid[t_pa[t]] << 16) | pid[t_pb[t]];
     }
     __syncthreads();
     uint32_t kept_local = 0;
@@ -550,7 +529,7 @@ __global__ void __launch_bounds__(NT, GLOBAL ? 1 : 1024 / NT) track_kernel(const
         wk.tr_pos[h0 + k] = pos[p];
       }
       const size_t o = (size_t)tb + r;
-      wk.tr_logit[o] = use_mlp ? t_seed[t] : 0.0f;
+      wk.tr_logit[o] = 0.0f;  // the classifier's scoring kernel sets it
       wk.tr_nhits[o] = (uint16_t)n;
       wk.tr_hitoff[o] = t_hoff[r];
       wk.tr_event[o] = e;

@@ -18,7 +18,8 @@
 //     module i - 2's hits into the staging buffer (waited for at the round's
 //     end);
 // so every hit is read from global memory once.  After the rounds the kernel
-// applies the plain cuts (or the classifier), ranks the kept candidates
+// applies the plain cuts (with the classifier: keeps every candidate for the
+// batch's scoring kernel), ranks the kept candidates
 // canonically and writes their hits (module, canonical id) and the hits'
 // positions to scratch for the emit kernel, which fits them.  Candidate hit
 // lists (module << 16 | canonical id, and the positions, which a hit has at
@@ -627,28 +628,11 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       t_key[t] = keep ? ((ha << 16) | hb) : 0xFFFFFFFFu;
     }
   } else {
-    const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
-    const float kms = fit_kms(par);
-    for (uint32_t t = tid; t < ntr; t += NT) {
-      const uint32_t* th = trk + (size_t)t * TH;
-      const float2* tp = tpos + (size_t)t * TH;
-      const uint32_t n = t_n[t];
-      float st[12];
-      fit_track(
-          n,
-          [&](uint32_t k, float& x, float& y, int& m) {
-            const float2 v = tp[k];
-            m = (int)(th[k] >> 16);
-            x = v.x;
-            y = v.y;
-          },
-          s_z, sig2, kms, st);
-      float f[kMlpIn];
-      mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, (int)(th[0] >> 16), (int)(th[n - 1] >> 16), f);
-      const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
-      mseed[t] = logit;
-      t_key[t] = logit >= par.mlp_logit_threshold ? (((uint32_t)mpa[t] << 16) | mpb[t]) : 0xFFFFFFFFu;
-    }
+    // classifier: every candidate goes to scratch in canonical order; a flat
+    // kernel over the batch fits and scores them, and a per-event pass keeps
+    // those whose logit reaches the threshold (the kept ones stay in
+    // canonical order)
+    for (uint32_t t = tid; t < ntr; t += NT) t_key[t] = ((uint32_t)mpa[t] << 16) | mpb[t];
   }
   __syncthreads();
   uint32_t kept_local = 0;
@@ -723,7 +707,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       }
     }
     const size_t o = (size_t)tb + r;
-    __stcs(&wk.tr_logit[o], use_mlp ? mseed[t] : 0.0f);
+    __stcs(&wk.tr_logit[o], 0.0f);  // the classifier's scoring kernel sets it
     __stcs(&wk.tr_nhits[o], (unsigned short)n);
     __stcs(&wk.tr_hitoff[o], t_hoff[r]);
     __stcs(&wk.tr_event[o], e);

@@ -147,10 +147,12 @@ def _oracle_kept(geom, ev, params, mean, istd, thr):
     return r, keep, lg, ev_of
 
 
-def _run_mlp(V, geom, ev, st, thr):
+def _run_mlp(V, geom, ev, st, thr, schedule=None):
     p = V.Params(use_mlp=1, mlp_logit_threshold=float(thr))
     rec = V.Reconstructor(geom, p, max_events=ev.n_events, max_pixels=ev.n_pixels)
     rec.set_mlp(st.params_bf16, st.mean, st.istd)
+    if schedule:
+        rec.set_schedule(*schedule)
     res = rec.run(V.upload_events(ev))
     rec.close()
     return res
@@ -166,14 +168,18 @@ def trained(env, train_set):
     return st
 
 
-def test_fused_inference_parity(env, trained):
+@pytest.mark.parametrize("schedule", [None, (256, 0x60, 1), (256, 0x10, 1)])
+def test_fused_inference_parity(env, trained, schedule):
+    """The candidates the classifier keeps, their states and scores, as the
+    oracle's, under the default schedule (narrow and wide module windows),
+    the wide window alone and whole-event classes only."""
     V, ghost, torch, geom = env
     st = trained
     ev = velo_synth.generate(velo_synth.config(0))
     pb = (st.params_bf16.astype(np.uint32) << 16).view(np.float32)
     for thr in (-1.0, 1.5):
         r, keep, lg, ev_of = _oracle_kept(geom, ev, pb, st.mean, st.istd, thr)
-        res = _run_mlp(V, geom, ev, st, thr)
+        res = _run_mlp(V, geom, ev, st, thr, schedule)
         for e in range(ev.n_events):
             ts = np.nonzero((ev_of == e) & keep)[0]
             ref = [tuple(int(h) for h in r.track_hits(t)) for t in ts]
