@@ -12,9 +12,10 @@
 //      the best hit of the next module, phase B seeds triplets around every
 //      unused middle hit (section 2.3.1: seeds of three hits on consecutive
 //      layers, extended to the other layers);
-//   3. apply the plain cuts (or the classifier), rank the kept tracks
-//      canonically and write their hits (ids, positions, modules) to scratch;
-//      the emit kernel fits them.
+//   3. apply the plain cuts (with the classifier: keep every candidate for
+//      the batch's scoring kernel), rank the kept tracks canonically and
+//      write their hits (ids, positions, modules) to scratch; the emit
+//      kernel fits them.
 // Hits live in shared memory in (module, phi bin) order ("positions"); the
 // used flags and the windows refer to positions, every decision that prefers
 // one hit to another compares canonical ids.  Each candidate's hit positions
@@ -27,8 +28,6 @@
 #include <stdint.h>
 
 #include "velo_device.cuh"
-#include "velo_fit.cuh"
-#include "velo_mlp.cuh"
 #include "velo_track_common.cuh"
 
 namespace velo {

@@ -38,8 +38,6 @@
 #include <type_traits>
 
 #include "velo_device.cuh"
-#include "velo_fit.cuh"
-#include "velo_mlp.cuh"
 #include "velo_track_common.cuh"
 
 namespace velo {
