@@ -181,8 +181,15 @@ __global__ void __launch_bounds__(kEmitThreads) emit_fit_kernel(uint32_t n_event
 __global__ void __launch_bounds__(kEmitThreads) classify_kernel(uint32_t n_events, const DevGeometry* __restrict__ geo,
                                                                 DevParams par, WorkView wk) {
   __shared__ float s_z[kMaxModules];
+  // the network's parameters (BF16 pairs) and standardisation, read by every
+  // thread for every candidate: once per block into shared memory
+  __shared__ uint32_t s_w[(kMlpParams + 1) / 2];
+  __shared__ float s_norm[2 * kMlpIn];
   for (int m = threadIdx.x; m < kMaxModules; m += blockDim.x) s_z[m] = m < geo->n_modules ? geo->module_z[m] : 0.0f;
+  for (int q = threadIdx.x; q < (kMlpParams + 1) / 2; q += blockDim.x) s_w[q] = ((const uint32_t*)wk.mlp_w)[q];
+  for (int q = threadIdx.x; q < 2 * kMlpIn; q += blockDim.x) s_norm[q] = wk.mlp_norm[q];
   __syncthreads();
+  const uint16_t* w = (const uint16_t*)s_w;
   const float sig2 = fmul(par.sigma_meas, par.sigma_meas);
   const float kms = fit_kms(par);
   const uint32_t total = *(volatile uint32_t*)&wk.cnt->track_cursor;
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(kEmitThreads) classify_kernel(uint32_t n_event
     float f[kMlpIn];
     mlp_features(st[0], st[1], st[3], st[4], st[11], (int)n, (int)(__ldg(&th[0]) >> 16),
                  (int)(__ldg(&th[n - 1]) >> 16), f);
-    const float logit = mlp_logit(f, wk.mlp_w, wk.mlp_norm, wk.mlp_norm + kMlpIn);
+    const float logit = mlp_logit(f, w, s_norm, s_norm + kMlpIn);
     wk.tr_logit[t] = logit;
     wk.tr_orank[t] = logit >= par.mlp_logit_threshold ? 1u : 0u;
   }
