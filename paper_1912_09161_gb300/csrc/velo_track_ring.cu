@@ -307,6 +307,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
   const int nm = geo->n_modules;
   const float tol = par.tan_phi_tol, win = par.phi_window;
   constexpr bool use_mlp = MLP;
+  static_assert((GA == 1 || GA == 2) && (GB == 1 || GB == 2), "one or two lanes per item");
 
   // this CTA's global region
   const RingScratch& R = wk.ring[SH];
@@ -377,9 +378,13 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     // round: an array of both indexed by cur would live in local memory)
     const ActList A = act_list<C::ACT>(smem + L.act + (cur ? C::kActBytes : 0u));
     const ActList N = act_list<C::ACT>(smem + L.act + (cur ? 0u : C::kActBytes));
-    for (uint32_t j0 = (32u / GA) * warp; j0 < nact; j0 += NT / GA) {
-      const uint32_t j = j0 + lane / GA;
-      const int la = lane % GA;
+    // GA lanes per track, or one in the narrow shape where one pass of GA
+    // lanes per track would not cover the round's tracks
+    const int gsh = (GA == 2 && !(C::kNarrow && nact > (uint32_t)(NT / 2))) ? 1 : 0;
+    const int ga = 1 << gsh;
+    for (uint32_t j0 = (32u >> gsh) * warp; j0 < nact; j0 += (uint32_t)NT >> gsh) {
+      const uint32_t j = j0 + (lane >> gsh);
+      const int la = lane & (ga - 1);
       const bool valid = j < nact;
       float xl = 0.0f, yl = 0.0f, zl = 0.0f, tx = 0.0f, ty = 0.0f;
       uint32_t t = 0, n = 0, sk = 0, mz = 0;
@@ -398,7 +403,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
         const float xp = fadd(xl, fmul(tx, dzi));
         const float yp = fadd(yl, fmul(ty, dzi));
         const Cand cw = window_cands(Si.bins, 0, pseudo_angle(xl, yl), phi_halfwidth(xl, yl, win));
-        for (uint32_t k = la; k < cw.n(); k += GA) {
+        for (uint32_t k = la; k < cw.n(); k += ga) {
           const uint32_t p = cw.at(k);
           const float2 v = Si.pos[p];
           // scatter first (the most selective test; one that cannot beat
@@ -410,8 +415,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
           best = min(best, ((unsigned long long)__float_as_uint(s2) << 32) | ((uint32_t)Si.pid[p] << 16) | p);
         }
       }
-#pragma unroll
-      for (int off = 1; off < GA; off <<= 1) best = min(best, __shfl_xor_sync(kFull, best, off));
+      if (ga == 2) best = min(best, __shfl_xor_sync(kFull, best, 1));
       bool keep = false;
       if (valid && la == 0) {
         if (best != ~0ull) {
@@ -482,12 +486,16 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     {
       const float za = s_z[i + 2], zb = s_z[i + 1];
       const float dzab = fsub(za, zb), dzc = fsub(zi, zb), dzbc = fsub(zb, zi);
-      constexpr int NG = NT / GB;
-      const int g = tid / GB, gl = tid % GB;
       const uint32_t nbl = s_misc[R_NB];
+      // GB lanes per middle hit, or one in the narrow shape where one pass of
+      // GB lanes per hit would not cover the round's middle hits
+      const int bsh = (GB == 2 && !(C::kNarrow && nbl > (uint32_t)(NT / 2))) ? 1 : 0;
+      const int gb = 1 << bsh;
+      const uint32_t NG = (uint32_t)NT >> bsh;
+      const int g = tid >> bsh, gl = tid & (gb - 1);
       for (uint32_t b0 = 0; b0 < nbl; b0 += NG) {
         // a warp whose groups all lie past the list has nothing to do
-        if (b0 + (uint32_t)warp * (32u / GB) >= nbl) continue;
+        if (b0 + ((uint32_t)warp << (5 - bsh)) >= nbl) continue;
         const bool has = b0 + g < nbl;
         const uint32_t qb = has ? blist[b0 + g] : 0u;
         unsigned long long best = ~0ull;
@@ -498,7 +506,7 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
           const float pab = pseudo_angle(vb.x, vb.y), wb = phi_halfwidth(vb.x, vb.y, win);
           const Cand ca = window_cands(Sa.bins, 0, pab, wb);
           const Cand cc = window_cands(Si.bins, 0, pab, wb);
-          for (uint32_t k = gl; k < ca.n(); k += GB) {
+          for (uint32_t k = gl; k < ca.n(); k += gb) {
             const uint32_t qa = ca.at(k);
             if (bit(Sa.used, qa)) continue;
             const float2 va = Sa.pos[qa];
@@ -524,10 +532,9 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
             }
           }
         }
-#pragma unroll
-        for (int off = 1; off < GB; off <<= 1) {
-          const unsigned long long ob = __shfl_xor_sync(kFull, best, off);
-          const uint32_t op = __shfl_xor_sync(kFull, bpos, off);
+        if (gb == 2) {
+          const unsigned long long ob = __shfl_xor_sync(kFull, best, 1);
+          const uint32_t op = __shfl_xor_sync(kFull, bpos, 1);
           if (ob < best) {
             best = ob;
             bpos = op;
@@ -751,6 +758,10 @@ __global__ void __launch_bounds__(RS<SH>::NT, RS<SH>::CPS) track_ring_kernel(con
 
 // Lanes per active track in phase A (two in the narrow shape, whose 64
 // threads meet about 30 active tracks a round) and per middle hit in phase B.
+// The narrow shape takes one lane per item in a round whose items two lanes
+// each would not cover in one pass (about 33 middle hits a round on nominal
+// events: a second pass for a few hits cost more than the longer candidate
+// loops of one lane).
 template <int SH>
 constexpr int kRingGroupA = SH == kRingNarrow ? 2 : 1;
 constexpr int kRingGroupB = 2;
