@@ -103,47 +103,44 @@ __device__ __forceinline__ float bf16_hi(uint32_t p) { return __uint_as_float(p 
 // activations ReLU then BF16, sums in FP32 from the bias over ascending
 // inputs.  w: parameters as BF16 bits (4-byte aligned; every row starts at an
 // even index, so weights are read in pairs); mean / istd: standardisation.
-// The first layer is unrolled so that its outputs stay in registers; the
-// second runs four units' chains side by side, each in its own fixed order,
-// and adds their output terms in ascending unit order.
+// A loop over the first layer's units, two at a time: each pair's outputs
+// go straight into the second layer's 32 sums (registers), which so still
+// add their terms in ascending input order; the loop keeps the code small
+// enough for the instruction cache.
 __device__ __forceinline__ float mlp_logit(const float f[kMlpIn], const uint16_t* w, const float* mean,
                                            const float* istd) {
-  static_assert(kMlpIn % 2 == 0 && kMlpH % 4 == 0 && kOffW1 % 2 == 0 && kOffW2 % 2 == 0, "weight pairs");
+  static_assert(kMlpIn % 2 == 0 && kMlpH % 2 == 0 && kOffW1 % 2 == 0 && kOffW2 % 2 == 0, "weight pairs");
   const uint32_t* wp = (const uint32_t*)w;
   float x[kMlpIn];
 #pragma unroll
   for (int i = 0; i < kMlpIn; ++i) x[i] = bf16_round(fmul(fsub(f[i], mean[i]), istd[i]));
-  float h1[kMlpH];
+  float acc[kMlpH];
 #pragma unroll
-  for (int j = 0; j < kMlpH; ++j) {
-    float acc = bf16_value(w[kOffB1 + j]);
+  for (int u = 0; u < kMlpH; ++u) acc[u] = bf16_value(w[kOffB2 + u]);
+#pragma unroll 1
+  for (int j = 0; j < kMlpH; j += 2) {
+    float h[2];
 #pragma unroll
-    for (int i = 0; i < kMlpIn; i += 2) {
-      const uint32_t p = wp[(kOffW1 + j * kMlpIn + i) / 2];
-      acc = fadd(acc, fmul(bf16_lo(p), x[i]));
-      acc = fadd(acc, fmul(bf16_hi(p), x[i + 1]));
+    for (int q = 0; q < 2; ++q) {
+      float a = bf16_value(w[kOffB1 + j + q]);
+#pragma unroll
+      for (int i = 0; i < kMlpIn; i += 2) {
+        const uint32_t p = wp[(kOffW1 + (j + q) * kMlpIn + i) / 2];
+        a = fadd(a, fmul(bf16_lo(p), x[i]));
+        a = fadd(a, fmul(bf16_hi(p), x[i + 1]));
+      }
+      h[q] = bf16_round(fmaxf(a, 0.0f));
     }
-    h1[j] = bf16_round(fmaxf(acc, 0.0f));
+#pragma unroll
+    for (int u = 0; u < kMlpH; ++u) {
+      const uint32_t p = wp[(kOffW2 + u * kMlpH + j) / 2];
+      acc[u] = fadd(acc[u], fmul(bf16_lo(p), h[0]));
+      acc[u] = fadd(acc[u], fmul(bf16_hi(p), h[1]));
+    }
   }
   float out = bf16_value(w[kOffB3]);
-#pragma unroll 1
-  for (int j0 = 0; j0 < kMlpH; j0 += 4) {
-    float acc[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = bf16_value(w[kOffB2 + j0 + u]);
-#pragma unroll
-    for (int k = 0; k < kMlpH; k += 2) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t p = wp[(kOffW2 + (j0 + u) * kMlpH + k) / 2];
-        acc[u] = fadd(acc[u], fmul(bf16_lo(p), h1[k]));
-        acc[u] = fadd(acc[u], fmul(bf16_hi(p), h1[k + 1]));
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      out = fadd(out, fmul(bf16_value(w[kOffW3 + j0 + u]), bf16_round(fmaxf(acc[u], 0.0f))));
-  }
+  for (int u = 0; u < kMlpH; ++u) out = fadd(out, fmul(bf16_value(w[kOffW3 + u]), bf16_round(fmaxf(acc[u], 0.0f))));
   return out;
 }
 
