@@ -55,7 +55,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "track_kernel_nominal_10k.md")
 # sources of the tracking kernels, in the order the profile summary hashes them
 TRACK_SOURCES = ("velo_track_ring.cu", "velo_track.cu", "velo_track_common.cuh", "velo_internal.cuh",
-                 "velo_device.cuh", "velo_fit.cuh", "velo_mlp.cuh")
+                 "velo_device.cuh")
 # per call: clustering and its second pass, the queue ordering, the retry and
 # global-memory tracking passes, scan, and the two emit kernels; then one
 # launch per tracking class, and the wide-window pass when both window shapes
