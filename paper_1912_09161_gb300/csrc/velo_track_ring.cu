@@ -13,10 +13,10 @@
 // wide shape (nine events share an SM; the register budget sets the nine),
 // 15 KB in the narrow one (fourteen).  The hits come straight from the
 // clustering output:
-//   - during phase A of round i, one warp bins module i - 1 (staged a round
-//     earlier) by phi into the free slot, then issues the cp.async copies of
-//     module i - 2's hits into the staging buffer (waited for at the round's
-//     end);
+//   - after its phase A of round i, one warp bins module i - 1 (staged a
+//     round earlier) by phi into the free slot while the other warps seed,
+//     then issues the cp.async copies of module i - 2's hits into the
+//     staging buffer (waited for at the round's end);
 // so every hit is read from global memory once.  After the rounds the kernel
 // applies the plain cuts (with the classifier: keeps every candidate for the
 // batch's scoring kernel), ranks the kept candidates
@@ -152,6 +152,11 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src, 
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem_src), "l"(policy)
                : "memory");
+}
+// Named barriers 1 and 2 over n threads (barrier 0 is __syncthreads).
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -368,11 +373,11 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
     const auto Si = slot_of<SH>(slots, i), Sb = slot_of<SH>(slots, i + 1), Sa = slot_of<SH>(slots, i + 2);
     bool ovf = false;
     // phase A: every active track is extended into module i by its best
-    // hit (GA lanes per track).  Meanwhile warp NW - 2 makes the b and c
-    // hits of the last round's seeds used (modules i + 2 and i + 1) and
-    // lists the unused middle hits of module i + 1, and warp NW - 1 bins
-    // module i - 1 into the free slot, then stages module i - 2 (binned in
-    // the next round).
+    // hit (GA lanes per track).  Then warp NW - 2 makes the b and c hits of
+    // the last round's seeds used (modules i + 2 and i + 1) and lists the
+    // unused middle hits of module i + 1, and warp NW - 1 bins module i - 1
+    // into the free slot while the others seed, then stages module i - 2
+    // (binned in the next round).
     const uint32_t nact = s_misc[R_NACT + cur];
     // this round's active list and the next round's (pointers formed per
     // round: an array of both indexed by cur would live in local memory)
@@ -476,12 +481,25 @@ __device__ __forceinline__ void window_event(const DevGeometry* __restrict__ geo
       }
       if (lane == 0) s_misc[R_NB] = cnt;
     }
-    if (warp == NW - 1 && i >= 1) {
-      bin_module<SH>(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
-      if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage, lane, 32);  // after the warp's reads
+    // phase A and the used/pending update done: the binning warp signals its
+    // phase A on barrier 1 and bins while the other warps seed, then waits
+    // on barrier 2 for their phase A before it seeds itself.  Each barrier
+    // counts every thread once (arrive or sync), and every warp runs every
+    // round, so both complete each round.  An overflow in phase A is acted
+    // on at the round's end barrier (phase B's writes stay within bounds).
+    __threadfence_block();
+    if (warp == NW - 1) {
+      bar_arrive(1, NT);
+      if (i >= 1) {
+        bin_module<SH>(i - 1, s_cb, slots, s_wbin, [&](uint32_t j) { return stage[j]; });
+        if (i >= 2) stage_module(i - 2, s_cb, so, wk.prov, stage, lane, 32);  // after the warp's reads
+      }
+      bar_sync(2, NT);
+    } else {
+      bar_arrive(2, NT);
+      bar_sync(1, NT);
     }
-    if (__syncthreads_or(ovf)) { overflow = true; break; }
-    if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barrier
+    if (tid == 0) s_misc[R_NACT + cur] = 0;  // read by everyone before the barriers
     // phase B: seeds with the middle hit b in module i + 1
     {
       const float za = s_z[i + 2], zb = s_z[i + 1];
