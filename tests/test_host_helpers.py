@@ -43,6 +43,23 @@ def test_latency_summary_percentiles():
     assert s["max_ms"] == 100.0
 
 
+def test_profile_hash_covers_the_tracking_kernels_sources():
+    """The sources the profile hash covers are exactly the tracking kernels'
+    translation units and every local header they include, transitively, so
+    that a change to any of them voids the committed traffic figure."""
+    import re
+    csrc = os.path.join(ROOT, "paper_1912_09161_gb300", "csrc")
+    seen, todo = set(), ["velo_track_ring.cu", "velo_track.cu"]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue  # velo.h lives in include/ and is the public ABI
+        seen.add(f)
+        with open(os.path.join(csrc, f)) as fh:
+            todo += re.findall(r'^#include "([^"]+)"', fh.read(), re.M)
+    assert seen == set(bench.TRACK_SOURCES)
+
+
 def test_profile_traffic_needs_the_profiled_sources(tmp_path, monkeypatch):
     """The bench reports the ncu DRAM traffic only while the summary's source
     hash matches the kernel sources (a summary written here with the current
